@@ -1,0 +1,258 @@
+/*
+ * sgcp.h -- C ABI of the GB300 streaming-GCP library (libsgcp.so).
+ *
+ * Streaming Generalized CP decomposition (Phipps, Johnson, Kolda, arXiv
+ * 2110.14514).  As each tensor slice X_t (a d-way tensor, d = 2..4) arrives,
+ * the library fits its temporal weights s_t with the factor matrices held
+ * fixed (Alg. 3, or the Gaussian least-squares solve of Sec. 5), then updates
+ * the factor matrices A^(1..d) against the streaming objective of Sec. 4.2
+ * (eq. gcp_stream_objective): the GCP loss of the new slice, the model-based
+ * history penalty 1/2 sum_h w_h ||Mbar_h - M_h||^2 over a reservoir-sampled
+ * window of earlier steps, and lambda/mu regularisation (Alg. 4), with ADAM
+ * steps that are checkpointed and rolled back per epoch (Alg. 2).  Sparse
+ * slices use stratified sampling of nonzeros and zeros (Alg. 5, Alg. 6).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an sgcp_status and never throws or aborts.
+ *  - "device" pointers are CUDA global-memory pointers on the context's
+ *    device (for instance the data pointers of torch tensors); "host"
+ *    pointers are ordinary CPU memory.  The caller owns every pointer it
+ *    passes and must keep device inputs alive until the work queued on the
+ *    context's stream has completed.  The library owns its own state, which
+ *    it allocates at sgcp_create and frees at sgcp_destroy.
+ *  - Floating-point arrays use the context's element type: double when
+ *    params.precision == SGCP_PREC_F64, float otherwise.
+ *  - Factor matrices A^(k) are row-major I_k x R (row i = R contiguous
+ *    values), s is a vector of R values, dense slices are stored in C order
+ *    (last index fastest), sparse slices are COO with 0-based int32
+ *    coordinates, one row of ndim coordinates per nonzero.
+ *  - Work is queued asynchronously on the stream given to sgcp_create.
+ *    Argument errors are reported synchronously.  Errors detected on the
+ *    device (bad coordinates, exhausted zero sampling, non-finite values)
+ *    are latched into a device error word; sgcp_check / sgcp_stats read it
+ *    (synchronising the stream) and from then on the context answers
+ *    SGCP_ERR_STATE until it is destroyed.
+ *  - One context must be used by one host thread at a time.
+ *
+ * Limits: 2 <= ndim <= 4; rank R a multiple of 4 with 4 <= R <= 128; dense
+ * slices need ndim <= 3; coordinates fit int32; the product of the
+ * dimensions fits in 63 bits.
+ */
+#ifndef SGCP_H
+#define SGCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SGCP_OK = 0,
+    SGCP_ERR_ARG = 1,            /* invalid argument (reported synchronously) */
+    SGCP_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    SGCP_ERR_OOM = 3,            /* device allocation failed */
+    SGCP_ERR_SAMPLING_LIMIT = 4, /* a zero-sample slot found no zero within zero_attempt_cap tries */
+    SGCP_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    SGCP_ERR_NUMERIC = 6,        /* non-finite objective value */
+    SGCP_ERR_STATE = 7,          /* the context latched an earlier error */
+    SGCP_ERR_UNSUPPORTED = 8,    /* valid request outside the implemented limits */
+    SGCP_ERR_DATA = 9            /* slice data invalid: coordinate out of range or duplicate */
+} sgcp_status;
+
+/* GCP losses f(x, m) (Sec. 2.2, eq. GCP_problem; log m evaluated as log(m + log_eps)). */
+typedef enum {
+    SGCP_LOSS_GAUSSIAN = 0,        /* (x - m)^2 */
+    SGCP_LOSS_POISSON = 1,         /* m - x log m */
+    SGCP_LOSS_BERNOULLI_ODDS = 2,  /* log(m + 1) - x log m */
+    SGCP_LOSS_BERNOULLI_LOGIT = 3  /* log(1 + e^m) - x m */
+} sgcp_loss;
+
+typedef enum {
+    SGCP_PREC_F32 = 0,          /* all arithmetic in float (reductions of losses in double) */
+    SGCP_PREC_F64 = 1,          /* all arithmetic in double (dense slices only) */
+    SGCP_PREC_BF16_MTTKRP = 2,  /* dense MTTKRP operands in bf16 on tensor cores, fp32 accumulate */
+    SGCP_PREC_F16_MTTKRP = 3    /* dense MTTKRP operands in fp16 on tensor cores, fp32 accumulate */
+} sgcp_precision;
+
+typedef enum {
+    SGCP_TEMPORAL_ADAM = 0,     /* Alg. 3 */
+    SGCP_TEMPORAL_LSQ = 1       /* Gaussian least-squares solve (Sec. 5) */
+} sgcp_temporal;
+
+typedef enum {
+    SGCP_OPT_ADAM = 0,          /* Alg. 4 */
+    SGCP_OPT_LBFGS = 1          /* projected L-BFGS on the exact objective (dense slices; not in the paper) */
+} sgcp_optimizer;
+
+/* OnlineGCP arguments (Table 1) and solver settings (Table 2).  Fill with
+ * sgcp_params_default, then set the problem fields (ndim, dims, rank, loss). */
+typedef struct {
+    int32_t ndim;             /* d, number of slice modes (2..4) */
+    int32_t rank;             /* R */
+    int64_t dims[4];          /* I_1..I_d */
+    int32_t loss;             /* sgcp_loss */
+    int32_t precision;        /* sgcp_precision */
+    double lower_bound;       /* l; NaN selects the loss default (0 for Poisson/odds, -inf otherwise) */
+    double log_eps;           /* epsilon of log(m + eps) */
+    int32_t H;                /* maximum history window size */
+    int32_t temporal;         /* sgcp_temporal */
+    double w, theta;          /* history weights w_h = w theta^(t-h) */
+    double lambda, mu;        /* factor / temporal-weight regularisation */
+    int64_t p, q;             /* gradient samples: nonzeros, zeros (sparse slices) */
+    int64_t p_obj, q_obj;     /* objective samples: nonzeros, zeros (sparse slices) */
+    double tol_w, tol_f;      /* epoch loop continues while the estimate exceeds tol */
+    int32_t kappa_w, kappa_f; /* maximum epochs */
+    int32_t tau_w, tau_f;     /* iterations per epoch */
+    double alpha_w, alpha_f;  /* ADAM learning rates */
+    double beta1, beta2, adam_eps;
+    double alpha_decay;       /* learning-rate factor applied on a rejected epoch */
+    int32_t zero_attempt_cap; /* attempts per zero-sample slot */
+    int32_t optimizer;        /* sgcp_optimizer */
+    int32_t lbfgs_mem;        /* L-BFGS memory */
+    int32_t lbfgs_iters;      /* L-BFGS iterations per slice */
+    uint64_t seed;            /* Philox4x32-10 key for every random draw */
+} sgcp_params;
+
+/* One slice.  Sparse: nnz COO entries (idx [nnz][ndim] int32, vals [nnz]).
+ * Dense: vals holds the full slice in C order, idx is NULL.
+ * on_host = 1 means idx / vals are host pointers; the call copies them to the
+ * device on the context's stream before use (the copy is part of the call). */
+typedef struct {
+    int32_t is_sparse;
+    int32_t on_host;
+    int64_t nnz;
+    const int32_t* idx;
+    const void* vals;
+} sgcp_slice;
+
+/* Bits of sgcp_grad_opts.want */
+#define SGCP_WANT_FACTORS 1   /* G^(k) = Y~_(k) Z_k diag(s), k = 1..d   (eq. gcp_grad_A) */
+#define SGCP_WANT_TEMPORAL 2  /* g_s = Z' vec(Y~)                       (eq. gcp_grad_lambda) */
+#define SGCP_WANT_LOSS 4      /* F~ = sum over samples of weight * f(x, m) (Alg. 5 sample sum) */
+
+/* Sample sets: which Philox purpose pair a sparse draw uses (Alg. 5 / Alg. 6). */
+#define SGCP_SAMPLES_FACTOR_GRAD 0
+#define SGCP_SAMPLES_FACTOR_OBJ 1
+#define SGCP_SAMPLES_TEMPORAL_GRAD 2
+#define SGCP_SAMPLES_TEMPORAL_OBJ 3
+
+typedef struct {
+    int32_t want;             /* SGCP_WANT_* bits */
+    int32_t sample_set;       /* SGCP_SAMPLES_*; the GRAD sets draw p + q samples, the OBJ sets p_obj + q_obj */
+    int64_t t;                /* time index placed in the sample counter */
+    uint32_t draw;            /* draw index placed in the sample counter */
+    int32_t accumulate;       /* 0: outputs are overwritten; 1: results are added to them */
+    const void* y_scale;      /* device scalar (element type) multiplying every y and f; NULL = 1 */
+} sgcp_grad_opts;
+
+typedef struct {
+    int64_t t;                    /* slices processed */
+    int64_t iter;                 /* factor-solver iteration counter i of Alg. 1 / Alg. 4 */
+    double F_w, F_f;              /* final objective estimates of the last slice's two solvers */
+    int32_t epochs_w, epochs_f;   /* epochs run in the last slice */
+    uint32_t accept_w, accept_f;  /* bit e set when epoch e of the last slice was accepted */
+    double alpha_w, alpha_f;      /* learning rates after the last slice */
+    int32_t hist_len;             /* current history window size */
+    int32_t error_bits;           /* device error word (0 = none) */
+    int64_t kernels_launched;     /* kernels queued by this context so far (graph nodes included) */
+} sgcp_stats_t;
+
+typedef struct sgcp_ctx sgcp_ctx;
+
+/* Version string of the library. */
+const char* sgcp_version(void);
+
+/* Human-readable name of a status code. */
+const char* sgcp_status_string(sgcp_status status);
+
+/* Defaults of Table 2 of the paper (beta1 = 0.9, beta2 = 0.999, eps = 1e-8,
+ * tau = 100, theta = 1, lambda = mu = 0) plus kappa_w = kappa_f = 5,
+ * alpha_w = 0.1, alpha_f = 1e-3, tol = -inf, zero_attempt_cap = 64,
+ * log_eps = 1e-10, alpha_decay = 0.1.  Returns SGCP_ERR_ARG if p is NULL. */
+sgcp_status sgcp_params_default(sgcp_params* p);
+
+/* Create a streaming context (Alg. 1, before its loop).
+ *  params        problem and solver settings (copied).
+ *  init_factors  device, ndim pointers to I_k x R initial factor matrices (copied).
+ *  n_hist        size of the initial history window (0..H), hist_t (host, n_hist
+ *                time indices, each < the first slice's t) and hist_s (device,
+ *                n_hist x R temporal weights) describe it (Table 1).
+ *  t0            time index of the last warm-start slice; the first sgcp_step is t0 + 1.
+ *  cuda_stream   cudaStream_t to queue work on (NULL = the legacy default stream).
+ *  out           receives the context.
+ * Errors: SGCP_ERR_ARG (bad parameters), SGCP_ERR_UNSUPPORTED (outside the
+ * limits above), SGCP_ERR_OOM, SGCP_ERR_CUDA. */
+sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_factors,
+                        int32_t n_hist, const int64_t* hist_t, const void* hist_s,
+                        int64_t t0, void* cuda_stream, sgcp_ctx** out);
+
+/* Destroy a context and free its device state (synchronises its stream). */
+void sgcp_destroy(sgcp_ctx* ctx);
+
+/* Message describing the most recent error of ctx ("" if none). */
+const char* sgcp_last_error(const sgcp_ctx* ctx);
+
+/* Load a slice into the context: copies host data if on_host, checks
+ * coordinates, builds the nonzero-membership hash used to reject zero-sample
+ * candidates (Sec. 4.3) and the per-mode hot-row tables.  sgcp_gradient and
+ * sgcp_step call this themselves when given a slice other than the one
+ * loaded last (compared by pointers and nnz); call it explicitly after
+ * changing the contents behind the same pointers. */
+sgcp_status sgcp_ingest(sgcp_ctx* ctx, const sgcp_slice* X);
+
+/* One stochastic (sparse) or exact (dense) GCP gradient evaluation, the
+ * fused model -> loss derivative -> MTTKRP path (Sec. 2.2 eqs. gcp_grad_A and
+ * gcp_grad_lambda; Alg. 6 sampling for sparse slices):
+ *   G_out[k] (device, I_k x R)  <- Y~_(k) Z_k diag(s)        if SGCP_WANT_FACTORS
+ *   gs_out   (device, R)        <- Z' vec(Y~)                if SGCP_WANT_TEMPORAL
+ *   f_out    (device, 1 double) <- sum of weight * f(x, m)   if SGCP_WANT_LOSS
+ * s (device, R) and A (device, ndim pointers, I_k x R) are the point of
+ * evaluation.  History and regularisation terms are not included.  Outputs
+ * not requested may be NULL.  Asynchronous on the context stream. */
+sgcp_status sgcp_gradient(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, const void* const* A,
+                          const sgcp_grad_opts* opts, void* const* G_out, void* gs_out, double* f_out);
+
+/* Materialise the coordinates of one sparse sample draw (the same draw
+ * sgcp_gradient makes with these arguments): coords_out (device int32,
+ * [n][ndim]) with n = p + q (GRAD sets) or p_obj + q_obj (OBJ sets),
+ * nonzero samples first; attempt_out (device int32 [n] or NULL) receives the
+ * accepted attempt of each zero sample and -1 for nonzero samples. */
+sgcp_status sgcp_sample_coords(sgcp_ctx* ctx, const sgcp_slice* X, int32_t sample_set, int64_t t,
+                               uint32_t draw, int32_t* coords_out, int32_t* attempt_out);
+
+/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
+ * solve, factor solve, reservoir history update, Abar <- A).  Asynchronous;
+ * the whole solver sequence runs as CUDA graphs on the context stream. */
+sgcp_status sgcp_step(sgcp_ctx* ctx, const sgcp_slice* X_t);
+
+/* Copy the current factor matrices (device, ndim pointers) and the last
+ * temporal weights (device, R) out of the context; either may be NULL.
+ * t_out (host, may be NULL) receives the index of the last processed slice.
+ * Asynchronous on the context stream. */
+sgcp_status sgcp_factors(sgcp_ctx* ctx, void* const* A_out, void* s_out, int64_t* t_out);
+
+/* Copy the history window: h_out (host, H int64 time indices) and s_out
+ * (device, H x R weights, may be NULL); *n_out receives |window|. */
+sgcp_status sgcp_history(sgcp_ctx* ctx, int64_t* h_out, void* s_out, int32_t* n_out);
+
+/* Synchronise the context stream and return its latched device error status. */
+sgcp_status sgcp_check(sgcp_ctx* ctx);
+
+/* Synchronise and report solver statistics of the last slice. */
+sgcp_status sgcp_stats(sgcp_ctx* ctx, sgcp_stats_t* out);
+
+/* Checkpoint: the state that makes the stream resumable (t, i, Abar, s,
+ * history window, factor-solver ADAM moments, learning rate).  sgcp_state_size
+ * gives the byte size; export writes it to a host buffer, import restores it
+ * into a context created with the same params.  Both synchronise. */
+sgcp_status sgcp_state_size(const sgcp_ctx* ctx, size_t* size);
+sgcp_status sgcp_state_export(sgcp_ctx* ctx, void* host_buf, size_t size);
+sgcp_status sgcp_state_import(sgcp_ctx* ctx, const void* host_buf, size_t size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGCP_H */

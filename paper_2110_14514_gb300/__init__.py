@@ -1,0 +1,309 @@
+"""Python binding of libsgcp.so, the GB300 streaming-GCP library (arXiv 2110.14514).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The C entry points are exported under their C names
+(``sgcp_create``, ``sgcp_step``, ``sgcp_gradient``, ...) with ctypes
+signatures; ``Context`` wraps one ``sgcp_ctx`` and takes torch tensors, whose
+device pointers and CUDA stream it passes to the library.
+
+There is no CPU fallback.  Importing this package loads the shared library
+and raises ``ImportError`` if it has not been built
+(``python -m paper_2110_14514_gb300.build``).
+"""
+import ctypes
+import math
+import os
+
+from ctypes import POINTER, c_double, c_int32, c_int64, c_size_t, c_uint32, c_uint64, c_void_p, c_char_p
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsgcp.so")
+
+# ----------------------------------------------------------------------------- constants (sgcp.h)
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_SAMPLING_LIMIT, ERR_TIMEOUT, ERR_NUMERIC, ERR_STATE, ERR_UNSUPPORTED, ERR_DATA = range(10)
+LOSS = {"gaussian": 0, "poisson": 1, "bernoulli_odds": 2, "bernoulli_logit": 3}
+PREC_F32, PREC_F64, PREC_BF16_MTTKRP, PREC_F16_MTTKRP = 0, 1, 2, 3
+TEMPORAL_ADAM, TEMPORAL_LSQ = 0, 1
+OPT_ADAM, OPT_LBFGS = 0, 1
+WANT_FACTORS, WANT_TEMPORAL, WANT_LOSS = 1, 2, 4
+SAMPLES_FACTOR_GRAD, SAMPLES_FACTOR_OBJ, SAMPLES_TEMPORAL_GRAD, SAMPLES_TEMPORAL_OBJ = 0, 1, 2, 3
+
+
+class sgcp_params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", c_int32), ("rank", c_int32), ("dims", c_int64 * 4), ("loss", c_int32), ("precision", c_int32),
+        ("lower_bound", c_double), ("log_eps", c_double), ("H", c_int32), ("temporal", c_int32),
+        ("w", c_double), ("theta", c_double), ("lambda_", c_double), ("mu", c_double),
+        ("p", c_int64), ("q", c_int64), ("p_obj", c_int64), ("q_obj", c_int64),
+        ("tol_w", c_double), ("tol_f", c_double), ("kappa_w", c_int32), ("kappa_f", c_int32),
+        ("tau_w", c_int32), ("tau_f", c_int32), ("alpha_w", c_double), ("alpha_f", c_double),
+        ("beta1", c_double), ("beta2", c_double), ("adam_eps", c_double), ("alpha_decay", c_double),
+        ("zero_attempt_cap", c_int32), ("optimizer", c_int32), ("lbfgs_mem", c_int32), ("lbfgs_iters", c_int32),
+        ("seed", c_uint64),
+    ]
+
+
+class sgcp_slice(ctypes.Structure):
+    _fields_ = [("is_sparse", c_int32), ("on_host", c_int32), ("nnz", c_int64), ("idx", c_void_p),
+                ("vals", c_void_p)]
+
+
+class sgcp_grad_opts(ctypes.Structure):
+    _fields_ = [("want", c_int32), ("sample_set", c_int32), ("t", c_int64), ("draw", c_uint32),
+                ("accumulate", c_int32), ("y_scale", c_void_p)]
+
+
+class sgcp_stats_t(ctypes.Structure):
+    _fields_ = [("t", c_int64), ("iter", c_int64), ("F_w", c_double), ("F_f", c_double),
+                ("epochs_w", c_int32), ("epochs_f", c_int32), ("accept_w", c_uint32), ("accept_f", c_uint32),
+                ("alpha_w", c_double), ("alpha_f", c_double), ("hist_len", c_int32), ("error_bits", c_int32),
+                ("kernels_launched", c_int64)]
+
+
+_PTRS = POINTER(c_void_p)
+
+# (name, restype, argtypes) of every entry point declared in include/sgcp.h
+SIGNATURES = [
+    ("sgcp_version", c_char_p, []),
+    ("sgcp_status_string", c_char_p, [c_int32]),
+    ("sgcp_params_default", c_int32, [POINTER(sgcp_params)]),
+    ("sgcp_create", c_int32, [POINTER(sgcp_params), _PTRS, c_int32, POINTER(c_int64), c_void_p, c_int64, c_void_p,
+                              POINTER(c_void_p)]),
+    ("sgcp_destroy", None, [c_void_p]),
+    ("sgcp_last_error", c_char_p, [c_void_p]),
+    ("sgcp_ingest", c_int32, [c_void_p, POINTER(sgcp_slice)]),
+    ("sgcp_gradient", c_int32, [c_void_p, POINTER(sgcp_slice), c_void_p, _PTRS, POINTER(sgcp_grad_opts), _PTRS,
+                                c_void_p, c_void_p]),
+    ("sgcp_sample_coords", c_int32, [c_void_p, POINTER(sgcp_slice), c_int32, c_int64, c_uint32, c_void_p,
+                                     c_void_p]),
+    ("sgcp_step", c_int32, [c_void_p, POINTER(sgcp_slice)]),
+    ("sgcp_factors", c_int32, [c_void_p, _PTRS, c_void_p, POINTER(c_int64)]),
+    ("sgcp_history", c_int32, [c_void_p, POINTER(c_int64), c_void_p, POINTER(c_int32)]),
+    ("sgcp_check", c_int32, [c_void_p]),
+    ("sgcp_stats", c_int32, [c_void_p, POINTER(sgcp_stats_t)]),
+    ("sgcp_state_size", c_int32, [c_void_p, POINTER(c_size_t)]),
+    ("sgcp_state_export", c_int32, [c_void_p, c_void_p, c_size_t]),
+    ("sgcp_state_import", c_int32, [c_void_p, c_void_p, c_size_t]),
+]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsgcp.so is not built ({LIB_PATH}); run python -m paper_2110_14514_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+for _name, _res, _args in SIGNATURES:
+    globals()[_name] = getattr(lib, _name)
+
+
+class SgcpError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = lib.sgcp_status_string(status).decode()
+        super().__init__(f"{name}: {msg}" if msg else name)
+
+
+def _check(status, ctx=None):
+    if status != OK:
+        msg = lib.sgcp_last_error(ctx).decode() if ctx else ""
+        raise SgcpError(status, msg)
+
+
+def params(dims, rank, loss="gaussian", **kw):
+    """sgcp_params filled with the library defaults, then dims / rank / loss and any field in kw
+    (``lam`` sets lambda)."""
+    p = sgcp_params()
+    _check(lib.sgcp_params_default(ctypes.byref(p)))
+    p.ndim = len(dims)
+    for k, n in enumerate(dims):
+        p.dims[k] = int(n)
+    p.rank = int(rank)
+    p.loss = LOSS[loss] if isinstance(loss, str) else int(loss)
+    for k, v in kw.items():
+        if k == "lam":
+            k = "lambda_"
+        if k == "lower":
+            k = "lower_bound"
+        if v is None and k == "lower_bound":
+            v = math.nan
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr()) if t is not None else c_void_p(0)
+
+
+def _ptr_array(ts):
+    arr = (c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = t.data_ptr() if t is not None else 0
+    return arr
+
+
+def make_slice(X=None, idx=None, vals=None):
+    """sgcp_slice for a dense tensor X or COO (idx int32 [nnz, d], vals); host tensors set on_host."""
+    sl = sgcp_slice()
+    if X is not None:
+        sl.is_sparse = 0
+        sl.on_host = 0 if X.is_cuda else 1
+        sl.nnz = X.numel()
+        sl.idx = None
+        sl.vals = X.data_ptr()
+        keep = (X,)
+    else:
+        sl.is_sparse = 1
+        sl.on_host = 0 if vals.is_cuda else 1
+        sl.nnz = vals.numel()
+        sl.idx = idx.data_ptr() if idx.numel() else None
+        sl.vals = vals.data_ptr() if vals.numel() else None
+        keep = (idx, vals)
+    return sl, keep
+
+
+class Context:
+    """One streaming-GCP context (sgcp_create ... sgcp_destroy) on the current CUDA device."""
+
+    def __init__(self, p, init_factors, hist_t=(), hist_s=None, t0=0, stream=None):
+        import torch
+        self.p = p
+        self.ndim = p.ndim
+        self.R = p.rank
+        self.dims = [p.dims[k] for k in range(p.ndim)]
+        self.dtype = torch.float64 if p.precision == PREC_F64 else torch.float32
+        for a, n in zip(init_factors, self.dims):
+            assert a.is_cuda and a.dtype == self.dtype and a.is_contiguous() and tuple(a.shape) == (n, self.R)
+        # The library works on its own stream; every call orders it after the
+        # caller's current stream and the caller's stream after it.
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._torch = torch
+        self._enter()
+        ht = (c_int64 * max(len(hist_t), 1))(*[int(h) for h in hist_t])
+        out = c_void_p()
+        st = lib.sgcp_create(ctypes.byref(p), _ptr_array(init_factors), len(hist_t), ht,
+                             _ptr(hist_s), int(t0), c_void_p(self.stream.cuda_stream), ctypes.byref(out))
+        _check(st)
+        self.h = out
+        self._keep = None
+        self._leave()
+
+    def _enter(self):
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def _leave(self):
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sgcp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _slice(self, X=None, idx=None, vals=None):
+        sl, keep = make_slice(X, idx, vals)
+        self._keep = keep
+        return sl
+
+    def ingest(self, X=None, idx=None, vals=None):
+        sl = self._slice(X, idx, vals)
+        self._enter()
+        _check(lib.sgcp_ingest(self.h, ctypes.byref(sl)), self.h)
+        self._leave()
+
+    def step(self, X=None, idx=None, vals=None):
+        sl = self._slice(X, idx, vals)
+        self._enter()
+        _check(lib.sgcp_step(self.h, ctypes.byref(sl)), self.h)
+        self._leave()
+
+    def gradient(self, s, A, X=None, idx=None, vals=None, want=WANT_FACTORS | WANT_TEMPORAL | WANT_LOSS,
+                 sample_set=SAMPLES_FACTOR_GRAD, t=1, draw=0, G=None, gs=None, f=None, accumulate=False,
+                 y_scale=None):
+        """One fused gradient evaluation; returns (G list, gs, f) as device tensors."""
+        import torch
+        dev = s.device
+        if want & WANT_FACTORS and G is None:
+            G = [torch.empty((n, self.R), dtype=self.dtype, device=dev) for n in self.dims]
+        if want & WANT_TEMPORAL and gs is None:
+            gs = torch.empty(self.R, dtype=self.dtype, device=dev)
+        if want & WANT_LOSS and f is None:
+            f = torch.empty(1, dtype=torch.float64, device=dev)
+        opts = sgcp_grad_opts(want=want, sample_set=sample_set, t=int(t), draw=int(draw),
+                              accumulate=int(bool(accumulate)), y_scale=_ptr(y_scale))
+        sl = self._slice(X, idx, vals)
+        self._enter()
+        st = lib.sgcp_gradient(self.h, ctypes.byref(sl), _ptr(s), _ptr_array(A), ctypes.byref(opts),
+                               _ptr_array(G) if G is not None else None, _ptr(gs), _ptr(f))
+        self._leave()
+        _check(st, self.h)
+        return G, gs, f
+
+    def sample_coords(self, idx, vals, sample_set, t, draw, n):
+        import torch
+        coords = torch.empty((n, self.ndim), dtype=torch.int32, device=vals.device)
+        att = torch.empty(n, dtype=torch.int32, device=vals.device)
+        sl = self._slice(None, idx, vals)
+        self._enter()
+        _check(lib.sgcp_sample_coords(self.h, ctypes.byref(sl), sample_set, int(t), int(draw), _ptr(coords),
+                                      _ptr(att)), self.h)
+        self._leave()
+        return coords, att
+
+    def factors(self):
+        import torch
+        A = [torch.empty((n, self.R), dtype=self.dtype, device="cuda") for n in self.dims]
+        s = torch.empty(self.R, dtype=self.dtype, device="cuda")
+        t = c_int64()
+        self._enter()
+        _check(lib.sgcp_factors(self.h, _ptr_array(A), _ptr(s), ctypes.byref(t)), self.h)
+        self._leave()
+        return A, s, t.value
+
+    def history(self):
+        import torch
+        H = max(self.p.H, 1)
+        h = (c_int64 * H)()
+        s = torch.empty((H, self.R), dtype=self.dtype, device="cuda")
+        n = c_int32()
+        self._enter()
+        _check(lib.sgcp_history(self.h, h, _ptr(s), ctypes.byref(n)), self.h)
+        self._leave()
+        return [h[i] for i in range(n.value)], s[: n.value]
+
+    def check(self):
+        _check(lib.sgcp_check(self.h), self.h)
+
+    def stats(self):
+        st = sgcp_stats_t()
+        code = lib.sgcp_stats(self.h, ctypes.byref(st))
+        _check(code, self.h)
+        return {f: getattr(st, f) for f, _ in sgcp_stats_t._fields_}
+
+    def state_export(self):
+        n = c_size_t()
+        _check(lib.sgcp_state_size(self.h, ctypes.byref(n)), self.h)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib.sgcp_state_export(self.h, buf, n), self.h)
+        return buf.raw
+
+    def state_import(self, data):
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(lib.sgcp_state_import(self.h, buf, len(data)), self.h)

@@ -1,0 +1,1007 @@
+// C ABI of the streaming-GCP library: context state, slice loading, the
+// direct gradient entry point, and the OnlineGCP step (Alg. 1 loop body of
+// arXiv 2110.14514) enqueued as one captured CUDA graph per slice kind.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "sgcp.h"
+
+using namespace sgcp;
+
+struct sgcp_ctx {
+    sgcp_params P;
+    int ndim = 0, R = 0;
+    int64_t dims[4] = {0, 0, 0, 0};
+    int64_t row_off[4] = {0, 0, 0, 0};
+    int64_t nrows = 0, N = 0;
+    bool f64 = false;
+    size_t esz = 4;
+    double lower = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    std::string last_error;
+    sgcp_status sticky = SGCP_OK;
+    int64_t launches = 0;
+    std::vector<void*> allocs;
+
+    // factor-solver state (N elements each, element type T)
+    void *A = nullptr, *Abar = nullptr, *G = nullptr, *u = nullptr, *v = nullptr, *u_o = nullptr, *v_o = nullptr,
+         *a_o = nullptr;
+    // temporal-solver state (R each)
+    void *s = nullptr, *s_u = nullptr, *s_v = nullptr, *s_uo = nullptr, *s_vo = nullptr, *s_ao = nullptr,
+         *gs = nullptr;
+    // history window
+    void* s_hist = nullptr;
+    int64_t* h_dev = nullptr;
+    int32_t* hist_len_dev = nullptr;
+    std::vector<int64_t> hist_t;
+    double* SH = nullptr;
+    double* grams = nullptr;     // [6][ndim][R][R]
+    float* Bc = nullptr;         // [ndim][R][R]
+    float* Cc = nullptr;
+    double* lsq_work = nullptr;  // R*R + R
+    SolverState* st_w = nullptr;
+    SolverState* st_f = nullptr;
+    int* err = nullptr;
+    SliceDesc* slice_dev = nullptr;
+
+    // sparse-slice structures
+    unsigned long long* hkeys = nullptr;
+    int hlog2 = 0;
+    int32_t *counts = nullptr, *hot = nullptr, *hot_rows = nullptr;
+    int nhot = kMaxHot;
+
+    // staging of host slices
+    void* stage_idx = nullptr;
+    size_t stage_idx_bytes = 0;
+    void* stage_vals = nullptr;
+    size_t stage_vals_bytes = 0;
+
+    // slice currently loaded
+    bool loaded = false;
+    int loaded_sparse = 0;
+    const void* loaded_user_idx = nullptr;
+    const void* loaded_user_vals = nullptr;
+    int64_t loaded_nnz = -1;
+    SliceDesc cur{};
+
+    int64_t t = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [dense, sparse]
+    int64_t graph_kernels[2] = {0, 0};
+};
+
+namespace {
+
+sgcp_status fail(sgcp_ctx* c, sgcp_status st, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->last_error = buf;
+    }
+    return st;
+}
+
+sgcp_status cuda_fail(sgcp_ctx* c, cudaError_t e, const char* what) {
+    if (c) {
+        c->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+        c->sticky = SGCP_ERR_CUDA;
+    }
+    return e == cudaErrorMemoryAllocation ? SGCP_ERR_OOM : SGCP_ERR_CUDA;
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+sgcp_status dalloc(sgcp_ctx* c, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        c->last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SGCP_ERR_OOM : SGCP_ERR_CUDA;
+    }
+    c->allocs.push_back(*p);
+    return SGCP_OK;
+}
+
+template <typename P>
+sgcp_status dalloc_t(sgcp_ctx* c, P** p, size_t bytes) {
+    void* q = nullptr;
+    sgcp_status st = dalloc(c, &q, bytes);
+    *p = (P*)q;
+    return st;
+}
+
+void dfree(sgcp_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i)
+        if (c->allocs[i] == p) {
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            break;
+        }
+    cudaFree(p);
+}
+
+int64_t omega_of(const sgcp_ctx* c) {
+    int64_t w = 1;
+    for (int k = 0; k < c->ndim; ++k) w *= c->dims[k];
+    return w;
+}
+
+void* offs(void* base, int64_t elems, size_t esz) { return (char*)base + (size_t)elems * esz; }
+
+uint32_t purpose_nz(int set) {
+    switch (set) {
+        case SGCP_SAMPLES_FACTOR_GRAD: return PUR_GRAD_NZ;
+        case SGCP_SAMPLES_FACTOR_OBJ: return PUR_OBJ_NZ;
+        case SGCP_SAMPLES_TEMPORAL_GRAD: return PUR_TGRAD_NZ;
+        default: return PUR_TOBJ_NZ;
+    }
+}
+
+uint32_t purpose_z(int set) { return purpose_nz(set) + 1; }
+
+// Load X: stage host data, ingest sparse slices when they changed, fill c->cur.
+sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_ingest) {
+    if (!X) return fail(c, SGCP_ERR_ARG, "slice is NULL");
+    const bool sparse = X->is_sparse != 0;
+    const int64_t omega = omega_of(c);
+    const int64_t nnz = sparse ? X->nnz : omega;
+    if (sparse) {
+        if (c->f64) return fail(c, SGCP_ERR_UNSUPPORTED, "sparse slices need a float context");
+        if (nnz < 0 || nnz > omega || nnz >= (int64_t)1 << 31)
+            return fail(c, SGCP_ERR_ARG, "sparse slice nnz %lld out of range", (long long)nnz);
+        if (nnz > 0 && (!X->idx || !X->vals)) return fail(c, SGCP_ERR_ARG, "sparse slice without idx/vals");
+    } else {
+        if (!X->vals) return fail(c, SGCP_ERR_ARG, "dense slice without vals");
+        if (c->ndim > 3) return fail(c, SGCP_ERR_UNSUPPORTED, "dense slices support ndim <= 3");
+    }
+    const void* idx_d = X->idx;
+    const void* vals_d = X->vals;
+    if (X->on_host) {
+        const size_t ib = sparse ? (size_t)nnz * c->ndim * sizeof(int32_t) : 0;
+        const size_t vb = (size_t)nnz * (sparse ? sizeof(float) : c->esz);
+        if (ib > c->stage_idx_bytes) {
+            dfree(c, c->stage_idx);
+            c->stage_idx = nullptr;
+            c->stage_idx_bytes = 0;
+            sgcp_status st = dalloc(c, &c->stage_idx, ib);
+            if (st) return st;
+            c->stage_idx_bytes = ib;
+        }
+        if (vb > c->stage_vals_bytes) {
+            dfree(c, c->stage_vals);
+            c->stage_vals = nullptr;
+            c->stage_vals_bytes = 0;
+            sgcp_status st = dalloc(c, &c->stage_vals, vb);
+            if (st) return st;
+            c->stage_vals_bytes = vb;
+        }
+        if (ib) CK(cudaMemcpyAsync(c->stage_idx, X->idx, ib, cudaMemcpyHostToDevice, c->stream), "copy slice idx");
+        if (vb) CK(cudaMemcpyAsync(c->stage_vals, X->vals, vb, cudaMemcpyHostToDevice, c->stream), "copy slice vals");
+        idx_d = c->stage_idx;
+        vals_d = c->stage_vals;
+        force_ingest = true;
+    }
+    c->cur.idx = (const int32_t*)idx_d;
+    c->cur.vals = vals_d;
+    c->cur.nnz = nnz;
+    c->cur.t = t;
+    const bool same = c->loaded && c->loaded_sparse == (int)sparse && c->loaded_user_idx == X->idx &&
+                      c->loaded_user_vals == X->vals && c->loaded_nnz == nnz;
+    if (sparse && (force_ingest || !same)) {
+        int hl = 10;
+        while (((int64_t)1 << hl) < 2 * nnz) ++hl;
+        if (hl > c->hlog2) {
+            dfree(c, c->hkeys);
+            c->hkeys = nullptr;
+            sgcp_status st = dalloc_t(c, &c->hkeys, ((size_t)1 << hl) * sizeof(unsigned long long));
+            if (st) return st;
+            c->hlog2 = hl;
+        }
+        CK(cudaMemsetAsync(c->hkeys, 0xFF, ((size_t)1 << c->hlog2) * sizeof(unsigned long long), c->stream),
+           "clear hash");
+        CK(cudaMemsetAsync(c->counts, 0, (size_t)c->nrows * sizeof(int32_t), c->stream), "clear counts");
+        CK(cudaMemsetAsync(c->hot, 0xFF, (size_t)c->nrows * sizeof(int32_t), c->stream), "clear hot");
+        CK(cudaMemsetAsync(c->hot_rows, 0xFF, (size_t)c->ndim * kMaxHot * sizeof(int32_t), c->stream),
+           "clear hot rows");
+        IngestArgs ia{};
+        ia.slice = c->cur;
+        ia.ndim = c->ndim;
+        for (int k = 0; k < 4; ++k) {
+            ia.dims[k] = c->dims[k];
+            ia.row_off[k] = c->row_off[k];
+        }
+        ia.hkeys = c->hkeys;
+        ia.hlog2 = c->hlog2;
+        ia.counts = c->counts;
+        ia.hot = c->hot;
+        ia.hot_rows = c->hot_rows;
+        ia.sub_stride = nnz > 131072 ? nnz / 131072 : 1;
+        ia.nhot = c->nhot;
+        ia.err = c->err;
+        if (nnz > 0) CK(launch_ingest(ia, nnz, c->stream, &c->launches), "ingest");
+    }
+    c->loaded = true;
+    c->loaded_sparse = (int)sparse;
+    c->loaded_user_idx = X->idx;
+    c->loaded_user_vals = X->vals;
+    c->loaded_nnz = nnz;
+    return SGCP_OK;
+}
+
+SparseGradArgs sparse_args(sgcp_ctx* c, const SliceDesc* slice_dev, int set, uint32_t draw, int want,
+                           const void* s, const void* const* A, void* const* G, void* gs, double* f, int loss,
+                           const void* y_scale, const int32_t* skip) {
+    SparseGradArgs a{};
+    a.slice = slice_dev;
+    a.inline_slice = c->cur;
+    a.ndim = c->ndim;
+    a.R = c->R;
+    for (int k = 0; k < 4; ++k) a.dims[k] = c->dims[k];
+    for (int k = 0; k < c->ndim; ++k) {
+        a.A[k] = (const float*)A[k];
+        a.G[k] = G ? (float*)G[k] : nullptr;
+        a.hot[k] = c->hot + c->row_off[k];
+    }
+    a.s = (const float*)s;
+    a.gs = (float*)gs;
+    a.f = f;
+    a.hkeys = c->hkeys;
+    a.hlog2 = c->hlog2;
+    a.hot_rows = c->hot_rows;
+    a.nhot = c->nhot;
+    a.key0 = (uint32_t)(c->P.seed & 0xFFFFFFFFu);
+    a.key1 = (uint32_t)(c->P.seed >> 32);
+    a.draw = draw;
+    a.pur_nz = purpose_nz(set);
+    a.pur_z = purpose_z(set);
+    const bool obj = (set == SGCP_SAMPLES_FACTOR_OBJ || set == SGCP_SAMPLES_TEMPORAL_OBJ);
+    a.p = obj ? c->P.p_obj : c->P.p;
+    a.q = obj ? c->P.q_obj : c->P.q;
+    a.all_nnz = 0;
+    a.cap = c->P.zero_attempt_cap;
+    a.want = want;
+    a.loss = loss;
+    a.eps = (float)c->P.log_eps;
+    a.y_scale = (const float*)y_scale;
+    a.err = c->err;
+    a.skip = skip;
+    return a;
+}
+
+template <typename T>
+DenseGradArgs<T> dense_args(sgcp_ctx* c, const SliceDesc* slice_dev, int want, const void* s, const void* const* A,
+                            void* const* G, void* gs, double* f, int loss, const void* y_scale, const int32_t* skip) {
+    DenseGradArgs<T> a{};
+    a.slice = slice_dev;
+    a.inline_slice = c->cur;
+    a.ndim = c->ndim;
+    a.R = c->R;
+    for (int k = 0; k < 3; ++k) a.dims[k] = c->dims[k];
+    for (int k = 0; k < c->ndim; ++k) {
+        a.A[k] = (const T*)A[k];
+        a.G[k] = G ? (T*)G[k] : nullptr;
+    }
+    a.s = (const T*)s;
+    a.gs = (T*)gs;
+    a.f = f;
+    a.want = want;
+    a.loss = loss;
+    a.eps = (T)c->P.log_eps;
+    a.y_scale = (const T*)y_scale;
+    a.skip = skip;
+    return a;
+}
+
+// Gradient launch used by both the direct entry point and the step graph.
+sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_dev, int set, uint32_t draw, int want,
+                             const void* s, const void* const* A, void* const* G, void* gs, double* f, int loss,
+                             const void* y_scale, const int32_t* skip, int all_nnz = 0) {
+    if (sparse) {
+        SparseGradArgs a = sparse_args(c, slice_dev, set, draw, want, s, A, G, gs, f, loss, y_scale, skip);
+        a.all_nnz = all_nnz;
+        int64_t total;
+        if (all_nnz) total = (int64_t)1 << 40;   // grid-stride over nnz (unknown when captured): full grid
+        else {
+            const bool obj = (set == SGCP_SAMPLES_FACTOR_OBJ || set == SGCP_SAMPLES_TEMPORAL_OBJ);
+            total = obj ? c->P.p_obj + c->P.q_obj : c->P.p + c->P.q;
+        }
+        CK(launch_sparse_grad(a, total, c->stream, &c->launches), "sparse gradient");
+    } else if (c->f64) {
+        DenseGradArgs<double> a = dense_args<double>(c, slice_dev, want, s, A, G, gs, f, loss, y_scale, skip);
+        CK(launch_dense_grad<double>(a, c->stream, &c->launches), "dense gradient");
+    } else {
+        DenseGradArgs<float> a = dense_args<float>(c, slice_dev, want, s, A, G, gs, f, loss, y_scale, skip);
+        CK(launch_dense_grad<float>(a, c->stream, &c->launches), "dense gradient");
+    }
+    return SGCP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One OnlineGCP step (Alg. 1 body minus the host-side reservoir choice),
+// enqueued on c->stream; captured into a graph by build_graph.
+// ---------------------------------------------------------------------------
+template <typename T>
+sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
+    const int R = c->R, d = c->ndim;
+    const sgcp_params& P = c->P;
+    const size_t esz = sizeof(T);
+    const void* Aptr[4];
+    void* Gptr[4];
+    for (int k = 0; k < d; ++k) {
+        Aptr[k] = offs(c->A, c->row_off[k] * R, esz);
+        Gptr[k] = offs(c->G, c->row_off[k] * R, esz);
+    }
+    const size_t gram_mode_bytes = (size_t)d * R * R * sizeof(double);
+    GramArgs<T> ga{};
+    ga.ndim = d;
+    ga.R = R;
+    for (int k = 0; k < 4; ++k) {
+        ga.dims[k] = c->dims[k];
+        ga.row_off[k] = c->row_off[k];
+    }
+    ga.A = (const T*)c->A;
+    ga.Abar = (const T*)c->Abar;
+    ga.out = c->grams;
+    const int loss = P.loss;
+
+    CK(launch_history_SH<T>(R, (const T*)c->s_hist, c->h_dev, c->hist_len_dev, c->slice_dev, P.w, P.theta, c->SH,
+                            c->stream, &c->launches),
+       "S_H");
+
+    // ---------------- temporal weights (Alg. 3, or the least-squares solve) ----------------
+    if (P.temporal == SGCP_TEMPORAL_LSQ) {
+        CK(cudaMemsetAsync(c->grams, 0, gram_mode_bytes, c->stream), "clear grams");
+        ga.npairs = 1;
+        ga.sel_u[0] = SEL_A;
+        ga.sel_v[0] = SEL_A;
+        ga.skip = nullptr;
+        CK(launch_gram<T>(ga, c->nrows, c->stream, &c->launches), "gram");
+        CK(cudaMemsetAsync(c->gs, 0, R * esz, c->stream), "clear gs");
+        sgcp_status st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD, 0, SGCP_WANT_TEMPORAL,
+                                          c->s, Aptr, nullptr, c->gs, nullptr, LOSS_IDENTITY_X, nullptr, nullptr, 1);
+        if (st) return st;
+        CK(launch_lsq_solve<T>(d, R, c->grams, (const T*)c->gs, P.mu, c->lower, (T*)c->s, c->lsq_work, c->err,
+                               c->stream, &c->launches),
+           "lsq solve");
+    } else {
+        SolverState* sw = c->st_w;
+        const int32_t* skip = &sw->done;
+        CK(launch_adam_reset<T>(R, (const T*)c->s, (T*)c->s_u, (T*)c->s_v, (T*)c->s_ao, (T*)c->s_uo, (T*)c->s_vo, 1,
+                                (T*)c->s, c->stream, &c->launches),
+           "adam init");
+        CK(launch_solver_init(sw, P.alpha_w, 1, c->stream, &c->launches), "solver init");
+        CK(cudaMemsetAsync(c->gs, 0, R * esz, c->stream), "clear gs");
+        sgcp_status st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s,
+                                          Aptr, nullptr, nullptr, &sw->F_new, loss, nullptr, nullptr);
+        if (st) return st;
+        CK(launch_obj_finish_w<T>(sw, (const T*)c->s, R, P.mu, 1, c->err, nullptr, c->stream, &c->launches), "obj");
+        for (int e = 0; e < P.kappa_w; ++e) {
+            CK(launch_epoch_begin(sw, P.tol_w, nullptr, c->stream, &c->launches), "epoch begin");
+            for (int it = 0; it < P.tau_w; ++it) {
+                st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD, (uint32_t)(e * P.tau_w + it),
+                                      SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs, nullptr, loss, nullptr, skip);
+                if (st) return st;
+                CK(launch_temporal_adam<T>(R, (T*)c->s, (T*)c->gs, (T*)c->s_u, (T*)c->s_v, P.mu, P.beta1, P.beta2,
+                                           P.adam_eps, c->lower, sw, skip, c->stream, &c->launches),
+                   "temporal adam");
+            }
+            st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s, Aptr,
+                                  nullptr, nullptr, &sw->F_new, loss, nullptr, skip);
+            if (st) return st;
+            CK(launch_obj_finish_w<T>(sw, (const T*)c->s, R, P.mu, 0, c->err, skip, c->stream, &c->launches), "obj");
+            CK(launch_epoch_end<T>(sw, R, (T*)c->s, (T*)c->s_u, (T*)c->s_v, (T*)c->s_ao, (T*)c->s_uo, (T*)c->s_vo,
+                                   P.tau_w, P.alpha_decay, nullptr, c->stream, &c->launches),
+               "epoch end");
+        }
+    }
+
+    // ---------------- factor matrices (Alg. 4) ----------------
+    SolverState* sf = c->st_f;
+    const int32_t* skip = &sf->done;
+    const bool hist_possible = P.H > 0;
+    CK(launch_solver_init(sf, P.alpha_f, 0, c->stream, &c->launches), "solver init");
+    auto objective_f = [&](int set_cur, const int32_t* sk) -> sgcp_status {
+        sgcp_status st2 = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_OBJ, 0, SGCP_WANT_LOSS, c->s,
+                                           Aptr, nullptr, nullptr, &sf->F_new, loss, nullptr, sk);
+        if (st2) return st2;
+        CK(cudaMemsetAsync(c->grams, 0, 6 * gram_mode_bytes, c->stream), "clear grams");
+        GramArgs<T> g6 = ga;
+        g6.npairs = 6;
+        const int su[6] = {SEL_A, SEL_ABAR, SEL_ABAR, SEL_D, SEL_D, SEL_ABAR};
+        const int sv[6] = {SEL_A, SEL_ABAR, SEL_A, SEL_D, SEL_A, SEL_D};
+        for (int i = 0; i < 6; ++i) {
+            g6.sel_u[i] = su[i];
+            g6.sel_v[i] = sv[i];
+        }
+        g6.skip = sk;
+        CK(launch_gram<T>(g6, c->nrows, c->stream, &c->launches), "gram6");
+        CK(launch_obj_finish_f(sf, d, R, c->grams, c->SH, c->hist_len_dev, P.lambda, set_cur, c->err, sk, c->stream,
+                               &c->launches),
+           "obj f");
+        return SGCP_OK;
+    };
+    sgcp_status st = objective_f(1, nullptr);
+    if (st) return st;
+    FactorUpdateArgs<T> fu{};
+    fu.ndim = d;
+    fu.R = R;
+    fu.nrows = c->nrows;
+    for (int k = 0; k < 4; ++k) fu.row_off[k] = c->row_off[k];
+    fu.A = (T*)c->A;
+    fu.Abar = (const T*)c->Abar;
+    fu.G = (T*)c->G;
+    fu.u = (T*)c->u;
+    fu.v = (T*)c->v;
+    fu.B = hist_possible ? c->Bc : nullptr;
+    fu.C = hist_possible ? c->Cc : nullptr;
+    fu.hist_len = c->hist_len_dev;
+    fu.lam = P.lambda;
+    fu.beta1 = P.beta1;
+    fu.beta2 = P.beta2;
+    fu.eps = P.adam_eps;
+    fu.lower = c->lower;
+    fu.st = sf;
+    fu.skip = skip;
+    for (int e = 0; e < P.kappa_f; ++e) {
+        CK(launch_epoch_begin(sf, P.tol_f, nullptr, c->stream, &c->launches), "epoch begin");
+        for (int it = 0; it < P.tau_f; ++it) {
+            st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
+                                  SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip);
+            if (st) return st;
+            if (hist_possible) {
+                CK(cudaMemsetAsync(c->grams, 0, 2 * gram_mode_bytes, c->stream), "clear grams");
+                GramArgs<T> g2 = ga;
+                g2.npairs = 2;
+                g2.sel_u[0] = SEL_A;
+                g2.sel_v[0] = SEL_A;
+                g2.sel_u[1] = SEL_D;
+                g2.sel_v[1] = SEL_A;
+                g2.skip = skip;
+                CK(launch_gram<T>(g2, c->nrows, c->stream, &c->launches), "gram2");
+                CK(launch_hist_coeffs(d, R, c->grams, c->SH, c->hist_len_dev, c->Bc, c->Cc, skip, c->stream,
+                                      &c->launches),
+                   "hist coeffs");
+            }
+            CK(launch_factor_update<T>(fu, c->stream, &c->launches), "factor update");
+        }
+        st = objective_f(0, skip);
+        if (st) return st;
+        CK(launch_epoch_end<T>(sf, c->N, (T*)c->A, (T*)c->u, (T*)c->v, (T*)c->a_o, (T*)c->u_o, (T*)c->v_o, P.tau_f,
+                               P.alpha_decay, nullptr, c->stream, &c->launches),
+           "epoch end");
+    }
+    CK(cudaMemcpyAsync(c->Abar, c->A, (size_t)c->N * esz, cudaMemcpyDeviceToDevice, c->stream), "Abar <- A");
+    return SGCP_OK;
+}
+
+sgcp_status build_graph(sgcp_ctx* c, bool sparse) {
+    const int gi = sparse ? 1 : 0;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    const int64_t before = c->launches;
+    sgcp_status st = c->f64 ? enqueue_step<double>(c, sparse) : enqueue_step<float>(c, sparse);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->launches = before;
+    if (st != SGCP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) cudaGraphGetNodes(g, nodes.data(), &n);
+    int64_t kernels = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    e = cudaGraphInstantiate(&c->graph[gi], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "instantiate graph");
+    c->graph_kernels[gi] = kernels;
+    return SGCP_OK;
+}
+
+uint32_t reservoir_index(uint64_t seed, int64_t t) {
+    uint32_t ctr[4] = {0u, 0u, 0u, counter_word3(PUR_RESERVOIR, t)};
+    philox4x32_10(ctr, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    return 1u + bounded_u32(ctr[0], (uint32_t)t);
+}
+
+sgcp_status check_ready(sgcp_ctx* c) {
+    if (!c) return SGCP_ERR_ARG;
+    if (c->sticky != SGCP_OK) return SGCP_ERR_STATE;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return SGCP_OK;
+}
+
+sgcp_status status_from_err(int bits) {
+    if (bits & (ERRB_COORD | ERRB_DUP)) return SGCP_ERR_DATA;
+    if (bits & ERRB_SAMPLING) return SGCP_ERR_SAMPLING_LIMIT;
+    if (bits & (ERRB_NUMERIC | ERRB_SOLVE)) return SGCP_ERR_NUMERIC;
+    if (bits) return SGCP_ERR_STATE;
+    return SGCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sgcp_version(void) { return "sgcp 0.1.0 (sm_103a)"; }
+
+const char* sgcp_status_string(sgcp_status s) {
+    switch (s) {
+        case SGCP_OK: return "SGCP_OK";
+        case SGCP_ERR_ARG: return "SGCP_ERR_ARG";
+        case SGCP_ERR_CUDA: return "SGCP_ERR_CUDA";
+        case SGCP_ERR_OOM: return "SGCP_ERR_OOM";
+        case SGCP_ERR_SAMPLING_LIMIT: return "SGCP_ERR_SAMPLING_LIMIT";
+        case SGCP_ERR_TIMEOUT: return "SGCP_ERR_TIMEOUT";
+        case SGCP_ERR_NUMERIC: return "SGCP_ERR_NUMERIC";
+        case SGCP_ERR_STATE: return "SGCP_ERR_STATE";
+        case SGCP_ERR_UNSUPPORTED: return "SGCP_ERR_UNSUPPORTED";
+        case SGCP_ERR_DATA: return "SGCP_ERR_DATA";
+    }
+    return "SGCP_ERR_UNKNOWN";
+}
+
+sgcp_status sgcp_params_default(sgcp_params* p) {
+    if (!p) return SGCP_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->ndim = 3;
+    p->rank = 8;
+    p->loss = SGCP_LOSS_GAUSSIAN;
+    p->precision = SGCP_PREC_F32;
+    p->lower_bound = std::nan("");
+    p->log_eps = 1e-10;
+    p->H = 0;
+    p->temporal = SGCP_TEMPORAL_ADAM;
+    p->w = 1.0;
+    p->theta = 1.0;
+    p->lambda = 0.0;
+    p->mu = 0.0;
+    p->tol_w = -INFINITY;
+    p->tol_f = -INFINITY;
+    p->kappa_w = 5;
+    p->kappa_f = 5;
+    p->tau_w = 100;
+    p->tau_f = 100;
+    p->alpha_w = 0.1;
+    p->alpha_f = 1e-3;
+    p->beta1 = 0.9;
+    p->beta2 = 0.999;
+    p->adam_eps = 1e-8;
+    p->alpha_decay = 0.1;
+    p->zero_attempt_cap = 64;
+    p->optimizer = SGCP_OPT_ADAM;
+    p->lbfgs_mem = 5;
+    p->lbfgs_iters = 10;
+    p->seed = 0;
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_factors, int32_t n_hist,
+                        const int64_t* hist_t, const void* hist_s, int64_t t0, void* cuda_stream, sgcp_ctx** out) {
+    if (!params || !init_factors || !out) return SGCP_ERR_ARG;
+    *out = nullptr;
+    const sgcp_params& P = *params;
+    if (P.ndim < 2 || P.ndim > 4) return SGCP_ERR_UNSUPPORTED;
+    if (P.rank < 4 || P.rank > 128 || P.rank % 4 != 0) return SGCP_ERR_UNSUPPORTED;
+    if (P.loss < 0 || P.loss > 3) return SGCP_ERR_ARG;
+    if (P.precision < 0 || P.precision > 3) return SGCP_ERR_ARG;
+    if (P.precision == SGCP_PREC_BF16_MTTKRP || P.precision == SGCP_PREC_F16_MTTKRP) return SGCP_ERR_UNSUPPORTED;
+    if (P.optimizer != SGCP_OPT_ADAM) return SGCP_ERR_UNSUPPORTED;
+    if (P.temporal == SGCP_TEMPORAL_LSQ && P.loss != SGCP_LOSS_GAUSSIAN) return SGCP_ERR_ARG;
+    if (P.H < 0 || n_hist < 0 || n_hist > P.H || (n_hist > 0 && (!hist_t || !hist_s))) return SGCP_ERR_ARG;
+    if (P.kappa_w < 0 || P.kappa_f < 0 || P.tau_w < 0 || P.tau_f < 0 || P.kappa_w > 32 || P.kappa_f > 32)
+        return SGCP_ERR_ARG;
+    if (P.p < 0 || P.q < 0 || P.p_obj < 0 || P.q_obj < 0 || P.p + P.q >= ((int64_t)1 << 32) ||
+        P.p_obj + P.q_obj >= ((int64_t)1 << 32) || P.zero_attempt_cap < 1)
+        return SGCP_ERR_ARG;
+    double omega = 1.0;
+    for (int k = 0; k < P.ndim; ++k) {
+        if (P.dims[k] < 1 || P.dims[k] > 0x7fffffff) return SGCP_ERR_ARG;
+        omega *= (double)P.dims[k];
+    }
+    if (omega > 9.0e18) return SGCP_ERR_UNSUPPORTED;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SGCP_ERR_CUDA;   // no usable CUDA device
+    }
+    sgcp_ctx* c = new (std::nothrow) sgcp_ctx();
+    if (!c) return SGCP_ERR_OOM;
+    c->P = P;
+    c->ndim = P.ndim;
+    c->R = P.rank;
+    c->f64 = P.precision == SGCP_PREC_F64;
+    c->esz = c->f64 ? 8 : 4;
+    if (std::isnan(P.lower_bound))
+        c->lower = (P.loss == SGCP_LOSS_POISSON || P.loss == SGCP_LOSS_BERNOULLI_ODDS) ? 0.0 : -INFINITY;
+    else
+        c->lower = P.lower_bound;
+    for (int k = 0; k < c->ndim; ++k) {
+        c->dims[k] = P.dims[k];
+        c->row_off[k] = c->nrows;
+        c->nrows += P.dims[k];
+    }
+    for (int k = c->ndim; k < 4; ++k) c->row_off[k] = c->nrows;
+    c->N = c->nrows * c->R;
+    c->device = dev;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return SGCP_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    auto bail = [&](sgcp_status st) {
+        sgcp_destroy(c);
+        return st;
+    };
+    const size_t nb = (size_t)c->N * c->esz, rb = (size_t)c->R * c->esz;
+    void** vecN[] = {&c->A, &c->Abar, &c->G, &c->u, &c->v, &c->u_o, &c->v_o, &c->a_o};
+    for (void** p : vecN)
+        if (sgcp_status st = dalloc(c, p, nb)) return bail(st);
+    void** vecR[] = {&c->s, &c->s_u, &c->s_v, &c->s_uo, &c->s_vo, &c->s_ao, &c->gs};
+    for (void** p : vecR)
+        if (sgcp_status st = dalloc(c, p, rb)) return bail(st);
+    const int Hs = P.H > 0 ? P.H : 1;
+    const size_t RR = (size_t)c->R * c->R;
+    sgcp_status st = SGCP_OK;
+    if ((st = dalloc(c, &c->s_hist, (size_t)Hs * rb)) || (st = dalloc_t(c, &c->h_dev, Hs * sizeof(int64_t))) ||
+        (st = dalloc_t(c, &c->hist_len_dev, sizeof(int32_t))) || (st = dalloc_t(c, &c->SH, RR * sizeof(double))) ||
+        (st = dalloc_t(c, &c->grams, 6 * c->ndim * RR * sizeof(double))) ||
+        (st = dalloc_t(c, &c->Bc, c->ndim * RR * sizeof(float))) ||
+        (st = dalloc_t(c, &c->Cc, c->ndim * RR * sizeof(float))) ||
+        (st = dalloc_t(c, &c->lsq_work, (RR + c->R) * sizeof(double))) ||
+        (st = dalloc_t(c, &c->st_w, sizeof(SolverState))) || (st = dalloc_t(c, &c->st_f, sizeof(SolverState))) ||
+        (st = dalloc_t(c, &c->err, sizeof(int))) || (st = dalloc_t(c, &c->slice_dev, sizeof(SliceDesc))) ||
+        (st = dalloc_t(c, &c->counts, c->nrows * sizeof(int32_t))) ||
+        (st = dalloc_t(c, &c->hot, c->nrows * sizeof(int32_t))) ||
+        (st = dalloc_t(c, &c->hot_rows, c->ndim * kMaxHot * sizeof(int32_t))))
+        return bail(st);
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < c->ndim && e == cudaSuccess; ++k) {
+        if (!init_factors[k]) return bail(SGCP_ERR_ARG);
+        e = cudaMemcpyAsync(offs(c->A, c->row_off[k] * c->R, c->esz), init_factors[k],
+                            (size_t)c->dims[k] * c->R * c->esz, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->Abar, c->A, nb, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->a_o, c->A, nb, cudaMemcpyDeviceToDevice, s);
+    void* zeroN[] = {c->G, c->u, c->v, c->u_o, c->v_o};
+    for (void* p : zeroN)
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, nb, s);
+    void* zeroR[] = {c->s, c->s_u, c->s_v, c->s_uo, c->s_vo, c->s_ao, c->gs};
+    for (void* p : zeroR)
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, rb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->s_hist, 0, (size_t)Hs * rb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->SH, 0, RR * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->st_w, 0, sizeof(SolverState), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->st_f, 0, sizeof(SolverState), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->Bc, 0, c->ndim * RR * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->Cc, 0, c->ndim * RR * sizeof(float), s);
+    std::vector<int64_t> hv(Hs, 0);
+    for (int i = 0; i < n_hist; ++i) {
+        if (hist_t[i] > t0) return bail(SGCP_ERR_ARG);
+        hv[i] = hist_t[i];
+        c->hist_t.push_back(hist_t[i]);
+    }
+    if (e == cudaSuccess && n_hist > 0)
+        e = cudaMemcpyAsync(c->s_hist, hist_s, (size_t)n_hist * rb, cudaMemcpyDeviceToDevice, s);
+    // host -> device copies of small init data, then wait (the host vectors die here)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_dev, hv.data(), Hs * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    int32_t nh = n_hist;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hist_len_dev, &nh, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "create");
+        return bail(e == cudaErrorMemoryAllocation ? SGCP_ERR_OOM : SGCP_ERR_CUDA);
+    }
+    c->t = t0;
+    *out = c;
+    return SGCP_OK;
+}
+
+void sgcp_destroy(sgcp_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* sgcp_last_error(const sgcp_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+sgcp_status sgcp_ingest(sgcp_ctx* c, const sgcp_slice* X) {
+    if (sgcp_status st = check_ready(c)) return st;
+    return load_slice(c, X, c->t + 1, true);
+}
+
+sgcp_status sgcp_gradient(sgcp_ctx* c, const sgcp_slice* X, const void* s, const void* const* A,
+                          const sgcp_grad_opts* opts, void* const* G_out, void* gs_out, double* f_out) {
+    if (sgcp_status st = check_ready(c)) return st;
+    if (!opts || !s || !A) return fail(c, SGCP_ERR_ARG, "gradient: NULL argument");
+    const int want = opts->want;
+    if (want & ~7) return fail(c, SGCP_ERR_ARG, "gradient: bad want bits");
+    if ((want & SGCP_WANT_FACTORS) && !G_out) return fail(c, SGCP_ERR_ARG, "gradient: G_out is NULL");
+    if ((want & SGCP_WANT_TEMPORAL) && !gs_out) return fail(c, SGCP_ERR_ARG, "gradient: gs_out is NULL");
+    if ((want & SGCP_WANT_LOSS) && !f_out) return fail(c, SGCP_ERR_ARG, "gradient: f_out is NULL");
+    if (opts->sample_set < 0 || opts->sample_set > 3) return fail(c, SGCP_ERR_ARG, "gradient: bad sample set");
+    for (int k = 0; k < c->ndim; ++k) {
+        if (!A[k]) return fail(c, SGCP_ERR_ARG, "gradient: A[%d] is NULL", k);
+        if ((want & SGCP_WANT_FACTORS) && !G_out[k]) return fail(c, SGCP_ERR_ARG, "gradient: G_out[%d] is NULL", k);
+    }
+    if (sgcp_status st = load_slice(c, X, opts->t, false)) return st;
+    if (!opts->accumulate) {
+        if (want & SGCP_WANT_FACTORS)
+            for (int k = 0; k < c->ndim; ++k)
+                CK(cudaMemsetAsync(G_out[k], 0, (size_t)c->dims[k] * c->R * c->esz, c->stream), "clear G");
+        if (want & SGCP_WANT_TEMPORAL) CK(cudaMemsetAsync(gs_out, 0, (size_t)c->R * c->esz, c->stream), "clear gs");
+        if (want & SGCP_WANT_LOSS) CK(cudaMemsetAsync(f_out, 0, sizeof(double), c->stream), "clear f");
+    }
+    if (want == 0) return SGCP_OK;
+    return enqueue_gradient(c, X->is_sparse != 0, nullptr, opts->sample_set, opts->draw, want, s, A, G_out, gs_out,
+                            f_out, c->P.loss, opts->y_scale, nullptr);
+}
+
+sgcp_status sgcp_sample_coords(sgcp_ctx* c, const sgcp_slice* X, int32_t set, int64_t t, uint32_t draw,
+                               int32_t* coords_out, int32_t* attempt_out) {
+    if (sgcp_status st = check_ready(c)) return st;
+    if (!X || !X->is_sparse || !coords_out || set < 0 || set > 3)
+        return fail(c, SGCP_ERR_ARG, "sample_coords: bad argument");
+    if (sgcp_status st = load_slice(c, X, t, false)) return st;
+    const void* Adummy[4] = {c->A, c->A, c->A, c->A};
+    SparseGradArgs a = sparse_args(c, nullptr, set, draw, 0, c->s, Adummy, nullptr, nullptr, nullptr, c->P.loss,
+                                   nullptr, nullptr);
+    a.coords_out = coords_out;
+    a.attempt_out = attempt_out;
+    const bool obj = (set == SGCP_SAMPLES_FACTOR_OBJ || set == SGCP_SAMPLES_TEMPORAL_OBJ);
+    const int64_t total = obj ? c->P.p_obj + c->P.q_obj : c->P.p + c->P.q;
+    CK(launch_sample_coords(a, total, c->stream, &c->launches), "sample coords");
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
+    if (sgcp_status st = check_ready(c)) return st;
+    if (!X) return fail(c, SGCP_ERR_ARG, "step: slice is NULL");
+    const int64_t t = c->t + 1;
+    const bool sparse = X->is_sparse != 0;
+    if (sparse && (c->P.p + c->P.q == 0 || c->P.p_obj + c->P.q_obj == 0) && c->P.temporal != SGCP_TEMPORAL_LSQ)
+        return fail(c, SGCP_ERR_ARG, "step: sparse slices need p + q > 0 and p_obj + q_obj > 0");
+    if (sgcp_status st = load_slice(c, X, t, false)) return st;
+    CK(launch_write_desc(c->slice_dev, c->cur, c->stream, &c->launches), "slice descriptor");
+    const int gi = sparse ? 1 : 0;
+    if (!c->graph[gi])
+        if (sgcp_status st = build_graph(c, sparse)) return st;
+    CK(cudaGraphLaunch(c->graph[gi], c->stream), "graph launch");
+    c->launches += c->graph_kernels[gi];
+    // reservoir update of the history window (Alg. 1), decided on the host from t alone
+    if (c->P.H > 0) {
+        int slot = -1;
+        int len = (int)c->hist_t.size();
+        if (len < c->P.H) {
+            slot = len;
+            c->hist_t.push_back(t);
+            len += 1;
+        } else {
+            const uint32_t j = reservoir_index(c->P.seed, t);
+            if ((int64_t)j <= c->P.H) {
+                slot = (int)j - 1;
+                c->hist_t[slot] = t;
+            }
+        }
+        if (slot >= 0) {
+            cudaError_t e = c->f64 ? launch_hist_update<double>(c->R, (double*)c->s_hist, c->h_dev, c->hist_len_dev,
+                                                                 slot, t, len, (const double*)c->s, c->stream,
+                                                                 &c->launches)
+                                   : launch_hist_update<float>(c->R, (float*)c->s_hist, c->h_dev, c->hist_len_dev,
+                                                               slot, t, len, (const float*)c->s, c->stream,
+                                                               &c->launches);
+            if (e != cudaSuccess) return cuda_fail(c, e, "history update");
+        }
+    }
+    c->t = t;
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_factors(sgcp_ctx* c, void* const* A_out, void* s_out, int64_t* t_out) {
+    if (!c) return SGCP_ERR_ARG;
+    if (A_out)
+        for (int k = 0; k < c->ndim; ++k) {
+            if (!A_out[k]) continue;
+            CK(cudaMemcpyAsync(A_out[k], offs(c->A, c->row_off[k] * c->R, c->esz), (size_t)c->dims[k] * c->R * c->esz,
+                               cudaMemcpyDeviceToDevice, c->stream),
+               "copy factors");
+        }
+    if (s_out) CK(cudaMemcpyAsync(s_out, c->s, (size_t)c->R * c->esz, cudaMemcpyDeviceToDevice, c->stream), "copy s");
+    if (t_out) *t_out = c->t;
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_history(sgcp_ctx* c, int64_t* h_out, void* s_out, int32_t* n_out) {
+    if (!c) return SGCP_ERR_ARG;
+    const int n = (int)c->hist_t.size();
+    if (n_out) *n_out = n;
+    if (h_out)
+        for (int i = 0; i < n; ++i) h_out[i] = c->hist_t[i];
+    if (s_out && n)
+        CK(cudaMemcpyAsync(s_out, c->s_hist, (size_t)n * c->R * c->esz, cudaMemcpyDeviceToDevice, c->stream),
+           "copy history");
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_check(sgcp_ctx* c) {
+    if (!c) return SGCP_ERR_ARG;
+    if (c->sticky != SGCP_OK) return SGCP_ERR_STATE;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    int bits = 0;
+    e = cudaMemcpy(&bits, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read error word");
+    if (bits) {
+        c->sticky = status_from_err(bits);
+        char buf[128];
+        snprintf(buf, sizeof(buf), "device error bits 0x%x", bits);
+        c->last_error = buf;
+        return c->sticky;
+    }
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_stats(sgcp_ctx* c, sgcp_stats_t* out) {
+    if (!c || !out) return SGCP_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    sgcp_status st = sgcp_check(c);
+    SolverState w{}, f{};
+    int bits = 0;
+    cudaMemcpy(&w, c->st_w, sizeof(w), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&f, c->st_f, sizeof(f), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&bits, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+    out->t = c->t;
+    out->iter = f.i;
+    out->F_w = w.F_cur;
+    out->F_f = f.F_cur;
+    out->epochs_w = w.epoch;
+    out->epochs_f = f.epoch;
+    out->accept_w = w.accept;
+    out->accept_f = f.accept;
+    out->alpha_w = w.alpha;
+    out->alpha_f = f.alpha;
+    out->hist_len = (int32_t)c->hist_t.size();
+    out->error_bits = bits;
+    out->kernels_launched = c->launches;
+    return st;
+}
+
+// Checkpoint layout: header, then Abar, s, history weights, u, v (element type T).
+struct CkptHeader {
+    uint64_t magic;
+    int32_t ndim, R, H, hist_len, esz, pad;
+    int64_t dims[4];
+    int64_t t;
+    int64_t iter;
+    int64_t hist_t[1];   // followed by H - 1 more
+};
+
+static size_t ckpt_size(const sgcp_ctx* c) {
+    const int Hs = c->P.H > 0 ? c->P.H : 1;
+    return sizeof(CkptHeader) + (size_t)(Hs - 1) * sizeof(int64_t) +
+           ((size_t)3 * c->N + c->R + (size_t)Hs * c->R) * c->esz;
+}
+
+sgcp_status sgcp_state_size(const sgcp_ctx* c, size_t* size) {
+    if (!c || !size) return SGCP_ERR_ARG;
+    *size = ckpt_size(c);
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_state_export(sgcp_ctx* c, void* buf, size_t size) {
+    if (!c || !buf) return SGCP_ERR_ARG;
+    if (size < ckpt_size(c)) return fail(c, SGCP_ERR_ARG, "state_export: buffer too small");
+    if (sgcp_status st = sgcp_check(c)) return st;
+    const int Hs = c->P.H > 0 ? c->P.H : 1;
+    CkptHeader* h = (CkptHeader*)buf;
+    h->magic = 0x5347435053544154ull;
+    h->ndim = c->ndim;
+    h->R = c->R;
+    h->H = c->P.H;
+    h->hist_len = (int32_t)c->hist_t.size();
+    h->esz = (int32_t)c->esz;
+    h->pad = 0;
+    for (int k = 0; k < 4; ++k) h->dims[k] = c->dims[k];
+    h->t = c->t;
+    SolverState f{};
+    CK(cudaMemcpy(&f, c->st_f, sizeof(f), cudaMemcpyDeviceToHost), "read state");
+    h->iter = f.i;
+    for (int i = 0; i < Hs; ++i) h->hist_t[i] = i < (int)c->hist_t.size() ? c->hist_t[i] : 0;
+    char* p = (char*)buf + sizeof(CkptHeader) + (size_t)(Hs - 1) * sizeof(int64_t);
+    const size_t nb = (size_t)c->N * c->esz;
+    CK(cudaMemcpy(p, c->Abar, nb, cudaMemcpyDeviceToHost), "export");
+    p += nb;
+    CK(cudaMemcpy(p, c->s, (size_t)c->R * c->esz, cudaMemcpyDeviceToHost), "export");
+    p += (size_t)c->R * c->esz;
+    CK(cudaMemcpy(p, c->s_hist, (size_t)Hs * c->R * c->esz, cudaMemcpyDeviceToHost), "export");
+    p += (size_t)Hs * c->R * c->esz;
+    CK(cudaMemcpy(p, c->u, nb, cudaMemcpyDeviceToHost), "export");
+    p += nb;
+    CK(cudaMemcpy(p, c->v, nb, cudaMemcpyDeviceToHost), "export");
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_state_import(sgcp_ctx* c, const void* buf, size_t size) {
+    if (!c || !buf) return SGCP_ERR_ARG;
+    if (sgcp_status st = check_ready(c)) return st;
+    if (size < ckpt_size(c)) return fail(c, SGCP_ERR_ARG, "state_import: buffer too small");
+    const CkptHeader* h = (const CkptHeader*)buf;
+    if (h->magic != 0x5347435053544154ull || h->ndim != c->ndim || h->R != c->R || h->H != c->P.H ||
+        h->esz != (int32_t)c->esz)
+        return fail(c, SGCP_ERR_ARG, "state_import: checkpoint does not match this context");
+    for (int k = 0; k < c->ndim; ++k)
+        if (h->dims[k] != c->dims[k]) return fail(c, SGCP_ERR_ARG, "state_import: dims differ");
+    const int Hs = c->P.H > 0 ? c->P.H : 1;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    const char* p = (const char*)buf + sizeof(CkptHeader) + (size_t)(Hs - 1) * sizeof(int64_t);
+    const size_t nb = (size_t)c->N * c->esz;
+    CK(cudaMemcpy(c->Abar, p, nb, cudaMemcpyHostToDevice), "import");
+    CK(cudaMemcpy(c->A, p, nb, cudaMemcpyHostToDevice), "import");
+    CK(cudaMemcpy(c->a_o, p, nb, cudaMemcpyHostToDevice), "import");
+    p += nb;
+    CK(cudaMemcpy(c->s, p, (size_t)c->R * c->esz, cudaMemcpyHostToDevice), "import");
+    p += (size_t)c->R * c->esz;
+    CK(cudaMemcpy(c->s_hist, p, (size_t)Hs * c->R * c->esz, cudaMemcpyHostToDevice), "import");
+    p += (size_t)Hs * c->R * c->esz;
+    CK(cudaMemcpy(c->u, p, nb, cudaMemcpyHostToDevice), "import");
+    CK(cudaMemcpy(c->u_o, p, nb, cudaMemcpyHostToDevice), "import");
+    p += nb;
+    CK(cudaMemcpy(c->v, p, nb, cudaMemcpyHostToDevice), "import");
+    CK(cudaMemcpy(c->v_o, p, nb, cudaMemcpyHostToDevice), "import");
+    c->hist_t.clear();
+    std::vector<int64_t> hv(Hs, 0);
+    for (int i = 0; i < h->hist_len; ++i) {
+        c->hist_t.push_back(h->hist_t[i]);
+        hv[i] = h->hist_t[i];
+    }
+    CK(cudaMemcpy(c->h_dev, hv.data(), Hs * sizeof(int64_t), cudaMemcpyHostToDevice), "import");
+    int32_t nh = h->hist_len;
+    CK(cudaMemcpy(c->hist_len_dev, &nh, sizeof(int32_t), cudaMemcpyHostToDevice), "import");
+    SolverState f{};
+    CK(cudaMemcpy(&f, c->st_f, sizeof(f), cudaMemcpyDeviceToHost), "import");
+    f.i = (int32_t)h->iter;
+    CK(cudaMemcpy(c->st_f, &f, sizeof(f), cudaMemcpyHostToDevice), "import");
+    CK(cudaMemset(c->G, 0, nb), "import");
+    c->t = h->t;
+    c->loaded = false;
+    return SGCP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Shared device helpers of the streaming-GCP library: Philox4x32-10, bounded
+// integers, GCP losses, error bits and the device-resident step descriptor.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#define SGCP_FULL_MASK 0xffffffffu
+
+namespace sgcp {
+
+// ---------------------------------------------------------------------------
+// Device error word bits (latched with atomicOr, read by sgcp_check).
+// ---------------------------------------------------------------------------
+enum ErrBits : int {
+    ERRB_COORD = 1,      // a COO coordinate outside [0, I_k)
+    ERRB_DUP = 2,        // a COO coordinate repeated
+    ERRB_SAMPLING = 4,   // a zero-sample slot exhausted its attempts
+    ERRB_NUMERIC = 8,    // non-finite objective
+    ERRB_HASH = 16,      // nonzero hash table full (cannot happen at load <= 1/2)
+    ERRB_SOLVE = 32      // least-squares normal matrix not positive definite
+};
+
+// Purposes of the Philox counter (high byte of counter word 3).
+enum Purpose : uint32_t {
+    PUR_GRAD_NZ = 0, PUR_GRAD_Z = 1, PUR_OBJ_NZ = 2, PUR_OBJ_Z = 3, PUR_RESERVOIR = 4,
+    PUR_TGRAD_NZ = 5, PUR_TGRAD_Z = 6, PUR_TOBJ_NZ = 7, PUR_TOBJ_Z = 8
+};
+
+// Loss ids; LOSS_IDENTITY_X is internal: y = x, f = 0 (gives Z' vec(X) for the
+// least-squares temporal solve).
+enum LossId : int { LOSS_GAUSSIAN = 0, LOSS_POISSON = 1, LOSS_ODDS = 2, LOSS_LOGIT = 3, LOSS_IDENTITY_X = 4 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3): 10 rounds of
+//   (c0, c1, c2, c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+        const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+#else
+        const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// Multiply-shift bounded integer: floor(u * n / 2^32), n <= 2^32 - 1.
+__host__ __device__ inline uint32_t bounded_u32(uint32_t u, uint32_t n) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(u, n);
+#else
+    return (uint32_t)(((uint64_t)u * n) >> 32);
+#endif
+}
+
+__host__ __device__ inline uint32_t counter_word3(uint32_t purpose, int64_t t) {
+    return (purpose << 24) | ((uint32_t)t & 0xFFFFFFu);
+}
+
+// ---------------------------------------------------------------------------
+// GCP losses (Sec. 2.2): f(x, m) and y = df/dm.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void loss_eval(int loss, T x, T m, T eps, T& f, T& y) {
+    switch (loss) {
+        case LOSS_GAUSSIAN: {
+            const T d = m - x;
+            f = d * d;
+            y = T(2) * d;
+            break;
+        }
+        case LOSS_POISSON: {
+            const T me = m + eps;
+            f = m - x * log(me);
+            y = T(1) - x / me;
+            break;
+        }
+        case LOSS_ODDS: {
+            const T me = m + eps;
+            f = log(m + T(1)) - x * log(me);
+            y = T(1) / (m + T(1)) - x / me;
+            break;
+        }
+        case LOSS_LOGIT: {
+            f = (m > T(0) ? m : T(0)) + log1p(exp(-fabs(m))) - x * m;
+            y = T(1) / (T(1) + exp(-m)) - x;
+            break;
+        }
+        default: {  // LOSS_IDENTITY_X
+            f = T(0);
+            y = x;
+            break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Device-resident description of the slice currently loaded; kernels captured
+// in a CUDA graph read it so that one graph serves every slice.
+// ---------------------------------------------------------------------------
+struct SliceDesc {
+    const int32_t* idx;   // sparse: [nnz][ndim]
+    const void* vals;     // sparse: [nnz]; dense: full slice, C order
+    int64_t nnz;          // sparse: number of nonzeros; dense: prod I_k
+    int64_t t;            // time index of the slice
+};
+
+// Device-resident scalars of one solver (Alg. 2-4).
+struct SolverState {
+    double F_cur;      // current accepted estimate
+    double F_old;      // estimate at the start of the epoch
+    double F_new;      // accumulator of the estimate after the epoch
+    double alpha;      // learning rate
+    int32_t i;         // iteration counter for the bias correction
+    int32_t epoch;     // epochs run
+    int32_t done;      // set once the estimate is <= tol (Alg. 3/4 loop test)
+    uint32_t accept;   // bit e = epoch e accepted
+    uint32_t ticket;   // last-block counter of the row-update kernel
+    int32_t pad;
+};
+
+// Hot-row privatisation limits of the sparse kernel.
+constexpr int kMaxHot = 64;
+
+__device__ __forceinline__ void set_err(int* err, int bits) {
+    if (err) atomicOr(err, bits);
+}
+
+}  // namespace sgcp

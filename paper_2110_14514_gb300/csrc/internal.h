@@ -1,0 +1,185 @@
+// Internal launcher interfaces between the kernel files and the C ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sgcp {
+
+// Arguments of the fused sparse sample -> model -> y -> MTTKRP kernel.
+struct SparseGradArgs {
+    const SliceDesc* slice;          // device descriptor (graph path) or nullptr
+    SliceDesc inline_slice;          // used when slice == nullptr
+    int ndim;
+    int R;
+    int64_t dims[4];
+    const float* A[4];
+    const float* s;
+    float* G[4];                     // SGCP_WANT_FACTORS outputs (accumulated into)
+    float* gs;                       // SGCP_WANT_TEMPORAL output (accumulated into)
+    double* f;                       // SGCP_WANT_LOSS output (accumulated into)
+    const unsigned long long* hkeys; // nonzero-membership hash (open addressing)
+    int hlog2;                       // log2 of the table size
+    const int32_t* hot[4];           // per-mode row -> hot slot (-1 = not hot)
+    const int32_t* hot_rows;         // [ndim][kMaxHot] slot -> row
+    int nhot;                        // slots per mode (0 disables privatisation)
+    uint32_t key0, key1;             // Philox key
+    uint32_t draw;
+    uint32_t pur_nz, pur_z;
+    int64_t p, q;                    // requested sample counts
+    int all_nnz;                     // 1: visit every nonzero once with weight 1, no zeros
+    int cap;                         // attempts per zero slot
+    int want;                        // SGCP_WANT_* bits
+    int loss;
+    float eps;
+    const float* y_scale;            // device scalar or nullptr
+    int* err;                        // device error word
+    const int32_t* skip;             // device flag: nonzero -> kernel does nothing
+    int32_t* coords_out;             // sample-coordinate dump mode (nullptr otherwise)
+    int32_t* attempt_out;
+};
+
+// Arguments of the dense fused gradient kernels (3-way tiled and the 2-way path).
+template <typename T>
+struct DenseGradArgs {
+    const SliceDesc* slice;  // device descriptor or nullptr; vals = T[prod dims], C order
+    SliceDesc inline_slice;  // used when slice == nullptr
+    int ndim;
+    int R;
+    int64_t dims[3];
+    const T* A[3];
+    const T* s;
+    T* G[3];
+    T* gs;
+    double* f;
+    int want;
+    int loss;
+    T eps;
+    const T* y_scale;
+    const int32_t* skip;
+};
+
+struct IngestArgs {
+    SliceDesc slice;
+    int ndim;
+    int64_t dims[4];
+    unsigned long long* hkeys;
+    int hlog2;
+    int32_t* counts;        // concatenated per-mode row counts (sum I_k)
+    int32_t* hot;           // concatenated per-mode row -> slot (sum I_k), preset to -1
+    int32_t* hot_rows;      // [ndim][kMaxHot]
+    int64_t row_off[4];
+    int64_t sub_stride;     // histogram every sub_stride-th nonzero
+    int nhot;
+    int* err;
+};
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_ingest(const IngestArgs& a, int64_t nnz_host, cudaStream_t st, int64_t* launches);
+cudaError_t launch_sparse_grad(const SparseGradArgs& a, int64_t total_samples, cudaStream_t st, int64_t* launches);
+cudaError_t launch_sample_coords(const SparseGradArgs& a, int64_t total_samples, cudaStream_t st, int64_t* launches);
+template <typename T>
+cudaError_t launch_dense_grad(const DenseGradArgs<T>& a, cudaStream_t st, int64_t* launches);
+
+// ---------------------------------------------------------------------------
+// Solver kernels (k_solver.cu)
+// ---------------------------------------------------------------------------
+// Which factor set a Gram pair uses.
+enum GramSel : int { SEL_A = 0, SEL_ABAR = 1, SEL_D = 2 };
+
+template <typename T>
+struct GramArgs {
+    int ndim;
+    int R;
+    int64_t dims[4];
+    int64_t row_off[4];       // row offsets of each mode in the concatenated factor buffer
+    const T* A;               // concatenated factors, rows of R
+    const T* Abar;
+    int npairs;
+    int sel_u[6], sel_v[6];
+    double* out;              // [npairs][ndim][R][R], accumulated into (zeroed by the caller)
+    const int32_t* skip;
+};
+
+template <typename T>
+struct FactorUpdateArgs {
+    int ndim;
+    int R;
+    int64_t nrows;            // sum I_k
+    int64_t row_off[4];
+    T* A;
+    const T* Abar;
+    T* G;
+    T* u;
+    T* v;
+    const float* B;           // [ndim][R][R]  (Gamma_k * S_H) or nullptr
+    const float* C;           // [ndim][R][R]  ((Gamma_k - Gammabar_k) * S_H) or nullptr
+    const int32_t* hist_len;  // device: history terms apply when *hist_len > 0
+    double lam;
+    double beta1, beta2, eps, lower;
+    SolverState* st;
+    const int32_t* skip;
+};
+
+template <typename T>
+cudaError_t launch_gram(const GramArgs<T>& a, int64_t nrows, cudaStream_t st, int64_t* launches);
+// B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H from grams [P_n = A'A, E_n = D'A].
+cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
+                               float* B, float* C, const int32_t* skip, cudaStream_t st, int64_t* launches);
+template <typename T>
+cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, int64_t* launches);
+
+// Temporal-weight ADAM step: g = gs + mu s; Alg. 2 Step; gs <- 0; i <- i + 1.
+template <typename T>
+cudaError_t launch_temporal_adam(int R, T* s, T* gs, T* u, T* v, double mu, double beta1, double beta2,
+                                 double eps, double lower, SolverState* st, const int32_t* skip, cudaStream_t stream,
+                                 int64_t* launches);
+
+// Solver bookkeeping.
+cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
+                               int64_t* launches);
+cudaError_t launch_epoch_begin(SolverState* st, double tol, int32_t* skip, cudaStream_t stream, int64_t* launches);
+template <typename T>
+cudaError_t launch_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
+                             double decay, const int32_t* skip, cudaStream_t stream, int64_t* launches);
+template <typename T>
+cudaError_t launch_adam_reset(int64_t n, const T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int zero_a, T* a_zero,
+                              cudaStream_t stream, int64_t* launches);
+
+// Objective finishing terms.
+// Temporal: F_new += mu/2 ||s||^2; if set_cur, F_cur = F_new.
+template <typename T>
+cudaError_t launch_obj_finish_w(SolverState* st, const T* s, int R, double mu, int set_cur, int* err,
+                                const int32_t* skip, cudaStream_t stream, int64_t* launches);
+// Factor: F_new += 1/2 <S_H, telescoped history Gram sum> + lambda/2 sum ||A||^2.
+// grams: [6][ndim][R][R] for pairs (A,A), (Abar,Abar), (Abar,A), (D,D), (D,A), (Abar,D).
+cudaError_t launch_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
+                                const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip,
+                                cudaStream_t stream, int64_t* launches);
+
+// S_H = sum_h w theta^(t-h) s_h s_h' over the window (double R x R).
+template <typename T>
+cudaError_t launch_history_SH(int R, const T* s_hist, const int64_t* h_dev, const int32_t* hist_len,
+                              const SliceDesc* slice, double w, double theta, double* SH, cudaStream_t stream,
+                              int64_t* launches);
+
+// Least-squares temporal solve: (Gamma + mu/2 I) s = rhs, s <- max(s, l), Gamma = *_n P_n.
+template <typename T>
+cudaError_t launch_lsq_solve(int ndim, int R, const double* P, const T* rhs, double mu, double lower, T* s,
+                             double* work, int* err, cudaStream_t stream, int64_t* launches);
+
+// Write a slice descriptor into device memory (by-value kernel argument, so
+// no host buffer has to outlive the call).
+cudaError_t launch_write_desc(SliceDesc* dst, SliceDesc val, cudaStream_t stream, int64_t* launches);
+// History slot update after step t: slot <- (t, s_t), window length <- len.
+template <typename T>
+cudaError_t launch_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_len, int slot, int64_t t, int len,
+                               const T* s, cudaStream_t stream, int64_t* launches);
+
+// Small helpers.
+template <typename T>
+cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, int64_t* launches);
+
+}  // namespace sgcp

@@ -1,0 +1,655 @@
+// Solver kernels of OnlineGCP (arXiv 2110.14514 Sec. 4.2-4.4): Gram matrices,
+// history-penalty coefficients, the fused history + regularisation + ADAM row
+// update of the factor matrices (eq. spatial_gcp_grad, Alg. 2, Alg. 4), the
+// temporal-weight ADAM step (Alg. 3), per-epoch accept / rollback, the
+// objective's history and regularisation terms (Alg. 5), the history weight
+// matrix S_H and the Gaussian least-squares temporal solve (Sec. 5).
+//
+// History algebra used here.  With Gamma_k = *_{n != k} A^(n)'A^(n),
+// Gammabar_k = *_{n != k} Abar^(n)'A^(n) and S_H = sum_h w_h s_h s_h', the
+// per-h loop of eq. spatial_gcp_grad collapses because
+// diag(s_h) B diag(s_h) = B * (s_h s_h'):
+//   sum_h w_h (A Gamma_h-term - Abar Gammabar_h-term)
+//     = A (Gamma_k * S_H) - Abar (Gammabar_k * S_H)
+//     = D (Gamma_k * S_H) + Abar ((Gamma_k - Gammabar_k) * S_H),   D = A - Abar,
+// and Gamma_k - Gammabar_k is summed from differences E_n = D^(n)'A^(n)
+// (telescoping over the Hadamard factors) so nothing cancels when A ~ Abar.
+#include "internal.h"
+#include "sgcp.h"
+
+namespace sgcp {
+
+// ---------------------------------------------------------------------------
+// Gram matrices Gram(U, V)[l][m] = sum_r U[r][l] V[r][m], U, V in {A, Abar, D}.
+// grid = (row chunks, ndim, npairs); float partials per chunk, double sums.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T gsel(int sel, const T* A, const T* Ab, int64_t i) {
+    return sel == SEL_A ? A[i] : (sel == SEL_ABAR ? Ab[i] : A[i] - Ab[i]);
+}
+
+constexpr int kGramRows = 256;   // rows per block
+constexpr int kGramStage = 32;   // rows staged in shared memory at a time
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.skip && *a.skip) return;
+    const int k = blockIdx.y, pr = blockIdx.z, R = a.R;
+    const int64_t I = a.dims[k];
+    const int64_t r0 = (int64_t)blockIdx.x * kGramRows;
+    if (r0 >= I) return;
+    const int64_t r1 = min(r0 + (int64_t)kGramRows, I);
+    const T* A = a.A + a.row_off[k] * R;
+    const T* Ab = a.Abar + a.row_off[k] * R;
+    const int su = a.sel_u[pr], svv = a.sel_v[pr];
+    T* Us = reinterpret_cast<T*>(smem_raw);          // [stage][R]
+    T* Vs = Us + kGramStage * R;                      // [stage][R]
+    float* red = reinterpret_cast<float*>(Vs + kGramStage * R);   // [groups][R*R]
+    const int tq = R / 4;                 // 4x4 output tiles per dimension
+    const int tiles = tq * tq;
+    const int groups = tiles >= 256 ? 1 : 256 / tiles;
+    const int tid = threadIdx.x;
+    const int grp = tid / (tiles < 256 ? tiles : 256);
+    float acc[4][4][4];                   // up to 4 tiles per thread (R = 128)
+    const int per = (tiles + 255) / 256;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[t][x][y] = 0.0f;
+    for (int64_t base = r0; base < r1; base += kGramStage) {
+        const int nr = (int)min((int64_t)kGramStage, r1 - base);
+        __syncthreads();
+        for (int i = tid; i < nr * R; i += blockDim.x) {
+            Us[i] = gsel(su, A, Ab, base * R + i);
+            Vs[i] = gsel(svv, A, Ab, base * R + i);
+        }
+        __syncthreads();
+        if (grp < groups) {
+            for (int t = 0; t < per; ++t) {
+                const int tile = (tiles >= 256 ? tid + 256 * t : tid % tiles);
+                if (tile >= tiles || t >= 4) break;
+                const int tl = tile / tq, tm = tile % tq;
+                for (int r = grp; r < nr; r += groups) {
+                    float u[4], v[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        u[x] = (float)Us[r * R + tl * 4 + x];
+                        v[x] = (float)Vs[r * R + tm * 4 + x];
+                    }
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[t][x][y] += u[x] * v[y];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // reduce the row groups in shared memory, then one double atomic per output
+    for (int i = tid; i < groups * R * R; i += blockDim.x) red[i] = 0.0f;
+    __syncthreads();
+    if (grp < groups) {
+        for (int t = 0; t < per && t < 4; ++t) {
+            const int tile = (tiles >= 256 ? tid + 256 * t : tid % tiles);
+            if (tile >= tiles) break;
+            const int tl = tile / tq, tm = tile % tq;
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) red[grp * R * R + (tl * 4 + x) * R + tm * 4 + y] = acc[t][x][y];
+        }
+    }
+    __syncthreads();
+    double* out = a.out + ((int64_t)pr * a.ndim + k) * R * R;
+    for (int i = tid; i < R * R; i += blockDim.x) {
+        double sum = 0.0;
+        for (int g = 0; g < groups; ++g) sum += (double)red[g * R * R + i];
+        atomicAdd(out + i, sum);
+    }
+}
+
+template <typename T>
+cudaError_t launch_gram(const GramArgs<T>& a, int64_t, cudaStream_t st, int64_t* launches) {
+    int64_t maxI = 0;
+    for (int k = 0; k < a.ndim; ++k) maxI = a.dims[k] > maxI ? a.dims[k] : maxI;
+    const int tiles = (a.R / 4) * (a.R / 4);
+    const int groups = tiles >= 256 ? 1 : 256 / tiles;
+    const size_t smem = 2 * kGramStage * a.R * sizeof(T) + (size_t)groups * a.R * a.R * sizeof(float);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)((maxI + kGramRows - 1) / kGramRows), a.ndim, a.npairs);
+    k_gram<T><<<grid, 256, smem, st>>>(a);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// B_k = Gamma_k * S_H and C_k = (Gamma_k - Gammabar_k) * S_H  (float outputs)
+// grams = [P (ndim x R x R) | E (ndim x R x R)], P_n = A'A, E_n = D'A.
+// ---------------------------------------------------------------------------
+__global__ void k_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
+                              float* B, float* C, const int32_t* skip) {
+    if (skip && *skip) return;
+    const int k = blockIdx.x;
+    const bool on = *hist_len > 0;
+    const double* P = grams;
+    const double* E = grams + (int64_t)ndim * R * R;
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+        if (!on) {
+            B[k * R * R + i] = 0.0f;
+            C[k * R * R + i] = 0.0f;
+            continue;
+        }
+        double gam = 1.0, dgam = 0.0;
+        // telescoping: prod P - prod Q = sum_m (prod_{before} Q)(E_m)(prod_{after} P), Q = P - E
+        for (int m = 0; m < ndim; ++m) {
+            if (m == k) continue;
+            gam *= P[m * R * R + i];
+            double term = E[m * R * R + i];
+            for (int n = 0; n < ndim; ++n) {
+                if (n == k || n == m) continue;
+                term *= (n < m) ? (P[n * R * R + i] - E[n * R * R + i]) : P[n * R * R + i];
+            }
+            dgam += term;
+        }
+        B[k * R * R + i] = (float)(gam * SH[i]);
+        C[k * R * R + i] = (float)(dgam * SH[i]);
+    }
+}
+
+cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
+                               float* B, float* C, const int32_t* skip, cudaStream_t st, int64_t* launches) {
+    k_hist_coeffs<<<ndim, 256, 0, st>>>(ndim, R, grams, SH, hist_len, B, C, skip);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Factor row update: g = G + lambda a + d B_k + abar C_k; ADAM step (Alg. 2)
+// with bias correction alpha sqrt(1 - b2^(i+1)) / (1 - b1^(i+1)); projection
+// a <- max(a, l); G <- 0 for the next gradient.  The last block advances i.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.skip && *a.skip) return;
+    const int R = a.R;
+    const int rows_per = blockDim.x / R;         // R divides 256 or R >= 256 handled below
+    T* dsh = reinterpret_cast<T*>(smem_raw);     // [rows_per][R]  d = a - abar
+    T* bsh = dsh + rows_per * R;                 // [rows_per][R]  abar
+    const SolverState* st = a.st;
+    const int it = st->i;
+    const double alpha = st->alpha;
+    const double bias = sqrt(1.0 - pow(a.beta2, (double)(it + 1))) / (1.0 - pow(a.beta1, (double)(it + 1)));
+    const T at = (T)(alpha * bias);
+    const bool hist = a.B != nullptr && *a.hist_len > 0;
+    const int rl = threadIdx.x / R, j = threadIdx.x % R;
+    const bool tact = rl < rows_per;
+    for (int64_t rb = (int64_t)blockIdx.x * rows_per; rb < a.nrows; rb += (int64_t)gridDim.x * rows_per) {
+        const int64_t row = rb + rl;
+        const bool act = tact && row < a.nrows;
+        const int64_t idx = row * R + j;
+        T av = T(0), abv = T(0);
+        if (act) {
+            av = a.A[idx];
+            abv = a.Abar[idx];
+        }
+        if (hist) {
+            __syncthreads();
+            if (tact) {
+                dsh[rl * R + j] = av - abv;
+                bsh[rl * R + j] = abv;
+            }
+            __syncthreads();
+        }
+        if (act) {
+            int k = 0;
+            while (k + 1 < a.ndim && row >= a.row_off[k + 1]) ++k;
+            T g = a.G[idx] + (T)a.lam * av;
+            if (hist) {
+                const float* Bk = a.B + (int64_t)k * R * R;
+                const float* Ck = a.C + (int64_t)k * R * R;
+                T sb = T(0), sc = T(0);
+                for (int l = 0; l < R; ++l) {
+                    sb += dsh[rl * R + l] * (T)__ldg(Bk + l * R + j);
+                    sc += bsh[rl * R + l] * (T)__ldg(Ck + l * R + j);
+                }
+                g += sb + sc;
+            }
+            const T u = (T)a.beta1 * a.u[idx] + (T)(1.0 - a.beta1) * g;
+            const T v = (T)a.beta2 * a.v[idx] + (T)(1.0 - a.beta2) * g * g;
+            T an = av - at * u / (sqrt(v) + (T)a.eps);
+            if (an < (T)a.lower) an = (T)a.lower;
+            a.u[idx] = u;
+            a.v[idx] = v;
+            a.A[idx] = an;
+            a.G[idx] = T(0);
+        }
+    }
+    // last block advances the iteration counter (every block read i above)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.st->ticket, 1u);
+        if (prev == gridDim.x - 1) {
+            a.st->i = it + 1;
+            a.st->ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
+static int solver_num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename T>
+cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, int64_t* launches) {
+    const int threads = a.R <= 256 ? (256 / a.R) * a.R : 256;
+    if (a.R > 256) return cudaErrorInvalidValue;
+    const int rows_per = threads / a.R;
+    const size_t smem = 2 * (size_t)rows_per * a.R * sizeof(T);
+    int64_t want = (a.nrows + rows_per - 1) / rows_per;
+    const int64_t cap = 8LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_factor_update<T><<<blocks, threads, smem, st>>>(a);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Temporal ADAM step on s (one block).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_temporal_adam(int R, T* s, T* gs, T* u, T* v, double mu, double beta1, double beta2, double eps,
+                                double lower, SolverState* st, const int32_t* skip) {
+    if (skip && *skip) return;
+    const int it = st->i;
+    const double bias = sqrt(1.0 - pow(beta2, (double)(it + 1))) / (1.0 - pow(beta1, (double)(it + 1)));
+    const T at = (T)(st->alpha * bias);
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        const T g = gs[j] + (T)mu * s[j];
+        const T uu = (T)beta1 * u[j] + (T)(1.0 - beta1) * g;
+        const T vv = (T)beta2 * v[j] + (T)(1.0 - beta2) * g * g;
+        T sn = s[j] - at * uu / (sqrt(vv) + (T)eps);
+        if (sn < (T)lower) sn = (T)lower;
+        u[j] = uu;
+        v[j] = vv;
+        s[j] = sn;
+        gs[j] = T(0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->i = it + 1;
+}
+
+template <typename T>
+cudaError_t launch_temporal_adam(int R, T* s, T* gs, T* u, T* v, double mu, double beta1, double beta2, double eps,
+                                 double lower, SolverState* st, const int32_t* skip, cudaStream_t stream,
+                                 int64_t* launches) {
+    k_temporal_adam<T><<<1, 128, 0, stream>>>(R, s, gs, u, v, mu, beta1, beta2, eps, lower, st, skip);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Solver bookkeeping
+// ---------------------------------------------------------------------------
+__global__ void k_solver_init(SolverState* st, double alpha, int reset_counter) {
+    st->alpha = alpha;
+    st->epoch = 0;
+    st->done = 0;
+    st->accept = 0u;
+    st->ticket = 0u;
+    st->F_new = 0.0;
+    if (reset_counter) st->i = 0;
+}
+
+cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
+                               int64_t* launches) {
+    k_solver_init<<<1, 1, 0, stream>>>(st, alpha, reset_counter);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// Alg. 3/4 loop test "while F > tol": once it fails, every later kernel of
+// the solver call is skipped through st->done.
+__global__ void k_epoch_begin(SolverState* st, double tol) {
+    if (!st->done && !(st->F_cur > tol)) st->done = 1;
+    st->F_old = st->F_cur;
+    st->F_new = 0.0;
+}
+
+cudaError_t launch_epoch_begin(SolverState* st, double tol, int32_t*, cudaStream_t stream, int64_t* launches) {
+    k_epoch_begin<<<1, 1, 0, stream>>>(st, tol);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// Alg. 2 Update(passed) with passed = (F_new <= F_old) and F_new finite.
+template <typename T>
+__global__ void k_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
+                            double decay) {
+    if (st->done) return;
+    const double Fn = st->F_new, Fo = st->F_old;
+    const bool passed = !(Fn > Fo) && isfinite(Fn);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (passed) {
+            u_o[i] = u[i];
+            v_o[i] = v[i];
+            a_o[i] = a[i];
+        } else {
+            u[i] = u_o[i];
+            v[i] = v_o[i];
+            a[i] = a_o[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&st->ticket, 1u);
+        if (prev == gridDim.x - 1) {
+            if (passed) {
+                st->F_cur = Fn;
+                st->accept |= (st->epoch < 32) ? (1u << st->epoch) : 0u;
+            } else {
+                st->F_cur = Fo;
+                st->alpha *= decay;
+                st->i -= tau;
+            }
+            st->epoch += 1;
+            st->ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
+                             double decay, const int32_t*, cudaStream_t stream, int64_t* launches) {
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = 4LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_epoch_end<T><<<blocks, 256, 0, stream>>>(st, n, a, u, v, a_o, u_o, v_o, tau, decay);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ADAM Init (with the checkpoint set to the starting point); zero_a also sets a <- 0 first.
+template <typename T>
+__global__ void k_adam_reset(int64_t n, const T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int zero_a, T* a_zero) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (zero_a) a_zero[i] = T(0);
+        u[i] = T(0);
+        v[i] = T(0);
+        u_o[i] = T(0);
+        v_o[i] = T(0);
+        a_o[i] = zero_a ? T(0) : a[i];
+    }
+}
+
+template <typename T>
+cudaError_t launch_adam_reset(int64_t n, const T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int zero_a, T* a_zero,
+                              cudaStream_t stream, int64_t* launches) {
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = 4LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_adam_reset<T><<<blocks, 256, 0, stream>>>(n, a, u, v, a_o, u_o, v_o, zero_a, a_zero);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Objective terms
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_obj_finish_w(SolverState* st, const T* s, int R, double mu, int set_cur, int* err,
+                               const int32_t* skip) {
+    if (skip && *skip) return;
+    double ss = 0.0;
+    for (int j = 0; j < R; ++j) ss += (double)s[j] * (double)s[j];
+    const double F = st->F_new + 0.5 * mu * ss;
+    st->F_new = F;
+    if (!isfinite(F)) set_err(err, ERRB_NUMERIC);
+    if (set_cur) st->F_cur = F;
+}
+
+template <typename T>
+cudaError_t launch_obj_finish_w(SolverState* st, const T* s, int R, double mu, int set_cur, int* err,
+                                const int32_t* skip, cudaStream_t stream, int64_t* launches) {
+    k_obj_finish_w<T><<<1, 1, 0, stream>>>(st, s, R, mu, set_cur, err, skip);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// History objective 1/2 sum_h w_h ||Mbar_h - M_h||^2 in telescoped form:
+// M_h - Mbar_h = sum_k [[s_h; Abar^(1..k-1), D^(k), A^(k+1..d)]], so
+// ||.||^2 = sum_{k,l} s_h' (*_n Gram(U_kn, U_ln)) s_h with U_kn = Abar (n < k),
+// D (n = k), A (n > k); summed over h through S_H.
+__device__ __forceinline__ int which_mat(int k, int n) { return n < k ? SEL_ABAR : (n == k ? SEL_D : SEL_A); }
+
+// grams layout: pair index p in [(A,A), (Abar,Abar), (Abar,A), (D,D), (D,A), (Abar,D)].
+__device__ __forceinline__ double gram_entry(const double* grams, int ndim, int R, int n, int u, int v, int l, int m) {
+    // returns Gram(u, v)[l][m] for mode n, using Gram(v, u)[m][l] when only the transpose is stored
+    int p = -1;
+    bool tr = false;
+    if (u == SEL_A && v == SEL_A) p = 0;
+    else if (u == SEL_ABAR && v == SEL_ABAR) p = 1;
+    else if (u == SEL_ABAR && v == SEL_A) p = 2;
+    else if (u == SEL_A && v == SEL_ABAR) { p = 2; tr = true; }
+    else if (u == SEL_D && v == SEL_D) p = 3;
+    else if (u == SEL_D && v == SEL_A) p = 4;
+    else if (u == SEL_A && v == SEL_D) { p = 4; tr = true; }
+    else if (u == SEL_ABAR && v == SEL_D) p = 5;
+    else { p = 5; tr = true; }   // (D, Abar)
+    const double* g = grams + ((int64_t)p * ndim + n) * R * R;
+    return tr ? g[m * R + l] : g[l * R + m];
+}
+
+__global__ void k_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
+                               const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip) {
+    if (skip && *skip) return;
+    __shared__ double red[32];
+    double acc = 0.0, reg = 0.0;
+    const bool hist = *hist_len > 0;
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+        const int l = i / R, m = i % R;
+        if (hist) {
+            double tot = 0.0;
+            for (int k = 0; k < ndim; ++k)
+                for (int kk = 0; kk < ndim; ++kk) {
+                    double prod = 1.0;
+                    for (int n = 0; n < ndim; ++n)
+                        prod *= gram_entry(grams, ndim, R, n, which_mat(k, n), which_mat(kk, n), l, m);
+                    tot += prod;
+                }
+            acc += SH[i] * tot;
+        }
+        if (l == m)
+            for (int n = 0; n < ndim; ++n) reg += grams[((int64_t)0 * ndim + n) * R * R + i];
+    }
+    double v = 0.5 * acc + 0.5 * lam * reg;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(SGCP_FULL_MASK, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+        const double F = st->F_new + tot;
+        st->F_new = F;
+        if (!isfinite(F)) set_err(err, ERRB_NUMERIC);
+        if (set_cur) st->F_cur = F;
+    }
+}
+
+cudaError_t launch_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
+                                const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip,
+                                cudaStream_t stream, int64_t* launches) {
+    k_obj_finish_f<<<1, 256, 0, stream>>>(st, ndim, R, grams, SH, hist_len, lam, set_cur, err, skip);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// S_H = sum_{h in window} w theta^(t-h) s_h s_h'
+template <typename T>
+__global__ void k_history_SH(int R, const T* s_hist, const int64_t* h_dev, const int32_t* hist_len,
+                             const SliceDesc* slice, double w, double theta, double* SH) {
+    const int n = *hist_len;
+    const int64_t t = slice->t;
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+        const int l = i / R, m = i % R;
+        double acc = 0.0;
+        for (int h = 0; h < n; ++h) {
+            const double wh = w * pow(theta, (double)(t - h_dev[h]));
+            acc += wh * (double)s_hist[h * R + l] * (double)s_hist[h * R + m];
+        }
+        SH[i] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_history_SH(int R, const T* s_hist, const int64_t* h_dev, const int32_t* hist_len,
+                              const SliceDesc* slice, double w, double theta, double* SH, cudaStream_t stream,
+                              int64_t* launches) {
+    k_history_SH<T><<<1, 256, 0, stream>>>(R, s_hist, h_dev, hist_len, slice, w, theta, SH);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Least-squares temporal solve (one block, Cholesky in double).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lsq_solve(int ndim, int R, const double* P, const T* rhs, double mu, double lower, T* s,
+                            double* Mw, int* err) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+        double g = 1.0;
+        for (int n = 0; n < ndim; ++n) g *= P[(int64_t)n * R * R + i];
+        if (i / R == i % R) g += 0.5 * mu;
+        Mw[i] = g;
+    }
+    __syncthreads();
+    // in-place lower Cholesky factor, column by column
+    for (int c = 0; c < R; ++c) {
+        if (threadIdx.x == 0) {
+            double d = Mw[c * R + c];
+            for (int k = 0; k < c; ++k) d -= Mw[c * R + k] * Mw[c * R + k];
+            if (!(d > 0.0)) {
+                bad = 1;
+                d = 1.0;
+            }
+            Mw[c * R + c] = sqrt(d);
+        }
+        __syncthreads();
+        for (int r = c + 1 + threadIdx.x; r < R; r += blockDim.x) {
+            double v = Mw[r * R + c];
+            for (int k = 0; k < c; ++k) v -= Mw[r * R + k] * Mw[c * R + k];
+            Mw[r * R + c] = v / Mw[c * R + c];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* y = Mw + R * R;
+        for (int r = 0; r < R; ++r) {
+            double v = (double)rhs[r];
+            for (int k = 0; k < r; ++k) v -= Mw[r * R + k] * y[k];
+            y[r] = v / Mw[r * R + r];
+        }
+        for (int r = R - 1; r >= 0; --r) {
+            double v = y[r];
+            for (int k = r + 1; k < R; ++k) v -= Mw[k * R + r] * y[k];
+            y[r] = v / Mw[r * R + r];
+        }
+        for (int r = 0; r < R; ++r) {
+            double v = y[r];
+            if (v < lower) v = lower;
+            s[r] = (T)v;
+        }
+        if (bad) set_err(err, ERRB_SOLVE);
+    }
+}
+
+template <typename T>
+cudaError_t launch_lsq_solve(int ndim, int R, const double* P, const T* rhs, double mu, double lower, T* s,
+                             double* work, int* err, cudaStream_t stream, int64_t* launches) {
+    k_lsq_solve<T><<<1, 128, 0, stream>>>(ndim, R, P, rhs, mu, lower, s, work, err);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+__global__ void k_write_desc(SliceDesc* dst, SliceDesc val) { *dst = val; }
+
+cudaError_t launch_write_desc(SliceDesc* dst, SliceDesc val, cudaStream_t stream, int64_t* launches) {
+    k_write_desc<<<1, 1, 0, stream>>>(dst, val);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_len, int slot, int64_t t, int len,
+                              const T* s) {
+    for (int j = threadIdx.x; j < R; j += blockDim.x) s_hist[(int64_t)slot * R + j] = s[j];
+    if (threadIdx.x == 0) {
+        h_dev[slot] = t;
+        *hist_len = len;
+    }
+}
+
+template <typename T>
+cudaError_t launch_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_len, int slot, int64_t t, int len,
+                               const T* s, cudaStream_t stream, int64_t* launches) {
+    k_hist_update<T><<<1, 128, 0, stream>>>(R, s_hist, h_dev, hist_len, slot, t, len, s);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_copy(T* dst, const T* src, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+template <typename T>
+cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, int64_t* launches) {
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = 4LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_copy<T><<<blocks, 256, 0, stream>>>(dst, src, n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+#define SGCP_INST(T)                                                                                                  \
+    template cudaError_t launch_gram<T>(const GramArgs<T>&, int64_t, cudaStream_t, int64_t*);                        \
+    template cudaError_t launch_factor_update<T>(const FactorUpdateArgs<T>&, cudaStream_t, int64_t*);                \
+    template cudaError_t launch_temporal_adam<T>(int, T*, T*, T*, T*, double, double, double, double, double,        \
+                                                 SolverState*, const int32_t*, cudaStream_t, int64_t*);               \
+    template cudaError_t launch_epoch_end<T>(SolverState*, int64_t, T*, T*, T*, T*, T*, T*, int, double,             \
+                                             const int32_t*, cudaStream_t, int64_t*);                                 \
+    template cudaError_t launch_adam_reset<T>(int64_t, const T*, T*, T*, T*, T*, T*, int, T*, cudaStream_t,          \
+                                              int64_t*);                                                              \
+    template cudaError_t launch_obj_finish_w<T>(SolverState*, const T*, int, double, int, int*, const int32_t*,      \
+                                                cudaStream_t, int64_t*);                                              \
+    template cudaError_t launch_history_SH<T>(int, const T*, const int64_t*, const int32_t*, const SliceDesc*,       \
+                                              double, double, double*, cudaStream_t, int64_t*);                      \
+    template cudaError_t launch_lsq_solve<T>(int, int, const double*, const T*, double, double, T*, double*, int*,   \
+                                             cudaStream_t, int64_t*);                                                 \
+    template cudaError_t launch_copy<T>(T*, const T*, int64_t, cudaStream_t, int64_t*);                          \
+    template cudaError_t launch_hist_update<T>(int, T*, int64_t*, int32_t*, int, int64_t, int, const T*,            \
+                                               cudaStream_t, int64_t*);
+
+SGCP_INST(float)
+SGCP_INST(double)
+
+}  // namespace sgcp

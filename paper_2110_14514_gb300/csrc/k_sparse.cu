@@ -1,0 +1,471 @@
+// Sparse-slice kernels: slice ingest (nonzero hash + hot rows) and the fused
+// stratified-sample -> Kruskal model -> loss derivative -> all-mode MTTKRP
+// kernel (arXiv 2110.14514 Sec. 4.3, Alg. 5 / Alg. 6; Sec. 2.2 eqs.
+// gcp_grad_A, gcp_grad_lambda).
+//
+// Layout of the fused kernel: a warp owns chunks of 32 consecutive sample
+// slots.  In phase 1 every lane draws one sample (Philox counter -> COO entry
+// for a nonzero sample, bounded rejection against the nonzero hash for a zero
+// sample).  In phase 2 the warp walks its 32 samples SPW at a time: a group of
+// G = R/4 lanes handles one sample, each lane holding four consecutive rank
+// components j, so every factor-row gather is one 16-byte load per lane and
+// a 128-byte row for R = 32.  m is reduced with xor shuffles inside the
+// group, y = w df/dm(x, m) stays in registers (the sampled gradient tensor Y~
+// is never stored), and every mode's row contribution y s * prod_{n != k}
+// a^(n) is added with a 16-byte vector atomic -- or, for the few rows that
+// most nonzeros hit (Zipf-like modes), into a per-block shared-memory
+// accumulator flushed once at the end.
+#include "internal.h"
+#include "sgcp.h"
+
+namespace sgcp {
+
+static constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ unsigned long long hash_home(unsigned long long key, int hlog2) {
+    return (key * 0x9E3779B97F4A7C15ull) >> (64 - hlog2);
+}
+
+__device__ __forceinline__ bool hash_contains(const unsigned long long* __restrict__ keys, int hlog2,
+                                              unsigned long long key) {
+    const unsigned long long mask = (1ull << hlog2) - 1ull;
+    unsigned long long h = hash_home(key, hlog2);
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long k = __ldg(keys + h);
+        if (k == key) return true;
+        if (k == kEmpty) return false;
+        h = (h + 1ull) & mask;
+    }
+    return false;
+}
+
+// Per-draw constants shared by all threads.
+struct DrawSizes {
+    int64_t p_eff, total;
+    float w_nz, w_z;
+};
+
+__device__ __forceinline__ DrawSizes draw_sizes(const SparseGradArgs& a, const SliceDesc& sd) {
+    DrawSizes z;
+    const int64_t eta = sd.nnz;
+    int64_t omega = 1;
+    for (int k = 0; k < a.ndim; ++k) omega *= a.dims[k];
+    const int64_t zeta = omega - eta;
+    int64_t q_eff;
+    if (a.all_nnz) {
+        z.p_eff = eta;
+        q_eff = 0;
+    } else {
+        z.p_eff = eta > 0 ? a.p : 0;
+        q_eff = zeta > 0 ? a.q : 0;   // a slice without zeros drops its zero stratum
+    }
+    z.total = z.p_eff + q_eff;
+    z.w_nz = a.all_nnz ? 1.0f : (z.p_eff ? (float)((double)eta / (double)z.p_eff) : 0.0f);
+    z.w_z = q_eff ? (float)((double)zeta / (double)q_eff) : 0.0f;
+    return z;
+}
+
+// Draw sample slot c (Alg. 6 with the counter layout (slot, attempt, draw, purpose<<24 | t)).
+template <int D>
+__device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceDesc& sd, const DrawSizes& z,
+                                           int64_t c, int (&ci)[D], float& x, float& w, int& attempt, bool& ok) {
+    ok = false;
+    x = 0.0f;
+    w = 0.0f;
+    attempt = -1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) ci[k] = 0;
+    if (c >= z.total) return;
+    const float* vals = (const float*)sd.vals;
+    if (a.all_nnz || c < z.p_eff) {
+        int64_t e = c;
+        if (!a.all_nnz) {
+            uint32_t ctr[4] = {(uint32_t)c, 0u, a.draw, counter_word3(a.pur_nz, sd.t)};
+            philox4x32_10(ctr, a.key0, a.key1);
+            e = bounded_u32(ctr[0], (uint32_t)sd.nnz);
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) ci[k] = __ldg(sd.idx + e * D + k);
+        x = __ldg(vals + e);
+        w = z.w_nz;
+        ok = true;
+        return;
+    }
+    const uint32_t cz = (uint32_t)(c - z.p_eff);
+    const uint32_t w3 = counter_word3(a.pur_z, sd.t);
+    for (int att = 0; att < a.cap; ++att) {
+        uint32_t ctr[4] = {cz, (uint32_t)att, a.draw, w3};
+        philox4x32_10(ctr, a.key0, a.key1);
+        unsigned long long key = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            ci[k] = (int)bounded_u32(ctr[k], (uint32_t)a.dims[k]);
+            key = key * (unsigned long long)a.dims[k] + (unsigned long long)ci[k];
+        }
+        if (!hash_contains(a.hkeys, a.hlog2, key)) {
+            w = z.w_z;
+            attempt = att;
+            ok = true;
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) ci[k] = 0;
+    set_err(a.err, ERRB_SAMPLING);
+}
+
+__device__ __forceinline__ float4 f4mul(float4 a, float4 b) {
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ float4 f4scale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+
+template <int D, int RP>
+__global__ void __launch_bounds__(256) k_sparse_grad(const SparseGradArgs a) {
+    constexpr int G = RP / 4;        // lanes per sample
+    constexpr int SPW = 32 / G;      // samples per warp step
+    extern __shared__ __align__(16) float smem[];
+    if (a.skip && *a.skip) return;
+    const SliceDesc sd = a.slice ? *a.slice : a.inline_slice;
+    const DrawSizes z = draw_sizes(a, sd);
+    const bool wantG = (a.want & SGCP_WANT_FACTORS) != 0;
+    const bool wantS = (a.want & SGCP_WANT_TEMPORAL) != 0;
+    const bool wantF = (a.want & SGCP_WANT_LOSS) != 0;
+    const int nhot = wantG ? a.nhot : 0;
+    const int R = a.R;
+
+    float* hacc = smem;                                  // [D][nhot][RP]
+    float* gsb = smem + D * nhot * RP;                   // [RP]
+    double* fb = (double*)(gsb + RP);                    // [8]
+    for (int i = threadIdx.x; i < D * nhot * RP + RP; i += blockDim.x) smem[i] = 0.0f;
+    if (threadIdx.x < 8) fb[threadIdx.x] = 0.0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G;
+    const int j0 = gl * 4;
+    const bool lact = j0 < R;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 sv = lact ? *reinterpret_cast<const float4*>(a.s + j0) : zero4;
+    const float ysc = a.y_scale ? *a.y_scale : 1.0f;
+    float4 gsl = zero4;
+    double fl = 0.0;
+
+    const int64_t nchunks = (z.total + 31) / 32;
+    const int wpb = blockDim.x >> 5;
+    for (int64_t ch = (int64_t)blockIdx.x * wpb + warp; ch < nchunks; ch += (int64_t)gridDim.x * wpb) {
+        int ci[D];
+        float x, w;
+        int att;
+        bool ok;
+        gen_sample<D>(a, sd, z, ch * 32 + lane, ci, x, w, att, ok);
+        int hs[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) hs[k] = (nhot && ok) ? __ldg(a.hot[k] + ci[k]) : -1;
+
+#pragma unroll 2
+        for (int r = 0; r < 32 / SPW; ++r) {
+            const int src = r * SPW + grp;
+            int cj[D], hj[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                cj[k] = __shfl_sync(SGCP_FULL_MASK, ci[k], src);
+                hj[k] = __shfl_sync(SGCP_FULL_MASK, hs[k], src);
+            }
+            const float xj = __shfl_sync(SGCP_FULL_MASK, x, src);
+            const float wj = __shfl_sync(SGCP_FULL_MASK, w, src);
+            const int okj = __shfl_sync(SGCP_FULL_MASK, (int)ok, src);
+            float4 av[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                av[k] = lact ? __ldg(reinterpret_cast<const float4*>(a.A[k] + (int64_t)cj[k] * R + j0)) : zero4;
+            float4 pr = sv;
+#pragma unroll
+            for (int k = 0; k < D; ++k) pr = f4mul(pr, av[k]);
+            float mp = (pr.x + pr.y) + (pr.z + pr.w);
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) mp += __shfl_xor_sync(SGCP_FULL_MASK, mp, off);
+            float f, y;
+            loss_eval<float>(a.loss, xj, mp, a.eps, f, y);
+            const float yw = okj ? y * wj * ysc : 0.0f;
+            if (wantF && gl == 0 && okj) fl += (double)wj * (double)f * (double)ysc;
+            if (wantS && lact) {
+                float4 t = av[0];
+#pragma unroll
+                for (int k = 1; k < D; ++k) t = f4mul(t, av[k]);
+                gsl.x += yw * t.x;
+                gsl.y += yw * t.y;
+                gsl.z += yw * t.z;
+                gsl.w += yw * t.w;
+            }
+            if (wantG && okj && lact) {
+                const float4 ys = f4scale(sv, yw);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    float4 c = ys;
+#pragma unroll
+                    for (int n = 0; n < D; ++n)
+                        if (n != k) c = f4mul(c, av[n]);
+                    if (hj[k] >= 0) {
+                        float* hp = hacc + (k * nhot + hj[k]) * RP + j0;
+                        atomicAdd(hp + 0, c.x);
+                        atomicAdd(hp + 1, c.y);
+                        atomicAdd(hp + 2, c.z);
+                        atomicAdd(hp + 3, c.w);
+                    } else {
+                        atomicAdd(reinterpret_cast<float4*>(a.G[k] + (int64_t)cj[k] * R + j0), c);
+                    }
+                }
+            }
+        }
+    }
+
+    // temporal gradient: reduce over the groups of the warp, then the block
+    if (wantS) {
+#pragma unroll
+        for (int off = G; off < 32; off <<= 1) {
+            gsl.x += __shfl_xor_sync(SGCP_FULL_MASK, gsl.x, off);
+            gsl.y += __shfl_xor_sync(SGCP_FULL_MASK, gsl.y, off);
+            gsl.z += __shfl_xor_sync(SGCP_FULL_MASK, gsl.z, off);
+            gsl.w += __shfl_xor_sync(SGCP_FULL_MASK, gsl.w, off);
+        }
+        if (grp == 0 && lact) {
+            atomicAdd(gsb + j0 + 0, gsl.x);
+            atomicAdd(gsb + j0 + 1, gsl.y);
+            atomicAdd(gsb + j0 + 2, gsl.z);
+            atomicAdd(gsb + j0 + 3, gsl.w);
+        }
+    }
+    if (wantF) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) fl += __shfl_xor_sync(SGCP_FULL_MASK, fl, off);
+        if (lane == 0) fb[warp] = fl;
+    }
+    __syncthreads();
+    if (nhot) {
+        for (int i = threadIdx.x; i < D * nhot * RP; i += blockDim.x) {
+            const float v = hacc[i];
+            const int k = i / (nhot * RP), rem = i - k * nhot * RP;
+            const int slot = rem / RP, j = rem - slot * RP;
+            if (v != 0.0f && j < R) {
+                const int row = a.hot_rows[k * kMaxHot + slot];
+                if (row >= 0) atomicAdd(a.G[k] + (int64_t)row * R + j, v);
+            }
+        }
+    }
+    if (wantS) {
+        for (int j = threadIdx.x; j < R; j += blockDim.x)
+            if (gsb[j] != 0.0f) atomicAdd(a.gs + j, gsb[j]);
+    }
+    if (wantF && threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < wpb; ++i) tot += fb[i];
+        if (tot != 0.0) atomicAdd(a.f, tot);
+    }
+}
+
+template <int D>
+__global__ void k_sample_coords(const SparseGradArgs a) {
+    const SliceDesc sd = a.slice ? *a.slice : a.inline_slice;
+    const DrawSizes z = draw_sizes(a, sd);
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < z.total; c += (int64_t)gridDim.x * blockDim.x) {
+        int ci[D];
+        float x, w;
+        int att;
+        bool ok;
+        gen_sample<D>(a, sd, z, c, ci, x, w, att, ok);
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.coords_out[c * D + k] = ok ? ci[k] : -1;
+        if (a.attempt_out) a.attempt_out[c] = att;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ingest: validate coordinates, insert linear keys into the hash, and count a
+// strided subsample of nonzeros per row for the hot-row choice.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_ingest(const IngestArgs a) {
+    const SliceDesc sd = a.slice;
+    const unsigned long long mask = (1ull << a.hlog2) - 1ull;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < sd.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        int c[D];
+        bool bad = false;
+        unsigned long long key = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            c[k] = sd.idx[e * D + k];
+            if (c[k] < 0 || (int64_t)c[k] >= a.dims[k]) bad = true;
+            key = key * (unsigned long long)a.dims[k] + (unsigned long long)(unsigned)c[k];
+        }
+        if (bad) {
+            set_err(a.err, ERRB_COORD);
+            continue;
+        }
+        unsigned long long h = hash_home(key, a.hlog2);
+        for (unsigned long long probe = 0;; ++probe) {
+            if (probe > mask) {
+                set_err(a.err, ERRB_HASH);
+                break;
+            }
+            const unsigned long long prev = atomicCAS(a.hkeys + h, kEmpty, key);
+            if (prev == kEmpty) break;
+            if (prev == key) {
+                set_err(a.err, ERRB_DUP);
+                break;
+            }
+            h = (h + 1ull) & mask;
+        }
+        if (e % a.sub_stride == 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) atomicAdd(a.counts + a.row_off[k] + c[k], 1);
+        }
+    }
+}
+
+__device__ int block_sum_int(int v, int* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(SGCP_FULL_MASK, v, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+    return tot;
+}
+
+__device__ int block_max_int(int v, int* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(SGCP_FULL_MASK, v, off));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int m = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = max(m, red[i]);
+    return m;
+}
+
+// One block per mode: the nhot rows with the largest subsample counts (at
+// least kMinHot) get a shared-memory accumulator slot in the fused kernel.
+__global__ void k_hot_select(const IngestArgs a) {
+    constexpr int kMinHot = 4;
+    __shared__ int red[32];
+    __shared__ int nslot;
+    const int k = blockIdx.x;
+    const int64_t I = a.dims[k];
+    const int32_t* cnt = a.counts + a.row_off[k];
+    int mx = 0;
+    for (int64_t r = threadIdx.x; r < I; r += blockDim.x) mx = max(mx, cnt[r]);
+    mx = block_max_int(mx, red);
+    int lo = kMinHot, hi = max(mx + 1, kMinHot);
+    while (lo < hi) {
+        const int mid = lo + (hi - lo) / 2;
+        int n = 0;
+        for (int64_t r = threadIdx.x; r < I; r += blockDim.x) n += cnt[r] >= mid;
+        n = block_sum_int(n, red);
+        if (n <= a.nhot) hi = mid;
+        else lo = mid + 1;
+    }
+    if (threadIdx.x == 0) nslot = 0;
+    __syncthreads();
+    for (int64_t r = threadIdx.x; r < I; r += blockDim.x) {
+        if (cnt[r] >= lo) {
+            const int slot = atomicAdd(&nslot, 1);
+            if (slot < a.nhot) {
+                a.hot[a.row_off[k] + r] = slot;
+                a.hot_rows[k * kMaxHot + slot] = (int32_t)r;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+cudaError_t launch_ingest(const IngestArgs& a, int64_t nnz, cudaStream_t st, int64_t* launches) {
+    const int threads = 256;
+    int64_t want = (nnz + threads - 1) / threads;
+    const int blocks = (int)(want < 1 ? 1 : (want > 8 * num_sms() ? 8 * num_sms() : want));
+    switch (a.ndim) {
+        case 2: k_ingest<2><<<blocks, threads, 0, st>>>(a); break;
+        case 3: k_ingest<3><<<blocks, threads, 0, st>>>(a); break;
+        case 4: k_ingest<4><<<blocks, threads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (a.nhot > 0) {
+        k_hot_select<<<a.ndim, 1024, 0, st>>>(a);
+        if (launches) *launches += 1;
+    }
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <int D, int RP>
+static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
+    const int threads = 256;
+    const int nhot = (a.want & SGCP_WANT_FACTORS) ? a.nhot : 0;
+    const size_t smem = (size_t)(D * nhot * RP + RP) * sizeof(float) + 8 * sizeof(double);
+    static int occ = 0;
+    static size_t occ_smem = 0;
+    if (occ == 0 || occ_smem != smem) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_sparse_grad<D, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sparse_grad<D, RP>, threads, smem);
+        if (occ < 1) occ = 1;
+        occ_smem = smem;
+    }
+    const int64_t chunks = (total + 31) / 32;
+    int64_t want = (chunks + (threads / 32) - 1) / (threads / 32);
+    const int64_t cap = (int64_t)occ * num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_sparse_grad<D, RP><<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t dispatch_rank(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
+    if (a.R <= 4) return run_sparse<D, 4>(a, total, st);
+    if (a.R <= 8) return run_sparse<D, 8>(a, total, st);
+    if (a.R <= 16) return run_sparse<D, 16>(a, total, st);
+    if (a.R <= 32) return run_sparse<D, 32>(a, total, st);
+    if (a.R <= 64) return run_sparse<D, 64>(a, total, st);
+    return run_sparse<D, 128>(a, total, st);
+}
+
+cudaError_t launch_sparse_grad(const SparseGradArgs& a, int64_t total, cudaStream_t st, int64_t* launches) {
+    if (launches) *launches += 1;
+    switch (a.ndim) {
+        case 2: return dispatch_rank<2>(a, total, st);
+        case 3: return dispatch_rank<3>(a, total, st);
+        case 4: return dispatch_rank<4>(a, total, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sample_coords(const SparseGradArgs& a, int64_t total, cudaStream_t st, int64_t* launches) {
+    const int threads = 256;
+    int64_t want = (total + threads - 1) / threads;
+    const int blocks = (int)(want < 1 ? 1 : (want > 8 * num_sms() ? 8 * num_sms() : want));
+    if (launches) *launches += 1;
+    switch (a.ndim) {
+        case 2: k_sample_coords<2><<<blocks, threads, 0, st>>>(a); break;
+        case 3: k_sample_coords<3><<<blocks, threads, 0, st>>>(a); break;
+        case 4: k_sample_coords<4><<<blocks, threads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sgcp

@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and the ctypes structs have the C layout (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sgcp.h")
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_2110_14514_gb300 import build as b
+    b.build()
+    import paper_2110_14514_gb300 as sg
+    return sg
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgcp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_functions_are_exported(sg):
+    names = declared_functions()
+    assert "sgcp_gradient" in names and "sgcp_step" in names and len(names) >= 17
+    lib = ctypes.CDLL(sg.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    bound = {n for n, _, _ in sg.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_struct_layout_matches_c(sg, tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "sgcp.h"\n'
+        "int main(void){\n"
+        'printf("%zu %zu %zu %zu\\n", sizeof(sgcp_params), sizeof(sgcp_slice), sizeof(sgcp_grad_opts), sizeof(sgcp_stats_t));\n'
+        'printf("%zu %zu %zu %zu %zu\\n", offsetof(sgcp_params, lambda), offsetof(sgcp_params, p_obj), '
+        "offsetof(sgcp_params, zero_attempt_cap), offsetof(sgcp_params, seed), offsetof(sgcp_stats_t, kernels_launched));\n"
+        "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(x) for x in out]
+    assert sizes[:4] == [ctypes.sizeof(sg.sgcp_params), ctypes.sizeof(sg.sgcp_slice),
+                         ctypes.sizeof(sg.sgcp_grad_opts), ctypes.sizeof(sg.sgcp_stats_t)]
+    assert sizes[4:] == [sg.sgcp_params.lambda_.offset, sg.sgcp_params.p_obj.offset,
+                         sg.sgcp_params.zero_attempt_cap.offset, sg.sgcp_params.seed.offset,
+                         sg.sgcp_stats_t.kernels_launched.offset]
+
+
+def test_defaults_follow_table_2(sg):
+    p = sg.params((10, 20, 30), 8)
+    assert (p.beta1, p.beta2, p.adam_eps, p.tau_w, p.tau_f, p.theta, p.lambda_, p.mu) == \
+        (0.9, 0.999, 1e-8, 100, 100, 1.0, 0.0, 0.0)
+    assert p.tol_w == float("-inf") and p.zero_attempt_cap == 64
+
+
+def test_argument_errors_are_synchronous_without_a_gpu(sg):
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 3)()
+    bad = sg.params((10, 20, 30), 6)           # rank not a multiple of 4
+    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_UNSUPPORTED
+    bad = sg.params((10, 20, 30, 4, 5)[:4], 8, precision=sg.PREC_BF16_MTTKRP)
+    bad.ndim = 5
+    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_UNSUPPORTED
+    bad = sg.params((10, 20, 30), 8, "poisson", temporal=sg.TEMPORAL_LSQ)
+    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, ctypes.byref(out)) in (sg.ERR_ARG, sg.ERR_CUDA)
+    assert sg.sgcp_create(None, arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_ARG
+    assert sg.sgcp_status_string(sg.ERR_SAMPLING_LIMIT) == b"SGCP_ERR_SAMPLING_LIMIT"
+    assert sg.sgcp_params_default(None) == sg.ERR_ARG
+
+
+def test_no_cpu_fallback_when_cuda_is_missing(sg):
+    """Without a device the library refuses to create a context (it never computes on the host)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 3)()
+    p = sg.params((10, 20, 30), 8)
+    assert sg.sgcp_create(ctypes.byref(p), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_CUDA

@@ -1,0 +1,159 @@
+"""GPU parity of the whole OnlineGCP step (Alg. 1 body: temporal solve, factor
+solve with history, reservoir update) against the oracle, teacher-forced on
+the per-epoch accept/reject decisions the GPU took."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synthetic as S
+from oracle import gcp, solver
+
+
+@pytest.fixture(scope="module")
+def sg():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2110_14514_gb300 as sg
+    return sg
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def bits(mask, n):
+    return [bool((mask >> e) & 1) for e in range(n)]
+
+
+def oracle_params(P, **kw):
+    return solver.Params(**kw)
+
+
+def run_stream(sg, p, A0, slices, okw, tol, check_own=False):
+    ctx = sg.Context(p, [dev(a) for a in A0])
+    og = solver.OnlineGCP(solver.Params(**okw), [a.astype(np.float64) for a in A0])
+    try:
+        for t, X in enumerate(slices, start=1):
+            if "X" in X:
+                ctx.step(X=dev(X["X"]))
+                Xo = solver.Slice(dims=okw["dims"], X=X["X"])
+            else:
+                ctx.step(idx=dev(X["idx"]), vals=dev(X["val"]))
+                Xo = solver.Slice(dims=okw["dims"], idx=X["idx"], val=X["val"])
+            st = ctx.stats()
+            assert st["error_bits"] == 0 and st["t"] == t
+            dw = bits(st["accept_w"], st["epochs_w"]) if okw.get("temporal", "adam") == "adam" else []
+            df = bits(st["accept_f"], st["epochs_f"])
+            lw, lf = len(og.log_w), len(og.log_f)
+            out = og.step(Xo, decisions_w=iter(dw), decisions_f=iter(df))
+            if check_own:
+                assert [e["own"] for e in og.log_w[lw:]] == dw
+                assert [e["own"] for e in og.log_f[lf:]] == df
+            A, s, tt = ctx.factors()
+            assert tt == t
+            assert rel(s.cpu().numpy(), out["s"]) < tol, ("s", t, rel(s.cpu().numpy(), out["s"]))
+            for k in range(len(A0)):
+                assert rel(A[k].cpu().numpy(), og.Abar[k]) < tol, ("A", t, k, rel(A[k].cpu().numpy(), og.Abar[k]))
+            assert abs(st["F_f"] - out["F_f"]) <= tol * max(abs(out["F_f"]), 1.0), (st["F_f"], out["F_f"])
+            if out["F_w"] is not None:
+                assert abs(st["F_w"] - out["F_w"]) <= tol * max(abs(out["F_w"]), 1.0), (st["F_w"], out["F_w"])
+            assert st["iter"] == og.i
+            h, sh = ctx.history()
+            assert h == og.hist_t
+            if h:
+                assert rel(sh.cpu().numpy(), np.array(og.hist_s)) < tol
+    finally:
+        ctx.close()
+    return ctx
+
+
+def test_dense_2way_fp64_stream_matches_oracle(sg):
+    """The 20 x 30, R = 4, Gaussian FP64 stream with a history window of 3 over 6 slices:
+    FP64 on both sides, so the GPU's own accept/reject decisions must equal the oracle's."""
+    cfg = S.workload("dense_gaussian_2way")
+    A0 = S.init_factors(cfg)
+    slices = [{"X": S.dense_slice(cfg, t)[0]} for t in range(1, 7)]
+    kw = dict(H=3, w=1.0, theta=0.9, kappa_w=3, tau_w=8, alpha_w=0.05, kappa_f=3, tau_f=8, alpha_f=0.01, seed=77)
+    p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=sg.PREC_F64, **kw)
+    okw = dict(dims=cfg["dims"], rank=cfg["rank"], loss="gaussian", **kw)
+    run_stream(sg, p, A0, slices, okw, tol=1e-9, check_own=True)
+
+
+def test_dense_2way_lsq_temporal_fp64(sg):
+    cfg = S.workload("dense_gaussian_2way")
+    A0 = S.init_factors(cfg)
+    slices = [{"X": S.dense_slice(cfg, t)[0]} for t in range(1, 5)]
+    kw = dict(H=2, kappa_f=2, tau_f=6, alpha_f=0.01, lam=0.1, mu=0.2, seed=3)
+    p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=sg.PREC_F64, temporal=sg.TEMPORAL_LSQ, **kw)
+    okw = dict(dims=cfg["dims"], rank=cfg["rank"], loss="gaussian", temporal="lsq", **kw)
+    run_stream(sg, p, A0, slices, okw, tol=1e-9, check_own=True)
+
+
+def test_dense_3way_fp32_poisson_stream(sg):
+    dims, R = (30, 25, 20), 8
+    rng = np.random.default_rng(1)
+    At = [rng.random((n, R)) for n in dims]
+    A0 = [(a + 0.1 * rng.random(a.shape)).astype(np.float32) for a in At]
+    slices = []
+    for t in range(4):
+        st = rng.random(R)
+        M = np.einsum("ir,jr,kr,r->ijk", *At, st)
+        slices.append({"X": rng.poisson(M).astype(np.float32)})
+    kw = dict(H=2, w=2.0, kappa_w=2, tau_w=10, alpha_w=0.05, kappa_f=2, tau_f=10, alpha_f=0.005, seed=5)
+    p = sg.params(dims, R, "poisson", **kw)
+    okw = dict(dims=dims, rank=R, loss="poisson", **kw)
+    run_stream(sg, p, A0, slices, okw, tol=2e-4)
+
+
+@pytest.mark.parametrize("loss", ["bernoulli_logit", "poisson"])
+def test_sparse_stream_matches_oracle(sg, loss):
+    dims, R = (120, 90, 60), 8
+    cfg = S.workload("sparse_binary_zipf")
+    rng = np.random.default_rng(2)
+    A0 = [(0.3 * rng.random((n, R)) + 0.05).astype(np.float32) for n in dims]
+    slices = []
+    for t in range(1, 5):
+        idx, val = S.sparse_slice(cfg, t, nnz=4000, dims=dims)
+        slices.append({"idx": idx, "val": val})
+    kw = dict(H=2, w=1.0, kappa_w=2, tau_w=6, alpha_w=0.05, kappa_f=2, tau_f=6, alpha_f=0.01,
+              p=800, q=800, p_obj=1500, q_obj=1500, seed=99)
+    p = sg.params(dims, R, loss, **kw)
+    okw = dict(dims=dims, rank=R, loss=loss, **kw)
+    run_stream(sg, p, A0, slices, okw, tol=2e-4)
+
+
+def test_checkpoint_resume_continues_the_trajectory(sg):
+    cfg = S.workload("dense_gaussian_2way")
+    A0 = S.init_factors(cfg)
+    slices = [S.dense_slice(cfg, t)[0] for t in range(1, 6)]
+    kw = dict(H=2, kappa_w=2, tau_w=5, alpha_w=0.05, kappa_f=2, tau_f=5, alpha_f=0.01, seed=12)
+    p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=sg.PREC_F64, **kw)
+    with sg.Context(p, [dev(a) for a in A0]) as full:
+        for X in slices:
+            full.step(X=dev(X))
+        Af, sf, tf = full.factors()
+        stf = full.stats()
+    with sg.Context(p, [dev(a) for a in A0]) as first:
+        for X in slices[:3]:
+            first.step(X=dev(X))
+        blob = first.state_export()
+    with sg.Context(p, [dev(a) for a in A0]) as resumed:
+        resumed.state_import(blob)
+        for X in slices[3:]:
+            resumed.step(X=dev(X))
+        Ar, sr, tr = resumed.factors()
+        st = resumed.stats()
+    assert tr == tf == 5 and st["iter"] == stf["iter"]
+    for a, b in zip(Ar, Af):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
+    assert rel(sr.cpu().numpy(), sf.cpu().numpy()) < 1e-12
