@@ -35,7 +35,7 @@
  *  - One context must be used by one host thread at a time.
  *
  * Limits: 2 <= ndim <= 4; rank R a multiple of 4 with 4 <= R <= 128; dense
- * slices need ndim <= 3; coordinates fit int32; the product of the
+ * slices need ndim <= 3; I_k * R < 2^31 for every mode; the product of the
  * dimensions fits in 63 bits.
  */
 #ifndef SGCP_H
@@ -112,6 +112,9 @@ typedef struct {
     int32_t optimizer;        /* sgcp_optimizer */
     int32_t lbfgs_mem;        /* L-BFGS memory */
     int32_t lbfgs_iters;      /* L-BFGS iterations per slice */
+    int32_t sparse_cpl;       /* tuning: factor columns per lane in the sparse kernel (4, 8, 16; 0 = auto) */
+    int32_t hot_rows;         /* tuning: rows per mode accumulated in shared memory by the sparse kernel
+                                 (0..64; -1 = 16); results do not depend on it */
     uint64_t seed;            /* Philox4x32-10 key for every random draw */
 } sgcp_params;
 

@@ -8,7 +8,7 @@ device pointers and CUDA stream it passes to the library.
 
 There is no CPU fallback.  Importing this package loads the shared library
 and raises ``ImportError`` if it has not been built
-(``python -m paper_2110_14514_gb300.build``).
+(``python paper_2110_14514_gb300/build.py``).
 """
 import ctypes
 import math
@@ -39,7 +39,7 @@ class sgcp_params(ctypes.Structure):
         ("tau_w", c_int32), ("tau_f", c_int32), ("alpha_w", c_double), ("alpha_f", c_double),
         ("beta1", c_double), ("beta2", c_double), ("adam_eps", c_double), ("alpha_decay", c_double),
         ("zero_attempt_cap", c_int32), ("optimizer", c_int32), ("lbfgs_mem", c_int32), ("lbfgs_iters", c_int32),
-        ("seed", c_uint64),
+        ("sparse_cpl", c_int32), ("hot_rows", c_int32), ("seed", c_uint64),
     ]
 
 
@@ -89,7 +89,7 @@ SIGNATURES = [
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libsgcp.so is not built ({LIB_PATH}); run python -m paper_2110_14514_gb300.build")
+        raise ImportError(f"libsgcp.so is not built ({LIB_PATH}); run python paper_2110_14514_gb300/build.py")
     lib = ctypes.CDLL(LIB_PATH)
     for name, res, args in SIGNATURES:
         fn = getattr(lib, name)

@@ -3,7 +3,7 @@
 Each translation unit compiles in parallel to an object file, then nvcc links
 the shared library into ``paper_2110_14514_gb300/_build/``.  Objects are
 rebuilt only when a source or header is newer.  Usage:
-``python -m paper_2110_14514_gb300.build`` (or ``build()`` from Python).
+``python paper_2110_14514_gb300/build.py`` (or ``__graft_entry__.build()``).
 """
 import concurrent.futures as cf
 import os

@@ -44,8 +44,13 @@ struct sgcp_ctx {
     std::vector<int64_t> hist_t;
     double* SH = nullptr;
     double* grams = nullptr;     // [6][ndim][R][R]
-    float* Bc = nullptr;         // [ndim][R][R]
-    float* Cc = nullptr;
+    void* gpart = nullptr;       // Gram partial sums [6][ndim][gram_nblk][R][R], element type T
+    int gram_nblk = 1;
+    int64_t gram_rpb = 256;
+    cudaStream_t side = nullptr; // second capture stream: Gram work runs beside the gradient kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    void* Bc = nullptr;          // [ndim][R][R], element type T
+    void* Cc = nullptr;
     double* lsq_work = nullptr;  // R*R + R
     SolverState* st_w = nullptr;
     SolverState* st_f = nullptr;
@@ -281,6 +286,7 @@ SparseGradArgs sparse_args(sgcp_ctx* c, const SliceDesc* slice_dev, int set, uin
     a.y_scale = (const float*)y_scale;
     a.err = c->err;
     a.skip = skip;
+    a.cpl = c->P.sparse_cpl;
     return a;
 }
 
@@ -309,12 +315,38 @@ DenseGradArgs<T> dense_args(sgcp_ctx* c, const SliceDesc* slice_dev, int want, c
 }
 
 // Gradient launch used by both the direct entry point and the step graph.
+// Temporal-solver ADAM step fused into a temporal-gradient launch (nullptr = none).
+struct TStepSpec {
+    void *s, *u, *v;
+    SolverState* st;
+};
+
+template <typename T>
+TemporalStep<T> make_tstep(sgcp_ctx* c, const TStepSpec* ts) {
+    TemporalStep<T> t{};
+    t.s = (T*)ts->s;
+    t.u = (T*)ts->u;
+    t.v = (T*)ts->v;
+    t.st = ts->st;
+    t.mu = c->P.mu;
+    t.beta1 = c->P.beta1;
+    t.beta2 = c->P.beta2;
+    t.eps = c->P.adam_eps;
+    t.lower = c->lower;
+    return t;
+}
+
 sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_dev, int set, uint32_t draw, int want,
                              const void* s, const void* const* A, void* const* G, void* gs, double* f, int loss,
-                             const void* y_scale, const int32_t* skip, int all_nnz = 0) {
+                             const void* y_scale, const int32_t* skip, int all_nnz = 0,
+                             const TStepSpec* tstep = nullptr) {
     if (sparse) {
         SparseGradArgs a = sparse_args(c, slice_dev, set, draw, want, s, A, G, gs, f, loss, y_scale, skip);
         a.all_nnz = all_nnz;
+        if (tstep) {
+            a.tstep_on = 1;
+            a.tstep = make_tstep<float>(c, tstep);
+        }
         int64_t total;
         if (all_nnz) total = (int64_t)1 << 40;   // grid-stride over nnz (unknown when captured): full grid
         else {
@@ -324,9 +356,17 @@ sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_de
         CK(launch_sparse_grad(a, total, c->stream, &c->launches), "sparse gradient");
     } else if (c->f64) {
         DenseGradArgs<double> a = dense_args<double>(c, slice_dev, want, s, A, G, gs, f, loss, y_scale, skip);
+        if (tstep) {
+            a.tstep_on = 1;
+            a.tstep = make_tstep<double>(c, tstep);
+        }
         CK(launch_dense_grad<double>(a, c->stream, &c->launches), "dense gradient");
     } else {
         DenseGradArgs<float> a = dense_args<float>(c, slice_dev, want, s, A, G, gs, f, loss, y_scale, skip);
+        if (tstep) {
+            a.tstep_on = 1;
+            a.tstep = make_tstep<float>(c, tstep);
+        }
         CK(launch_dense_grad<float>(a, c->stream, &c->launches), "dense gradient");
     }
     return SGCP_OK;
@@ -347,7 +387,6 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
         Aptr[k] = offs(c->A, c->row_off[k] * R, esz);
         Gptr[k] = offs(c->G, c->row_off[k] * R, esz);
     }
-    const size_t gram_mode_bytes = (size_t)d * R * R * sizeof(double);
     GramArgs<T> ga{};
     ga.ndim = d;
     ga.R = R;
@@ -357,8 +396,20 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
     }
     ga.A = (const T*)c->A;
     ga.Abar = (const T*)c->Abar;
+    ga.part = (T*)c->gpart;
+    ga.nblk = c->gram_nblk;
+    ga.rows_per_block = c->gram_rpb;
     ga.out = c->grams;
     const int loss = P.loss;
+    // fork / join of the side stream inside the capture
+    auto fork = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+        return e == cudaSuccess ? cudaStreamWaitEvent(c->side, c->ev_fork, 0) : e;
+    };
+    auto join = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(c->ev_join, c->side);
+        return e == cudaSuccess ? cudaStreamWaitEvent(c->stream, c->ev_join, 0) : e;
+    };
 
     CK(launch_history_SH<T>(R, (const T*)c->s_hist, c->h_dev, c->hist_len_dev, c->slice_dev, P.w, P.theta, c->SH,
                             c->stream, &c->launches),
@@ -366,7 +417,6 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
 
     // ---------------- temporal weights (Alg. 3, or the least-squares solve) ----------------
     if (P.temporal == SGCP_TEMPORAL_LSQ) {
-        CK(cudaMemsetAsync(c->grams, 0, gram_mode_bytes, c->stream), "clear grams");
         ga.npairs = 1;
         ga.sel_u[0] = SEL_A;
         ga.sel_v[0] = SEL_A;
@@ -387,6 +437,7 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
            "adam init");
         CK(launch_solver_init(sw, P.alpha_w, 1, c->stream, &c->launches), "solver init");
         CK(cudaMemsetAsync(c->gs, 0, R * esz, c->stream), "clear gs");
+        const TStepSpec tsw{c->s, c->s_u, c->s_v, sw};
         sgcp_status st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s,
                                           Aptr, nullptr, nullptr, &sw->F_new, loss, nullptr, nullptr);
         if (st) return st;
@@ -395,18 +446,16 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
             CK(launch_epoch_begin(sw, P.tol_w, nullptr, c->stream, &c->launches), "epoch begin");
             for (int it = 0; it < P.tau_w; ++it) {
                 st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD, (uint32_t)(e * P.tau_w + it),
-                                      SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs, nullptr, loss, nullptr, skip);
+                                      SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs, nullptr, loss, nullptr, skip, 0,
+                                      &tsw);
                 if (st) return st;
-                CK(launch_temporal_adam<T>(R, (T*)c->s, (T*)c->gs, (T*)c->s_u, (T*)c->s_v, P.mu, P.beta1, P.beta2,
-                                           P.adam_eps, c->lower, sw, skip, c->stream, &c->launches),
-                   "temporal adam");
             }
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s, Aptr,
                                   nullptr, nullptr, &sw->F_new, loss, nullptr, skip);
             if (st) return st;
             CK(launch_obj_finish_w<T>(sw, (const T*)c->s, R, P.mu, 0, c->err, skip, c->stream, &c->launches), "obj");
             CK(launch_epoch_end<T>(sw, R, (T*)c->s, (T*)c->s_u, (T*)c->s_v, (T*)c->s_ao, (T*)c->s_uo, (T*)c->s_vo,
-                                   P.tau_w, P.alpha_decay, nullptr, c->stream, &c->launches),
+                                   P.tau_w, P.alpha_decay, P.beta1, P.beta2, c->stream, &c->launches),
                "epoch end");
         }
     }
@@ -417,10 +466,10 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
     const bool hist_possible = P.H > 0;
     CK(launch_solver_init(sf, P.alpha_f, 0, c->stream, &c->launches), "solver init");
     auto objective_f = [&](int set_cur, const int32_t* sk) -> sgcp_status {
+        CK(fork(), "fork");
         sgcp_status st2 = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_OBJ, 0, SGCP_WANT_LOSS, c->s,
                                            Aptr, nullptr, nullptr, &sf->F_new, loss, nullptr, sk);
         if (st2) return st2;
-        CK(cudaMemsetAsync(c->grams, 0, 6 * gram_mode_bytes, c->stream), "clear grams");
         GramArgs<T> g6 = ga;
         g6.npairs = 6;
         const int su[6] = {SEL_A, SEL_ABAR, SEL_ABAR, SEL_D, SEL_D, SEL_ABAR};
@@ -430,7 +479,8 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
             g6.sel_v[i] = sv[i];
         }
         g6.skip = sk;
-        CK(launch_gram<T>(g6, c->nrows, c->stream, &c->launches), "gram6");
+        CK(launch_gram<T>(g6, c->nrows, c->side, &c->launches), "gram6");
+        CK(join(), "join");
         CK(launch_obj_finish_f(sf, d, R, c->grams, c->SH, c->hist_len_dev, P.lambda, set_cur, c->err, sk, c->stream,
                                &c->launches),
            "obj f");
@@ -448,8 +498,8 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
     fu.G = (T*)c->G;
     fu.u = (T*)c->u;
     fu.v = (T*)c->v;
-    fu.B = hist_possible ? c->Bc : nullptr;
-    fu.C = hist_possible ? c->Cc : nullptr;
+    fu.B = hist_possible ? (const T*)c->Bc : nullptr;
+    fu.C = hist_possible ? (const T*)c->Cc : nullptr;
     fu.hist_len = c->hist_len_dev;
     fu.lam = P.lambda;
     fu.beta1 = P.beta1;
@@ -461,11 +511,12 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
     for (int e = 0; e < P.kappa_f; ++e) {
         CK(launch_epoch_begin(sf, P.tol_f, nullptr, c->stream, &c->launches), "epoch begin");
         for (int it = 0; it < P.tau_f; ++it) {
+            if (hist_possible) CK(fork(), "fork");
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
                                   SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip);
             if (st) return st;
             if (hist_possible) {
-                CK(cudaMemsetAsync(c->grams, 0, 2 * gram_mode_bytes, c->stream), "clear grams");
+                // history coefficients from the current A, beside the gradient kernel
                 GramArgs<T> g2 = ga;
                 g2.npairs = 2;
                 g2.sel_u[0] = SEL_A;
@@ -473,17 +524,18 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
                 g2.sel_u[1] = SEL_D;
                 g2.sel_v[1] = SEL_A;
                 g2.skip = skip;
-                CK(launch_gram<T>(g2, c->nrows, c->stream, &c->launches), "gram2");
-                CK(launch_hist_coeffs(d, R, c->grams, c->SH, c->hist_len_dev, c->Bc, c->Cc, skip, c->stream,
-                                      &c->launches),
+                CK(launch_gram<T>(g2, c->nrows, c->side, &c->launches), "gram2");
+                CK(launch_hist_coeffs<T>(d, R, c->grams, c->SH, c->hist_len_dev, (T*)c->Bc, (T*)c->Cc, skip,
+                                         c->side, &c->launches),
                    "hist coeffs");
+                CK(join(), "join");
             }
             CK(launch_factor_update<T>(fu, c->stream, &c->launches), "factor update");
         }
         st = objective_f(0, skip);
         if (st) return st;
         CK(launch_epoch_end<T>(sf, c->N, (T*)c->A, (T*)c->u, (T*)c->v, (T*)c->a_o, (T*)c->u_o, (T*)c->v_o, P.tau_f,
-                               P.alpha_decay, nullptr, c->stream, &c->launches),
+                               P.alpha_decay, P.beta1, P.beta2, c->stream, &c->launches),
            "epoch end");
     }
     CK(cudaMemcpyAsync(c->Abar, c->A, (size_t)c->N * esz, cudaMemcpyDeviceToDevice, c->stream), "Abar <- A");
@@ -594,6 +646,8 @@ sgcp_status sgcp_params_default(sgcp_params* p) {
     p->optimizer = SGCP_OPT_ADAM;
     p->lbfgs_mem = 5;
     p->lbfgs_iters = 10;
+    p->sparse_cpl = 0;
+    p->hot_rows = -1;
     p->seed = 0;
     return SGCP_OK;
 }
@@ -622,6 +676,9 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         omega *= (double)P.dims[k];
     }
     if (omega > 9.0e18) return SGCP_ERR_UNSUPPORTED;
+    for (int k = 0; k < P.ndim; ++k)   // row offsets are 32-bit inside the kernels
+        if ((double)P.dims[k] * P.rank >= 2147483648.0) return SGCP_ERR_UNSUPPORTED;
+    if (P.sparse_cpl != 0 && P.sparse_cpl != 4 && P.sparse_cpl != 8 && P.sparse_cpl != 16) return SGCP_ERR_ARG;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -647,6 +704,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     for (int k = c->ndim; k < 4; ++k) c->row_off[k] = c->nrows;
     c->N = c->nrows * c->R;
     c->device = dev;
+    c->nhot = P.hot_rows < 0 ? 16 : (P.hot_rows > kMaxHot ? kMaxHot : P.hot_rows);
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -661,6 +719,15 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         sgcp_destroy(c);
         return st;
     };
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(SGCP_ERR_CUDA);
+    {
+        int64_t maxI = 0;
+        for (int k = 0; k < c->ndim; ++k) maxI = c->dims[k] > maxI ? c->dims[k] : maxI;
+        gram_geometry(maxI, &c->gram_nblk, &c->gram_rpb);
+    }
     const size_t nb = (size_t)c->N * c->esz, rb = (size_t)c->R * c->esz;
     void** vecN[] = {&c->A, &c->Abar, &c->G, &c->u, &c->v, &c->u_o, &c->v_o, &c->a_o};
     for (void** p : vecN)
@@ -674,8 +741,8 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     if ((st = dalloc(c, &c->s_hist, (size_t)Hs * rb)) || (st = dalloc_t(c, &c->h_dev, Hs * sizeof(int64_t))) ||
         (st = dalloc_t(c, &c->hist_len_dev, sizeof(int32_t))) || (st = dalloc_t(c, &c->SH, RR * sizeof(double))) ||
         (st = dalloc_t(c, &c->grams, 6 * c->ndim * RR * sizeof(double))) ||
-        (st = dalloc_t(c, &c->Bc, c->ndim * RR * sizeof(float))) ||
-        (st = dalloc_t(c, &c->Cc, c->ndim * RR * sizeof(float))) ||
+        (st = dalloc(c, &c->gpart, (size_t)6 * c->ndim * c->gram_nblk * RR * c->esz)) ||
+        (st = dalloc(c, &c->Bc, c->ndim * RR * c->esz)) || (st = dalloc(c, &c->Cc, c->ndim * RR * c->esz)) ||
         (st = dalloc_t(c, &c->lsq_work, (RR + c->R) * sizeof(double))) ||
         (st = dalloc_t(c, &c->st_w, sizeof(SolverState))) || (st = dalloc_t(c, &c->st_f, sizeof(SolverState))) ||
         (st = dalloc_t(c, &c->err, sizeof(int))) || (st = dalloc_t(c, &c->slice_dev, sizeof(SliceDesc))) ||
@@ -700,11 +767,14 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, rb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->s_hist, 0, (size_t)Hs * rb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->SH, 0, RR * sizeof(double), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->st_w, 0, sizeof(SolverState), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->st_f, 0, sizeof(SolverState), s);
+    SolverState st0{};
+    st0.b1pow = 1.0;   // beta^i at i = 0
+    st0.b2pow = 1.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->st_w, &st0, sizeof(SolverState), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->st_f, &st0, sizeof(SolverState), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->Bc, 0, c->ndim * RR * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->Cc, 0, c->ndim * RR * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->Bc, 0, c->ndim * RR * c->esz, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->Cc, 0, c->ndim * RR * c->esz, s);
     std::vector<int64_t> hv(Hs, 0);
     for (int i = 0; i < n_hist; ++i) {
         if (hist_t[i] > t0) return bail(SGCP_ERR_ARG);
@@ -736,6 +806,9 @@ void sgcp_destroy(sgcp_ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -997,6 +1070,8 @@ sgcp_status sgcp_state_import(sgcp_ctx* c, const void* buf, size_t size) {
     SolverState f{};
     CK(cudaMemcpy(&f, c->st_f, sizeof(f), cudaMemcpyDeviceToHost), "import");
     f.i = (int32_t)h->iter;
+    f.b1pow = std::pow(c->P.beta1, (double)f.i);
+    f.b2pow = std::pow(c->P.beta2, (double)f.i);
     CK(cudaMemcpy(c->st_f, &f, sizeof(f), cudaMemcpyHostToDevice), "import");
     CK(cudaMemset(c->G, 0, nb), "import");
     c->t = h->t;

@@ -111,6 +111,19 @@ __device__ __forceinline__ void loss_eval(int loss, T x, T m, T eps, T& f, T& y)
     }
 }
 
+// y = df/dm alone (no loss value): the gradient kernels call this when the
+// loss is not requested, so the log / log1p of f are never evaluated.
+template <typename T>
+__device__ __forceinline__ T loss_dfdm(int loss, T x, T m, T eps) {
+    switch (loss) {
+        case LOSS_GAUSSIAN: return T(2) * (m - x);
+        case LOSS_POISSON: return T(1) - x / (m + eps);
+        case LOSS_ODDS: return T(1) / (m + T(1)) - x / (m + eps);
+        case LOSS_LOGIT: return T(1) / (T(1) + exp(-m)) - x;
+        default: return x;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Device-resident description of the slice currently loaded; kernels captured
 // in a CUDA graph read it so that one graph serves every slice.
@@ -132,9 +145,68 @@ struct SolverState {
     int32_t epoch;     // epochs run
     int32_t done;      // set once the estimate is <= tol (Alg. 3/4 loop test)
     uint32_t accept;   // bit e = epoch e accepted
-    uint32_t ticket;   // last-block counter of the row-update kernel
+    uint32_t ticket;   // last-block counter (row update, epoch end, fused temporal step)
     int32_t pad;
+    double b1pow;      // beta1^i
+    double b2pow;      // beta2^i
 };
+
+// ADAM bias-corrected learning rate for iteration i (Alg. 2 with exponent i+1):
+// alpha sqrt(1 - beta2^(i+1)) / (1 - beta1^(i+1)).
+__host__ __device__ inline double adam_rate(const SolverState& s, double beta1, double beta2) {
+    return s.alpha * sqrt(1.0 - s.b2pow * beta2) / (1.0 - s.b1pow * beta1);
+}
+
+// Parameters of the temporal-weight ADAM step fused into the last block of a
+// temporal-gradient kernel (Alg. 3: g = Z'y + mu s; Alg. 2 Step).
+template <typename T>
+struct TemporalStep {
+    T* s;
+    T* u;
+    T* v;
+    SolverState* st;
+    double mu, beta1, beta2, eps, lower;
+};
+
+// Last-block election: every block fences its global writes and takes a
+// ticket; the block that takes the last one sees all of them.
+__device__ __forceinline__ bool last_block_ticket(SolverState* st) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return last != 0;
+}
+
+// Run by all threads of the elected last block of a temporal-gradient kernel:
+// g = gs + mu s, ADAM step on s with the bias-corrected rate, gs <- 0, i <- i + 1.
+template <typename T>
+__device__ void temporal_step_tail(const TemporalStep<T>& ts, T* gs, int R) {
+    __shared__ double rate;
+    if (threadIdx.x == 0) rate = adam_rate(*ts.st, ts.beta1, ts.beta2);
+    __syncthreads();
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        const T g = __ldcg(gs + j) + (T)ts.mu * ts.s[j];
+        const T u = (T)ts.beta1 * ts.u[j] + (T)(1.0 - ts.beta1) * g;
+        const T v = (T)ts.beta2 * ts.v[j] + (T)(1.0 - ts.beta2) * g * g;
+        T sn = ts.s[j] - (T)rate * u / (sqrt(v) + (T)ts.eps);
+        if (sn < (T)ts.lower) sn = (T)ts.lower;
+        ts.u[j] = u;
+        ts.v[j] = v;
+        ts.s[j] = sn;
+        gs[j] = T(0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SolverState* st = ts.st;
+        st->i += 1;
+        st->b1pow *= ts.beta1;
+        st->b2pow *= ts.beta2;
+        st->ticket = 0u;
+        __threadfence();
+    }
+}
 
 // Hot-row privatisation limits of the sparse kernel.
 constexpr int kMaxHot = 64;

@@ -39,6 +39,9 @@ struct SparseGradArgs {
     const int32_t* skip;             // device flag: nonzero -> kernel does nothing
     int32_t* coords_out;             // sample-coordinate dump mode (nullptr otherwise)
     int32_t* attempt_out;
+    int tstep_on;                    // fuse the temporal ADAM step into the last block
+    TemporalStep<float> tstep;
+    int cpl;                         // columns per lane (4, 8, 16; 0 = default for R)
 };
 
 // Arguments of the dense fused gradient kernels (3-way tiled and the 2-way path).
@@ -59,6 +62,8 @@ struct DenseGradArgs {
     T eps;
     const T* y_scale;
     const int32_t* skip;
+    int tstep_on;            // fuse the temporal ADAM step into the last block
+    TemporalStep<T> tstep;
 };
 
 struct IngestArgs {
@@ -99,9 +104,15 @@ struct GramArgs {
     const T* Abar;
     int npairs;
     int sel_u[6], sel_v[6];
-    double* out;              // [npairs][ndim][R][R], accumulated into (zeroed by the caller)
+    T* part;                  // per-block partial sums [npairs][ndim][nblk][R][R]
+    int nblk;                 // blocks per mode (grid.x)
+    int64_t rows_per_block;   // multiple of the staging depth
+    double* out;              // [npairs][ndim][R][R] (written by launch_gram's reduce step)
     const int32_t* skip;
 };
+
+// Gram partial-sum geometry for a problem: blocks per mode and rows per block.
+void gram_geometry(int64_t max_dim, int* nblk, int64_t* rows_per_block);
 
 template <typename T>
 struct FactorUpdateArgs {
@@ -114,8 +125,8 @@ struct FactorUpdateArgs {
     T* G;
     T* u;
     T* v;
-    const float* B;           // [ndim][R][R]  (Gamma_k * S_H) or nullptr
-    const float* C;           // [ndim][R][R]  ((Gamma_k - Gammabar_k) * S_H) or nullptr
+    const T* B;               // [ndim][R][R]  (Gamma_k * S_H) or nullptr
+    const T* C;               // [ndim][R][R]  ((Gamma_k - Gammabar_k) * S_H) or nullptr
     const int32_t* hist_len;  // device: history terms apply when *hist_len > 0
     double lam;
     double beta1, beta2, eps, lower;
@@ -126,16 +137,12 @@ struct FactorUpdateArgs {
 template <typename T>
 cudaError_t launch_gram(const GramArgs<T>& a, int64_t nrows, cudaStream_t st, int64_t* launches);
 // B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H from grams [P_n = A'A, E_n = D'A].
+template <typename T>
 cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
-                               float* B, float* C, const int32_t* skip, cudaStream_t st, int64_t* launches);
+                               T* B, T* C, const int32_t* skip, cudaStream_t st, int64_t* launches);
 template <typename T>
 cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, int64_t* launches);
 
-// Temporal-weight ADAM step: g = gs + mu s; Alg. 2 Step; gs <- 0; i <- i + 1.
-template <typename T>
-cudaError_t launch_temporal_adam(int R, T* s, T* gs, T* u, T* v, double mu, double beta1, double beta2,
-                                 double eps, double lower, SolverState* st, const int32_t* skip, cudaStream_t stream,
-                                 int64_t* launches);
 
 // Solver bookkeeping.
 cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
@@ -143,7 +150,7 @@ cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter,
 cudaError_t launch_epoch_begin(SolverState* st, double tol, int32_t* skip, cudaStream_t stream, int64_t* launches);
 template <typename T>
 cudaError_t launch_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
-                             double decay, const int32_t* skip, cudaStream_t stream, int64_t* launches);
+                             double decay, double beta1, double beta2, cudaStream_t stream, int64_t* launches);
 template <typename T>
 cudaError_t launch_adam_reset(int64_t n, const T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int zero_a, T* a_zero,
                               cudaStream_t stream, int64_t* launches);

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) k_dense3(const DenseGradArgs<T> a, int n1
 #pragma unroll
         for (int c = 0; c < C::NC; ++c) g3[r][c] = T(0);
     T gsr = T(0);     // thread tid < R owns gs[tid]
-    double fsum = 0.0;
+    T fsum = T(0);    // per-thread loss partial; reduced in double below
 
     for (int t1 = 0; t1 < n1; ++t1) {
         const int64_t i1b = o1 + (int64_t)t1 * B1;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_dense3(const DenseGradArgs<T> a, int n1
                         const bool valid = i1 < I1 && i2 < I2 && i3 < I3;
                         T f, y;
                         loss_eval<T>(a.loss, Ys[row * 33 + col], m[rr][cc], a.eps, f, y);
-                        if (valid && wantF) fsum += (double)f * (double)ysc;
+                        if (valid && wantF) fsum += f * ysc;
                         Ys[row * 33 + col] = valid ? y * ysc : T(0);
                     }
             }
@@ -210,9 +210,10 @@ __global__ void __launch_bounds__(256) k_dense3(const DenseGradArgs<T> a, int n1
     }
     if (wantS && tid < R && gsr != T(0)) atomicAdd(a.gs + tid, gsr);
     if (wantF) {
+        double fd = (double)fsum;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(SGCP_FULL_MASK, fsum, off);
-        if ((tid & 31) == 0) fred[tid >> 5] = fsum;
+        for (int off = 16; off > 0; off >>= 1) fd += __shfl_xor_sync(SGCP_FULL_MASK, fd, off);
+        if ((tid & 31) == 0) fred[tid >> 5] = fd;
         __syncthreads();
         if (tid == 0) {
             double tot = 0.0;
@@ -220,6 +221,8 @@ __global__ void __launch_bounds__(256) k_dense3(const DenseGradArgs<T> a, int n1
             if (tot != 0.0) atomicAdd(a.f, tot);
         }
     }
+    // temporal solver: the last block applies the ADAM step to s (Alg. 3)
+    if (a.tstep_on && last_block_ticket(a.tstep.st)) temporal_step_tail<T>(a.tstep, a.gs, R);
 }
 
 static int dense_num_sms() {

@@ -21,15 +21,30 @@ namespace sgcp {
 
 // ---------------------------------------------------------------------------
 // Gram matrices Gram(U, V)[l][m] = sum_r U[r][l] V[r][m], U, V in {A, Abar, D}.
-// grid = (row chunks, ndim, npairs); float partials per chunk, double sums.
+// grid = (blocks per mode, ndim, npairs).  Each block writes the partial sum
+// over its rows (element type T); k_gram_reduce adds the partials in double.
+// No atomics, so results do not depend on scheduling.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T gsel(int sel, const T* A, const T* Ab, int64_t i) {
     return sel == SEL_A ? A[i] : (sel == SEL_ABAR ? Ab[i] : A[i] - Ab[i]);
 }
 
-constexpr int kGramRows = 256;   // rows per block
 constexpr int kGramStage = 32;   // rows staged in shared memory at a time
+constexpr int kGramMaxBlocks = 512;
+
+void gram_geometry(int64_t max_dim, int* nblk, int64_t* rows_per_block) {
+    int64_t rpb = 64;
+    int64_t nb = (max_dim + rpb - 1) / rpb;
+    if (nb > kGramMaxBlocks) {
+        nb = kGramMaxBlocks;
+        rpb = (max_dim + nb - 1) / nb;
+        rpb = (rpb + kGramStage - 1) / kGramStage * kGramStage;
+        nb = (max_dim + rpb - 1) / rpb;
+    }
+    *nblk = (int)(nb < 1 ? 1 : nb);
+    *rows_per_block = rpb;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
@@ -37,28 +52,28 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
     if (a.skip && *a.skip) return;
     const int k = blockIdx.y, pr = blockIdx.z, R = a.R;
     const int64_t I = a.dims[k];
-    const int64_t r0 = (int64_t)blockIdx.x * kGramRows;
+    const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_block;
     if (r0 >= I) return;
-    const int64_t r1 = min(r0 + (int64_t)kGramRows, I);
+    const int64_t r1 = min(r0 + a.rows_per_block, I);
     const T* A = a.A + a.row_off[k] * R;
     const T* Ab = a.Abar + a.row_off[k] * R;
     const int su = a.sel_u[pr], svv = a.sel_v[pr];
     T* Us = reinterpret_cast<T*>(smem_raw);          // [stage][R]
     T* Vs = Us + kGramStage * R;                      // [stage][R]
-    float* red = reinterpret_cast<float*>(Vs + kGramStage * R);   // [groups][R*R]
+    T* red = Vs + kGramStage * R;                     // [groups][R*R]
     const int tq = R / 4;                 // 4x4 output tiles per dimension
     const int tiles = tq * tq;
     const int groups = tiles >= 256 ? 1 : 256 / tiles;
     const int tid = threadIdx.x;
     const int grp = tid / (tiles < 256 ? tiles : 256);
-    float acc[4][4][4];                   // up to 4 tiles per thread (R = 128)
+    T acc[4][4][4];                       // up to 4 tiles per thread (R = 128)
     const int per = (tiles + 255) / 256;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[t][x][y] = 0.0f;
+            for (int y = 0; y < 4; ++y) acc[t][x][y] = T(0);
     for (int64_t base = r0; base < r1; base += kGramStage) {
         const int nr = (int)min((int64_t)kGramStage, r1 - base);
         __syncthreads();
@@ -68,16 +83,18 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
         }
         __syncthreads();
         if (grp < groups) {
-            for (int t = 0; t < per; ++t) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (t >= per) break;
                 const int tile = (tiles >= 256 ? tid + 256 * t : tid % tiles);
-                if (tile >= tiles || t >= 4) break;
+                if (tile >= tiles) break;
                 const int tl = tile / tq, tm = tile % tq;
                 for (int r = grp; r < nr; r += groups) {
-                    float u[4], v[4];
+                    T u[4], v[4];
 #pragma unroll
                     for (int x = 0; x < 4; ++x) {
-                        u[x] = (float)Us[r * R + tl * 4 + x];
-                        v[x] = (float)Vs[r * R + tm * 4 + x];
+                        u[x] = Us[r * R + tl * 4 + x];
+                        v[x] = Vs[r * R + tm * 4 + x];
                     }
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
@@ -88,11 +105,12 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
         }
     }
     __syncthreads();
-    // reduce the row groups in shared memory, then one double atomic per output
-    for (int i = tid; i < groups * R * R; i += blockDim.x) red[i] = 0.0f;
+    for (int i = tid; i < groups * R * R; i += blockDim.x) red[i] = T(0);
     __syncthreads();
     if (grp < groups) {
-        for (int t = 0; t < per && t < 4; ++t) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (t >= per) break;
             const int tile = (tiles >= 256 ? tid + 256 * t : tid % tiles);
             if (tile >= tiles) break;
             const int tl = tile / tq, tm = tile % tq;
@@ -103,26 +121,45 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
         }
     }
     __syncthreads();
-    double* out = a.out + ((int64_t)pr * a.ndim + k) * R * R;
+    T* out = a.part + (((int64_t)pr * a.ndim + k) * a.nblk + blockIdx.x) * R * R;
     for (int i = tid; i < R * R; i += blockDim.x) {
-        double sum = 0.0;
-        for (int g = 0; g < groups; ++g) sum += (double)red[g * R * R + i];
-        atomicAdd(out + i, sum);
+        T sum = T(0);
+        for (int g = 0; g < groups; ++g) sum += red[g * R * R + i];
+        out[i] = sum;
     }
+}
+
+// grams[p][k][i] = sum over the blocks of mode k of the partials: one warp
+// per output, lanes stride over the partials, double accumulation.
+template <typename T>
+__global__ void k_gram_reduce(const GramArgs<T> a) {
+    if (a.skip && *a.skip) return;
+    const int k = blockIdx.y, pr = blockIdx.z, RR = a.R * a.R;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= RR) return;
+    const int nb = (int)((a.dims[k] + a.rows_per_block - 1) / a.rows_per_block);
+    const T* part = a.part + ((int64_t)pr * a.ndim + k) * a.nblk * RR + i;
+    T sum = T(0);
+    for (int b = lane; b < nb; b += 32) sum += part[(int64_t)b * RR];
+    double ds = (double)sum;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ds += __shfl_xor_sync(SGCP_FULL_MASK, ds, off);
+    if (lane == 0) a.out[((int64_t)pr * a.ndim + k) * RR + i] = ds;
 }
 
 template <typename T>
 cudaError_t launch_gram(const GramArgs<T>& a, int64_t, cudaStream_t st, int64_t* launches) {
-    int64_t maxI = 0;
-    for (int k = 0; k < a.ndim; ++k) maxI = a.dims[k] > maxI ? a.dims[k] : maxI;
     const int tiles = (a.R / 4) * (a.R / 4);
     const int groups = tiles >= 256 ? 1 : 256 / tiles;
-    const size_t smem = 2 * kGramStage * a.R * sizeof(T) + (size_t)groups * a.R * a.R * sizeof(float);
+    const size_t smem = 2 * kGramStage * a.R * sizeof(T) + (size_t)groups * a.R * a.R * sizeof(T);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((unsigned)((maxI + kGramRows - 1) / kGramRows), a.ndim, a.npairs);
+    dim3 grid((unsigned)a.nblk, a.ndim, a.npairs);
     k_gram<T><<<grid, 256, smem, st>>>(a);
-    if (launches) *launches += 1;
+    dim3 rgrid((unsigned)((a.R * a.R + 7) / 8), a.ndim, a.npairs);
+    k_gram_reduce<T><<<rgrid, 256, 0, st>>>(a);
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 
@@ -130,115 +167,153 @@ cudaError_t launch_gram(const GramArgs<T>& a, int64_t, cudaStream_t st, int64_t*
 // B_k = Gamma_k * S_H and C_k = (Gamma_k - Gammabar_k) * S_H  (float outputs)
 // grams = [P (ndim x R x R) | E (ndim x R x R)], P_n = A'A, E_n = D'A.
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void k_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
-                              float* B, float* C, const int32_t* skip) {
+                              T* B, T* C, const int32_t* skip) {
     if (skip && *skip) return;
-    const int k = blockIdx.x;
     const bool on = *hist_len > 0;
+    const int RR = R * R;
     const double* P = grams;
-    const double* E = grams + (int64_t)ndim * R * R;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+    const double* E = grams + (int64_t)ndim * RR;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= RR) return;
+    T p[4], e[4];
+    for (int n = 0; n < ndim; ++n) {
+        p[n] = (T)P[n * RR + i];
+        e[n] = (T)E[n * RR + i];
+    }
+    const T sh = (T)SH[i];
+    for (int k = 0; k < ndim; ++k) {
         if (!on) {
-            B[k * R * R + i] = 0.0f;
-            C[k * R * R + i] = 0.0f;
+            B[k * RR + i] = T(0);
+            C[k * RR + i] = T(0);
             continue;
         }
-        double gam = 1.0, dgam = 0.0;
+        T gam = T(1), dgam = T(0);
         // telescoping: prod P - prod Q = sum_m (prod_{before} Q)(E_m)(prod_{after} P), Q = P - E
         for (int m = 0; m < ndim; ++m) {
             if (m == k) continue;
-            gam *= P[m * R * R + i];
-            double term = E[m * R * R + i];
+            gam *= p[m];
+            T term = e[m];
             for (int n = 0; n < ndim; ++n) {
                 if (n == k || n == m) continue;
-                term *= (n < m) ? (P[n * R * R + i] - E[n * R * R + i]) : P[n * R * R + i];
+                term *= (n < m) ? (p[n] - e[n]) : p[n];
             }
             dgam += term;
         }
-        B[k * R * R + i] = (float)(gam * SH[i]);
-        C[k * R * R + i] = (float)(dgam * SH[i]);
+        B[k * RR + i] = gam * sh;
+        C[k * RR + i] = dgam * sh;
     }
 }
 
+template <typename T>
 cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
-                               float* B, float* C, const int32_t* skip, cudaStream_t st, int64_t* launches) {
-    k_hist_coeffs<<<ndim, 256, 0, st>>>(ndim, R, grams, SH, hist_len, B, C, skip);
+                               T* B, T* C, const int32_t* skip, cudaStream_t st, int64_t* launches) {
+    k_hist_coeffs<T><<<(R * R + 127) / 128, 128, 0, st>>>(ndim, R, grams, SH, hist_len, B, C, skip);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Factor row update: g = G + lambda a + d B_k + abar C_k; ADAM step (Alg. 2)
-// with bias correction alpha sqrt(1 - b2^(i+1)) / (1 - b1^(i+1)); projection
-// a <- max(a, l); G <- 0 for the next gradient.  The last block advances i.
+// with the bias-corrected rate of iteration i; projection a <- max(a, l);
+// G <- 0 for the next gradient.  The last block advances i and beta^i.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T> a) {
+// Warp-per-row layout: LPR = min(R, 32) lanes per row, lane l holds columns
+// l, l + 32, ... of its row; the matrix-vector products with B_k, C_k take the
+// row entries by shuffle and B_k, C_k from shared memory.
+template <typename T, int VPL>
+__global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T> a, int coef_in_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double rate_s;
     if (a.skip && *a.skip) return;
-    const int R = a.R;
-    const int rows_per = blockDim.x / R;         // R divides 256 or R >= 256 handled below
-    T* dsh = reinterpret_cast<T*>(smem_raw);     // [rows_per][R]  d = a - abar
-    T* bsh = dsh + rows_per * R;                 // [rows_per][R]  abar
-    const SolverState* st = a.st;
-    const int it = st->i;
-    const double alpha = st->alpha;
-    const double bias = sqrt(1.0 - pow(a.beta2, (double)(it + 1))) / (1.0 - pow(a.beta1, (double)(it + 1)));
-    const T at = (T)(alpha * bias);
+    const int R = a.R, RR = R * R;
+    const int LPR = R < 32 ? R : 32;           // lanes per row
+    const int RPW = 32 / LPR;                  // rows per warp
     const bool hist = a.B != nullptr && *a.hist_len > 0;
-    const int rl = threadIdx.x / R, j = threadIdx.x % R;
-    const bool tact = rl < rows_per;
-    for (int64_t rb = (int64_t)blockIdx.x * rows_per; rb < a.nrows; rb += (int64_t)gridDim.x * rows_per) {
-        const int64_t row = rb + rl;
-        const bool act = tact && row < a.nrows;
-        const int64_t idx = row * R + j;
-        T av = T(0), abv = T(0);
-        if (act) {
-            av = a.A[idx];
-            abv = a.Abar[idx];
+    T* Bs = reinterpret_cast<T*>(smem_raw);    // [ndim][R][R] then C
+    if (hist && coef_in_smem) {
+        for (int i = threadIdx.x; i < a.ndim * RR; i += blockDim.x) {
+            Bs[i] = a.B[i];
+            Bs[a.ndim * RR + i] = a.C[i];
+        }
+    }
+    if (threadIdx.x == 0) rate_s = adam_rate(*a.st, a.beta1, a.beta2);
+    __syncthreads();
+    const T* Bsrc = coef_in_smem ? Bs : a.B;
+    const T* Csrc = coef_in_smem ? Bs + a.ndim * RR : a.C;
+    const T at = (T)rate_s;
+    const T b1 = (T)a.beta1, b2 = (T)a.beta2, c1 = (T)(1.0 - a.beta1), c2 = (T)(1.0 - a.beta2);
+    const T lam = (T)a.lam, eps = (T)a.eps, lower = (T)a.lower;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / LPR, l0 = lane % LPR;
+    const int64_t wglobal = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t rb = wglobal * RPW; rb < a.nrows; rb += wstride * RPW) {
+        const int64_t row = rb + sub;
+        const bool act = row < a.nrows;
+        int k = 0;
+        while (k + 1 < a.ndim && row >= a.row_off[k + 1]) ++k;
+        T av[VPL], dv[VPL], bv[VPL], g[VPL];
+#pragma unroll
+        for (int c = 0; c < VPL; ++c) {
+            const int j = l0 + 32 * c;
+            const bool on = act && j < R;
+            const int64_t idx = row * R + j;
+            av[c] = on ? a.A[idx] : T(0);
+            bv[c] = on ? a.Abar[idx] : T(0);
+            dv[c] = av[c] - bv[c];
+            g[c] = on ? a.G[idx] + lam * av[c] : T(0);
         }
         if (hist) {
-            __syncthreads();
-            if (tact) {
-                dsh[rl * R + j] = av - abv;
-                bsh[rl * R + j] = abv;
-            }
-            __syncthreads();
-        }
-        if (act) {
-            int k = 0;
-            while (k + 1 < a.ndim && row >= a.row_off[k + 1]) ++k;
-            T g = a.G[idx] + (T)a.lam * av;
-            if (hist) {
-                const float* Bk = a.B + (int64_t)k * R * R;
-                const float* Ck = a.C + (int64_t)k * R * R;
-                T sb = T(0), sc = T(0);
-                for (int l = 0; l < R; ++l) {
-                    sb += dsh[rl * R + l] * (T)__ldg(Bk + l * R + j);
-                    sc += bsh[rl * R + l] * (T)__ldg(Ck + l * R + j);
+            const T* Bk = Bsrc + (int64_t)k * RR;
+            const T* Ck = Csrc + (int64_t)k * RR;
+            T sb[VPL], sc[VPL];
+#pragma unroll
+            for (int c = 0; c < VPL; ++c) sb[c] = sc[c] = T(0);
+#pragma unroll
+            for (int lc = 0; lc < VPL; ++lc) {
+                for (int ll = 0; ll < LPR; ++ll) {
+                    const int l = ll + 32 * lc;
+                    const T dl = __shfl_sync(SGCP_FULL_MASK, dv[lc], ll, LPR);
+                    const T bl = __shfl_sync(SGCP_FULL_MASK, bv[lc], ll, LPR);
+                    if (l < R) {
+#pragma unroll
+                        for (int c = 0; c < VPL; ++c) {
+                            const int j = l0 + 32 * c;
+                            if (j < R) {
+                                sb[c] += dl * Bk[l * R + j];
+                                sc[c] += bl * Ck[l * R + j];
+                            }
+                        }
+                    }
                 }
-                g += sb + sc;
             }
-            const T u = (T)a.beta1 * a.u[idx] + (T)(1.0 - a.beta1) * g;
-            const T v = (T)a.beta2 * a.v[idx] + (T)(1.0 - a.beta2) * g * g;
-            T an = av - at * u / (sqrt(v) + (T)a.eps);
-            if (an < (T)a.lower) an = (T)a.lower;
+#pragma unroll
+            for (int c = 0; c < VPL; ++c) g[c] += sb[c] + sc[c];
+        }
+#pragma unroll
+        for (int c = 0; c < VPL; ++c) {
+            const int j = l0 + 32 * c;
+            if (!act || j >= R) continue;
+            const int64_t idx = row * R + j;
+            const T u = b1 * a.u[idx] + c1 * g[c];
+            const T v = b2 * a.v[idx] + c2 * g[c] * g[c];
+            T an = av[c] - at * u / (sqrt(v) + eps);
+            if (an < lower) an = lower;
             a.u[idx] = u;
             a.v[idx] = v;
             a.A[idx] = an;
             a.G[idx] = T(0);
         }
     }
-    // last block advances the iteration counter (every block read i above)
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (last_block_ticket(a.st) && threadIdx.x == 0) {
+        SolverState* st = a.st;
+        st->i += 1;
+        st->b1pow *= a.beta1;
+        st->b2pow *= a.beta2;
+        st->ticket = 0u;
         __threadfence();
-        const unsigned prev = atomicAdd(&a.st->ticket, 1u);
-        if (prev == gridDim.x - 1) {
-            a.st->i = it + 1;
-            a.st->ticket = 0u;
-            __threadfence();
-        }
     }
 }
 
@@ -255,48 +330,32 @@ static int solver_num_sms() {
 
 template <typename T>
 cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, int64_t* launches) {
-    const int threads = a.R <= 256 ? (256 / a.R) * a.R : 256;
-    if (a.R > 256) return cudaErrorInvalidValue;
-    const int rows_per = threads / a.R;
-    const size_t smem = 2 * (size_t)rows_per * a.R * sizeof(T);
-    int64_t want = (a.nrows + rows_per - 1) / rows_per;
-    const int64_t cap = 8LL * solver_num_sms();
-    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_factor_update<T><<<blocks, threads, smem, st>>>(a);
-    if (launches) *launches += 1;
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Temporal ADAM step on s (one block).
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_temporal_adam(int R, T* s, T* gs, T* u, T* v, double mu, double beta1, double beta2, double eps,
-                                double lower, SolverState* st, const int32_t* skip) {
-    if (skip && *skip) return;
-    const int it = st->i;
-    const double bias = sqrt(1.0 - pow(beta2, (double)(it + 1))) / (1.0 - pow(beta1, (double)(it + 1)));
-    const T at = (T)(st->alpha * bias);
-    for (int j = threadIdx.x; j < R; j += blockDim.x) {
-        const T g = gs[j] + (T)mu * s[j];
-        const T uu = (T)beta1 * u[j] + (T)(1.0 - beta1) * g;
-        const T vv = (T)beta2 * v[j] + (T)(1.0 - beta2) * g * g;
-        T sn = s[j] - at * uu / (sqrt(vv) + (T)eps);
-        if (sn < (T)lower) sn = (T)lower;
-        u[j] = uu;
-        v[j] = vv;
-        s[j] = sn;
-        gs[j] = T(0);
+    if (a.R > 128) return cudaErrorInvalidValue;
+    const int LPR = a.R < 32 ? a.R : 32;
+    const int rows_per_block = 8 * (32 / LPR);
+    size_t smem = (a.B != nullptr) ? 2 * (size_t)a.ndim * a.R * a.R * sizeof(T) : 0;
+    int in_smem = 1;
+    if (smem > 160 * 1024) {
+        smem = 0;
+        in_smem = 0;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) st->i = it + 1;
-}
-
-template <typename T>
-cudaError_t launch_temporal_adam(int R, T* s, T* gs, T* u, T* v, double mu, double beta1, double beta2, double eps,
-                                 double lower, SolverState* st, const int32_t* skip, cudaStream_t stream,
-                                 int64_t* launches) {
-    k_temporal_adam<T><<<1, 128, 0, stream>>>(R, s, gs, u, v, mu, beta1, beta2, eps, lower, st, skip);
+    int64_t want = (a.nrows + rows_per_block - 1) / rows_per_block;
+    const int64_t cap = 2LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    const int vpl = (a.R + 31) / 32;
+#define SGCP_FU(V)                                                                                          \
+    do {                                                                                                    \
+        if (smem > 48 * 1024)                                                                               \
+            cudaFuncSetAttribute(k_factor_update<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_factor_update<T, V><<<blocks, 256, smem, st>>>(a, in_smem);                                       \
+    } while (0)
+    switch (vpl) {
+        case 1: SGCP_FU(1); break;
+        case 2: SGCP_FU(2); break;
+        case 3: SGCP_FU(3); break;
+        default: SGCP_FU(4); break;
+    }
+#undef SGCP_FU
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -311,7 +370,11 @@ __global__ void k_solver_init(SolverState* st, double alpha, int reset_counter) 
     st->accept = 0u;
     st->ticket = 0u;
     st->F_new = 0.0;
-    if (reset_counter) st->i = 0;
+    if (reset_counter) {
+        st->i = 0;
+        st->b1pow = 1.0;
+        st->b2pow = 1.0;
+    }
 }
 
 cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
@@ -338,7 +401,7 @@ cudaError_t launch_epoch_begin(SolverState* st, double tol, int32_t*, cudaStream
 // Alg. 2 Update(passed) with passed = (F_new <= F_old) and F_new finite.
 template <typename T>
 __global__ void k_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
-                            double decay) {
+                            double decay, double beta1, double beta2) {
     if (st->done) return;
     const double Fn = st->F_new, Fo = st->F_old;
     const bool passed = !(Fn > Fo) && isfinite(Fn);
@@ -353,33 +416,30 @@ __global__ void k_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o
             a[i] = a_o[i];
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&st->ticket, 1u);
-        if (prev == gridDim.x - 1) {
-            if (passed) {
-                st->F_cur = Fn;
-                st->accept |= (st->epoch < 32) ? (1u << st->epoch) : 0u;
-            } else {
-                st->F_cur = Fo;
-                st->alpha *= decay;
-                st->i -= tau;
-            }
-            st->epoch += 1;
-            st->ticket = 0u;
-            __threadfence();
+    if (last_block_ticket(st) && threadIdx.x == 0) {
+        if (passed) {
+            st->F_cur = Fn;
+            st->accept |= (st->epoch < 32) ? (1u << st->epoch) : 0u;
+        } else {
+            st->F_cur = Fo;
+            st->alpha *= decay;
+            st->i -= tau;
+            st->b1pow = pow(beta1, (double)st->i);
+            st->b2pow = pow(beta2, (double)st->i);
         }
+        st->epoch += 1;
+        st->ticket = 0u;
+        __threadfence();
     }
 }
 
 template <typename T>
 cudaError_t launch_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
-                             double decay, const int32_t*, cudaStream_t stream, int64_t* launches) {
+                             double decay, double beta1, double beta2, cudaStream_t stream, int64_t* launches) {
     int64_t want = (n + 255) / 256;
     const int64_t cap = 4LL * solver_num_sms();
     const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_epoch_end<T><<<blocks, 256, 0, stream>>>(st, n, a, u, v, a_o, u_o, v_o, tau, decay);
+    k_epoch_end<T><<<blocks, 256, 0, stream>>>(st, n, a, u, v, a_o, u_o, v_o, tau, decay, beta1, beta2);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -632,11 +692,11 @@ cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, in
 
 #define SGCP_INST(T)                                                                                                  \
     template cudaError_t launch_gram<T>(const GramArgs<T>&, int64_t, cudaStream_t, int64_t*);                        \
+    template cudaError_t launch_hist_coeffs<T>(int, int, const double*, const double*, const int32_t*, T*, T*,       \
+                                               const int32_t*, cudaStream_t, int64_t*);                              \
     template cudaError_t launch_factor_update<T>(const FactorUpdateArgs<T>&, cudaStream_t, int64_t*);                \
-    template cudaError_t launch_temporal_adam<T>(int, T*, T*, T*, T*, double, double, double, double, double,        \
-                                                 SolverState*, const int32_t*, cudaStream_t, int64_t*);               \
-    template cudaError_t launch_epoch_end<T>(SolverState*, int64_t, T*, T*, T*, T*, T*, T*, int, double,             \
-                                             const int32_t*, cudaStream_t, int64_t*);                                 \
+    template cudaError_t launch_epoch_end<T>(SolverState*, int64_t, T*, T*, T*, T*, T*, T*, int, double, double,     \
+                                             double, cudaStream_t, int64_t*);                                         \
     template cudaError_t launch_adam_reset<T>(int64_t, const T*, T*, T*, T*, T*, T*, int, T*, cudaStream_t,          \
                                               int64_t*);                                                              \
     template cudaError_t launch_obj_finish_w<T>(SolverState*, const T*, int, double, int, int*, const int32_t*,      \

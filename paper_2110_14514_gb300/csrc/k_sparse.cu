@@ -119,14 +119,29 @@ __device__ __forceinline__ float4 f4mul(float4 a, float4 b) {
 }
 __device__ __forceinline__ float4 f4scale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
 
-template <int D, int RP>
-__global__ void __launch_bounds__(256) k_sparse_grad(const SparseGradArgs a) {
-    constexpr int G = RP / 4;        // lanes per sample
+// Hot-row accumulator layout: slot row of RP floats with column j of slot s
+// stored at (j + s) mod RP, so that samples with different hot slots that a
+// warp scatters in the same instruction fall in different shared-memory banks.
+__device__ __forceinline__ int hot_pos(int k, int slot, int nhot, int RP, int j) {
+    return (k * nhot + slot) * RP + ((j + slot) & (RP - 1));
+}
+
+// CPL = columns per lane (a multiple of 4): G = RP / CPL lanes share one
+// sample, SPW = 32 / G samples per warp step.  Wider lanes amortise the
+// per-sample scalar work (record load, loss derivative, reduction) over more
+// columns.
+template <int D, int RP, int CPL>
+__global__ void __launch_bounds__(256, 2) k_sparse_grad(const SparseGradArgs a) {
+    constexpr int G = RP / CPL;      // lanes per sample
     constexpr int SPW = 32 / G;      // samples per warp step
+    constexpr int NR = 32 / SPW;     // steps per chunk of 32 samples
+    constexpr int NV = CPL / 4;      // float4 per lane per row
+    constexpr int RS = (2 * D + 2 + 3) / 4 * 4;   // words per staged sample record
     extern __shared__ __align__(16) float smem[];
+    __shared__ __align__(16) int srec[8 * 32 * RS];   // 8 warps x 32 records
+    __shared__ DrawSizes zs;
     if (a.skip && *a.skip) return;
     const SliceDesc sd = a.slice ? *a.slice : a.inline_slice;
-    const DrawSizes z = draw_sizes(a, sd);
     const bool wantG = (a.want & SGCP_WANT_FACTORS) != 0;
     const bool wantS = (a.want & SGCP_WANT_TEMPORAL) != 0;
     const bool wantF = (a.want & SGCP_WANT_LOSS) != 0;
@@ -138,81 +153,135 @@ __global__ void __launch_bounds__(256) k_sparse_grad(const SparseGradArgs a) {
     double* fb = (double*)(gsb + RP);                    // [8]
     for (int i = threadIdx.x; i < D * nhot * RP + RP; i += blockDim.x) smem[i] = 0.0f;
     if (threadIdx.x < 8) fb[threadIdx.x] = 0.0;
+    if (threadIdx.x == 0) zs = draw_sizes(a, sd);        // the double divisions, once per block
     __syncthreads();
+    const DrawSizes z = zs;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
-    const int j0 = gl * 4;
-    const bool lact = j0 < R;
+    const int j0 = gl * CPL;
+    int* wrec = srec + warp * 32 * RS;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 sv = lact ? *reinterpret_cast<const float4*>(a.s + j0) : zero4;
+    float4 sv[NV];
+    bool vact[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        vact[v] = j0 + 4 * v < R;
+        sv[v] = vact[v] ? *reinterpret_cast<const float4*>(a.s + j0 + 4 * v) : zero4;
+    }
     const float ysc = a.y_scale ? *a.y_scale : 1.0f;
-    float4 gsl = zero4;
-    double fl = 0.0;
+    float4 gsl[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) gsl[v] = zero4;
+    float fl = 0.0f;        // per-lane loss partial (a few samples); reduced in double below
 
     const int64_t nchunks = (z.total + 31) / 32;
     const int wpb = blockDim.x >> 5;
-    for (int64_t ch = (int64_t)blockIdx.x * wpb + warp; ch < nchunks; ch += (int64_t)gridDim.x * wpb) {
-        int ci[D];
-        float x, w;
-        int att;
-        bool ok;
-        gen_sample<D>(a, sd, z, ch * 32 + lane, ci, x, w, att, ok);
-        int hs[D];
+    const int64_t stride = (int64_t)gridDim.x * wpb;
+    int64_t ch = (int64_t)blockIdx.x * wpb + warp;
+
+    // Software pipeline: the sample of the next chunk (Philox, COO / hash and
+    // hot-table loads) is drawn while the current chunk's rows are processed.
+    int ci[D], hs[D];
+    float x = 0.0f, w = 0.0f;
+    int att;
+    bool ok = false;
+    auto draw = [&](int64_t c) {
+        gen_sample<D>(a, sd, z, c * 32 + lane, ci, x, w, att, ok);
 #pragma unroll
         for (int k = 0; k < D; ++k) hs[k] = (nhot && ok) ? __ldg(a.hot[k] + ci[k]) : -1;
+    };
+    if (ch < nchunks) draw(ch);
 
-#pragma unroll 2
-        for (int r = 0; r < 32 / SPW; ++r) {
-            const int src = r * SPW + grp;
-            int cj[D], hj[D];
+    for (; ch < nchunks; ch += stride) {
+        // stage the 32 records of this chunk: [coords | hot slots | x | w], w == 0 marks an empty slot
+        __syncwarp();
+        {
+            int* rec = wrec + lane * RS;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                cj[k] = __shfl_sync(SGCP_FULL_MASK, ci[k], src);
-                hj[k] = __shfl_sync(SGCP_FULL_MASK, hs[k], src);
+                rec[k] = ci[k];
+                rec[D + k] = hs[k];
             }
-            const float xj = __shfl_sync(SGCP_FULL_MASK, x, src);
-            const float wj = __shfl_sync(SGCP_FULL_MASK, w, src);
-            const int okj = __shfl_sync(SGCP_FULL_MASK, (int)ok, src);
-            float4 av[D];
+            rec[2 * D] = __float_as_int(x);
+            rec[2 * D + 1] = __float_as_int(ok ? w : 0.0f);
+        }
+        __syncwarp();
+        if (ch + stride < nchunks) draw(ch + stride);
+
+#pragma unroll 1
+        for (int r = 0; r < NR; ++r) {
+            const int src = r * SPW + grp;
+            int rv[RS];
+#pragma unroll
+            for (int q = 0; q < RS / 4; ++q) {
+                const int4 v4 = *reinterpret_cast<const int4*>(wrec + src * RS + 4 * q);
+                rv[4 * q + 0] = v4.x;
+                rv[4 * q + 1] = v4.y;
+                rv[4 * q + 2] = v4.z;
+                rv[4 * q + 3] = v4.w;
+            }
+            const float xj = __int_as_float(rv[2 * D]);
+            const float wj = __int_as_float(rv[2 * D + 1]);
+            const bool okj = wj != 0.0f;
+            uint32_t off[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) off[k] = (uint32_t)rv[k] * (uint32_t)R + (uint32_t)j0;
+            float4 av[D][NV];
 #pragma unroll
             for (int k = 0; k < D; ++k)
-                av[k] = lact ? __ldg(reinterpret_cast<const float4*>(a.A[k] + (int64_t)cj[k] * R + j0)) : zero4;
-            float4 pr = sv;
 #pragma unroll
-            for (int k = 0; k < D; ++k) pr = f4mul(pr, av[k]);
-            float mp = (pr.x + pr.y) + (pr.z + pr.w);
+                for (int v = 0; v < NV; ++v)
+                    av[k][v] = vact[v] ? __ldg(reinterpret_cast<const float4*>(a.A[k] + off[k] + 4 * v)) : zero4;
+            float mp = 0.0f;
 #pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) mp += __shfl_xor_sync(SGCP_FULL_MASK, mp, off);
-            float f, y;
-            loss_eval<float>(a.loss, xj, mp, a.eps, f, y);
-            const float yw = okj ? y * wj * ysc : 0.0f;
-            if (wantF && gl == 0 && okj) fl += (double)wj * (double)f * (double)ysc;
-            if (wantS && lact) {
-                float4 t = av[0];
+            for (int v = 0; v < NV; ++v) {
+                float4 pr = sv[v];
 #pragma unroll
-                for (int k = 1; k < D; ++k) t = f4mul(t, av[k]);
-                gsl.x += yw * t.x;
-                gsl.y += yw * t.y;
-                gsl.z += yw * t.z;
-                gsl.w += yw * t.w;
+                for (int k = 0; k < D; ++k) pr = f4mul(pr, av[k][v]);
+                mp += (pr.x + pr.y) + (pr.z + pr.w);
             }
-            if (wantG && okj && lact) {
-                const float4 ys = f4scale(sv, yw);
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) mp += __shfl_xor_sync(SGCP_FULL_MASK, mp, o);
+            const float y = loss_dfdm<float>(a.loss, xj, mp, a.eps);
+            const float yw = okj ? y * wj * ysc : 0.0f;
+            if (wantF && gl == 0 && okj) {
+                float f, yy;
+                loss_eval<float>(a.loss, xj, mp, a.eps, f, yy);
+                fl += wj * f * ysc;
+            }
+            if (wantS) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    float4 t = av[0][v];
+#pragma unroll
+                    for (int k = 1; k < D; ++k) t = f4mul(t, av[k][v]);
+                    gsl[v].x += yw * t.x;
+                    gsl[v].y += yw * t.y;
+                    gsl[v].z += yw * t.z;
+                    gsl[v].w += yw * t.w;
+                }
+            }
+            if (wantG && okj) {
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    float4 c = ys;
+                    const int hj = rv[D + k];
 #pragma unroll
-                    for (int n = 0; n < D; ++n)
-                        if (n != k) c = f4mul(c, av[n]);
-                    if (hj[k] >= 0) {
-                        float* hp = hacc + (k * nhot + hj[k]) * RP + j0;
-                        atomicAdd(hp + 0, c.x);
-                        atomicAdd(hp + 1, c.y);
-                        atomicAdd(hp + 2, c.z);
-                        atomicAdd(hp + 3, c.w);
-                    } else {
-                        atomicAdd(reinterpret_cast<float4*>(a.G[k] + (int64_t)cj[k] * R + j0), c);
+                    for (int v = 0; v < NV; ++v) {
+                        if (!vact[v]) continue;
+                        float4 c = f4scale(sv[v], yw);
+#pragma unroll
+                        for (int n = 0; n < D; ++n)
+                            if (n != k) c = f4mul(c, av[n][v]);
+                        if (hj >= 0) {
+                            const int jj = j0 + 4 * v;
+                            atomicAdd(hacc + hot_pos(k, hj, nhot, RP, jj + 0), c.x);
+                            atomicAdd(hacc + hot_pos(k, hj, nhot, RP, jj + 1), c.y);
+                            atomicAdd(hacc + hot_pos(k, hj, nhot, RP, jj + 2), c.z);
+                            atomicAdd(hacc + hot_pos(k, hj, nhot, RP, jj + 3), c.w);
+                        } else {
+                            atomicAdd(reinterpret_cast<float4*>(a.G[k] + off[k] + 4 * v), c);
+                        }
                     }
                 }
             }
@@ -222,33 +291,38 @@ __global__ void __launch_bounds__(256) k_sparse_grad(const SparseGradArgs a) {
     // temporal gradient: reduce over the groups of the warp, then the block
     if (wantS) {
 #pragma unroll
-        for (int off = G; off < 32; off <<= 1) {
-            gsl.x += __shfl_xor_sync(SGCP_FULL_MASK, gsl.x, off);
-            gsl.y += __shfl_xor_sync(SGCP_FULL_MASK, gsl.y, off);
-            gsl.z += __shfl_xor_sync(SGCP_FULL_MASK, gsl.z, off);
-            gsl.w += __shfl_xor_sync(SGCP_FULL_MASK, gsl.w, off);
-        }
-        if (grp == 0 && lact) {
-            atomicAdd(gsb + j0 + 0, gsl.x);
-            atomicAdd(gsb + j0 + 1, gsl.y);
-            atomicAdd(gsb + j0 + 2, gsl.z);
-            atomicAdd(gsb + j0 + 3, gsl.w);
+        for (int v = 0; v < NV; ++v) {
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) {
+                gsl[v].x += __shfl_xor_sync(SGCP_FULL_MASK, gsl[v].x, o);
+                gsl[v].y += __shfl_xor_sync(SGCP_FULL_MASK, gsl[v].y, o);
+                gsl[v].z += __shfl_xor_sync(SGCP_FULL_MASK, gsl[v].z, o);
+                gsl[v].w += __shfl_xor_sync(SGCP_FULL_MASK, gsl[v].w, o);
+            }
+            if (grp == 0 && vact[v]) {
+                atomicAdd(gsb + j0 + 4 * v + 0, gsl[v].x);
+                atomicAdd(gsb + j0 + 4 * v + 1, gsl[v].y);
+                atomicAdd(gsb + j0 + 4 * v + 2, gsl[v].z);
+                atomicAdd(gsb + j0 + 4 * v + 3, gsl[v].w);
+            }
         }
     }
     if (wantF) {
+        double fd = (double)fl;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) fl += __shfl_xor_sync(SGCP_FULL_MASK, fl, off);
-        if (lane == 0) fb[warp] = fl;
+        for (int o = 16; o > 0; o >>= 1) fd += __shfl_xor_sync(SGCP_FULL_MASK, fd, o);
+        if (lane == 0) fb[warp] = fd;
     }
     __syncthreads();
     if (nhot) {
         for (int i = threadIdx.x; i < D * nhot * RP; i += blockDim.x) {
-            const float v = hacc[i];
+            const float val = hacc[i];
             const int k = i / (nhot * RP), rem = i - k * nhot * RP;
-            const int slot = rem / RP, j = rem - slot * RP;
-            if (v != 0.0f && j < R) {
+            const int slot = rem / RP, p = rem - slot * RP;
+            const int j = (p - slot) & (RP - 1);     // undo the column rotation
+            if (val != 0.0f && j < R) {
                 const int row = a.hot_rows[k * kMaxHot + slot];
-                if (row >= 0) atomicAdd(a.G[k] + (int64_t)row * R + j, v);
+                if (row >= 0) atomicAdd(a.G[k] + (int64_t)row * R + j, val);
             }
         }
     }
@@ -261,6 +335,8 @@ __global__ void __launch_bounds__(256) k_sparse_grad(const SparseGradArgs a) {
         for (int i = 0; i < wpb; ++i) tot += fb[i];
         if (tot != 0.0) atomicAdd(a.f, tot);
     }
+    // temporal solver: the last block applies the ADAM step to s (Alg. 3)
+    if (a.tstep_on && last_block_ticket(a.tstep.st)) temporal_step_tail<float>(a.tstep, a.gs, R);
 }
 
 template <int D>
@@ -412,7 +488,7 @@ cudaError_t launch_ingest(const IngestArgs& a, int64_t nnz, cudaStream_t st, int
     return cudaGetLastError();
 }
 
-template <int D, int RP>
+template <int D, int RP, int CPL>
 static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
     const int threads = 256;
     const int nhot = (a.want & SGCP_WANT_FACTORS) ? a.nhot : 0;
@@ -421,8 +497,8 @@ static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream
     static size_t occ_smem = 0;
     if (occ == 0 || occ_smem != smem) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_sparse_grad<D, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sparse_grad<D, RP>, threads, smem);
+            cudaFuncSetAttribute(k_sparse_grad<D, RP, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sparse_grad<D, RP, CPL>, threads, smem);
         if (occ < 1) occ = 1;
         occ_smem = smem;
     }
@@ -430,18 +506,32 @@ static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream
     int64_t want = (chunks + (threads / 32) - 1) / (threads / 32);
     const int64_t cap = (int64_t)occ * num_sms();
     const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_sparse_grad<D, RP><<<blocks, threads, smem, st>>>(a);
+    k_sparse_grad<D, RP, CPL><<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// Columns per lane: 4 when the kernel scatters factor rows (more lanes issue
+// the atomics), 8 for the gather-only temporal / loss launches; a nonzero
+// a.cpl (4, 8, 16) overrides the choice.  Defaults measured on GB300 with
+// the 10000 x 5000 x 2000, R = 32 workload.
+template <int D, int RP>
+static cudaError_t run_sparse_cpl(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
+    int cpl = a.cpl ? a.cpl : ((a.want & SGCP_WANT_FACTORS) ? 4 : (RP >= 16 ? 8 : 4));
+    if (cpl > RP) cpl = RP;
+    if (RP / cpl > 32) cpl = RP / 32;
+    if (cpl >= 16 && RP >= 16) return run_sparse<D, RP, (RP >= 16 ? 16 : 4)>(a, total, st);
+    if (cpl >= 8 && RP >= 8) return run_sparse<D, RP, (RP >= 8 ? 8 : 4)>(a, total, st);
+    return run_sparse<D, RP, (RP / 4 <= 32 ? 4 : 8)>(a, total, st);
 }
 
 template <int D>
 static cudaError_t dispatch_rank(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
-    if (a.R <= 4) return run_sparse<D, 4>(a, total, st);
-    if (a.R <= 8) return run_sparse<D, 8>(a, total, st);
-    if (a.R <= 16) return run_sparse<D, 16>(a, total, st);
-    if (a.R <= 32) return run_sparse<D, 32>(a, total, st);
-    if (a.R <= 64) return run_sparse<D, 64>(a, total, st);
-    return run_sparse<D, 128>(a, total, st);
+    if (a.R <= 4) return run_sparse_cpl<D, 4>(a, total, st);
+    if (a.R <= 8) return run_sparse_cpl<D, 8>(a, total, st);
+    if (a.R <= 16) return run_sparse_cpl<D, 16>(a, total, st);
+    if (a.R <= 32) return run_sparse_cpl<D, 32>(a, total, st);
+    if (a.R <= 64) return run_sparse_cpl<D, 64>(a, total, st);
+    return run_sparse_cpl<D, 128>(a, total, st);
 }
 
 cudaError_t launch_sparse_grad(const SparseGradArgs& a, int64_t total, cudaStream_t st, int64_t* launches) {

@@ -13,8 +13,8 @@ HEADER = os.path.join(ROOT, "include", "sgcp.h")
 
 @pytest.fixture(scope="module")
 def sg():
-    from paper_2110_14514_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2110_14514_gb300 as sg
     return sg
 

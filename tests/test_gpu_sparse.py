@@ -201,7 +201,11 @@ def test_full_size_sparse_binary_zipf_gradient(sg):
     dims, R = cfg["dims"], cfg["rank"]
     with make_ctx(sg, dims, R, cfg["loss"], A, p=cfg["p"], q=cfg["q"], p_obj=cfg["p_obj"], q_obj=cfg["q_obj"],
                   seed=2024) as ctx:
-        G, gs, f = ctx.gradient(dev(s), [dev(a) for a in A], idx=dev(idx), vals=dev(val), t=1, draw=0)
+        # factor gradient alone (the launch the factor solver makes), then temporal gradient + loss
+        G, _, _ = ctx.gradient(dev(s), [dev(a) for a in A], idx=dev(idx), vals=dev(val), t=1, draw=0,
+                               want=sg.WANT_FACTORS)
+        _, gs, f = ctx.gradient(dev(s), [dev(a) for a in A], idx=dev(idx), vals=dev(val), t=1, draw=0,
+                                want=sg.WANT_TEMPORAL | sg.WANT_LOSS)
         ctx.check()
     Go, gso, Fo = gcp.sampled_gradient(idx, val, dims, s, A, cfg["loss"], cfg["p"], cfg["q"], 2024, 1, 0)
     for k in range(3):
