@@ -225,6 +225,39 @@ sgcp_status sgcp_gradient(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, con
 sgcp_status sgcp_sample_coords(sgcp_ctx* ctx, const sgcp_slice* X, int32_t sample_set, int64_t t,
                                uint32_t draw, int32_t* coords_out, int32_t* attempt_out);
 
+/* The sparse gradient of sgcp_gradient without a context and without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library allocate device memory -- for
+ * instance a serving process that reserves its whole GPU memory budget at
+ * start-up, or a latency-critical loop where a cudaMalloc, which may
+ * synchronise the device, is not acceptable.
+ *
+ * It computes the same outputs as sgcp_gradient for a sparse slice (same
+ * Philox sample draw, same weights), from: params (ndim, dims, rank, loss,
+ * log_eps, p, q, p_obj, q_obj, zero_attempt_cap, sparse_cpl and seed are
+ * read; precision must not be SGCP_PREC_F64), the COO slice (device: idx
+ * [nnz][ndim] int32, vals [nnz] float), s (device, R floats), A (host array
+ * of ndim device pointers to I_k x R float matrices), opts, and the outputs
+ * G_out / gs_out / f_out as in sgcp_gradient.  err_out (device int32 or
+ * NULL) is set to 0 and then receives the device error bits of this call
+ * (coordinate out of range or duplicate: 1 or 2; zero sampling exhausted: 4).
+ * Work is queued on cuda_stream (NULL = legacy default stream).
+ *
+ * Its only scratch is a fixed 4 MiB device array (2^19 hash slots) inside
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  Hence nnz is limited to 262144 (SGCP_ERR_UNSUPPORTED
+ * beyond).  The first call on each device looks up that array's device
+ * address (with the device current); make this first call before any CUDA
+ * stream capture.  All calls share the array and each clears the part it
+ * uses, so calls whose GPU work overlaps (other streams or host threads)
+ * race on it and must be serialised by the caller.  No hot-row shared-memory
+ * tables are used, so the summation order differs from sgcp_gradient's
+ * within float rounding. */
+sgcp_status sgcp_gradient_sparse_noalloc(const sgcp_params* params, int64_t nnz, const int32_t* idx,
+                                         const float* vals, const float* s, const float* const* A,
+                                         const sgcp_grad_opts* opts, float* const* G_out, float* gs_out,
+                                         double* f_out, int32_t* err_out, void* cuda_stream);
+
 /* Process the next slice: one pass of the loop body of Alg. 1 (temporal
  * solve, factor solve, reservoir history update, Abar <- A).  Asynchronous;
  * the whole solver sequence runs as CUDA graphs on the context stream. */

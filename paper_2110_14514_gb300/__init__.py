@@ -84,6 +84,9 @@ SIGNATURES = [
     ("sgcp_state_size", c_int32, [c_void_p, POINTER(c_size_t)]),
     ("sgcp_state_export", c_int32, [c_void_p, c_void_p, c_size_t]),
     ("sgcp_state_import", c_int32, [c_void_p, c_void_p, c_size_t]),
+    ("sgcp_gradient_sparse_noalloc", c_int32, [POINTER(sgcp_params), c_int64, c_void_p, c_void_p, c_void_p, _PTRS,
+                                               POINTER(sgcp_grad_opts), _PTRS, c_void_p, c_void_p, c_void_p,
+                                               c_void_p]),
 ]
 
 

@@ -85,6 +85,9 @@ struct IngestArgs {
 cudaError_t launch_ingest(const IngestArgs& a, int64_t nnz_host, cudaStream_t st, int64_t* launches);
 cudaError_t launch_sparse_grad(const SparseGradArgs& a, int64_t total_samples, cudaStream_t st, int64_t* launches);
 cudaError_t launch_sample_coords(const SparseGradArgs& a, int64_t total_samples, cudaStream_t st, int64_t* launches);
+// Hash-only ingest into a caller-provided table of 2^hlog2 slots (cleared to all ones).
+cudaError_t launch_hash_build(const SliceDesc& sd, int ndim, const int64_t* dims, unsigned long long* keys, int hlog2,
+                              int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dense_grad(const DenseGradArgs<T>& a, cudaStream_t st, int64_t* launches);
 

@@ -559,3 +559,60 @@ cudaError_t launch_sample_coords(const SparseGradArgs& a, int64_t total, cudaStr
 }
 
 }  // namespace sgcp
+
+namespace sgcp {
+
+// Hash-only slice ingest used by the no-allocation gradient entry point:
+// checks coordinates and inserts the linear keys into a caller-provided
+// table (already cleared to all ones); no row histograms.
+template <int D>
+__global__ void k_hash_build(SliceDesc sd, int64_t d0, int64_t d1, int64_t d2, int64_t d3,
+                             unsigned long long* keys, int hlog2, int* err) {
+    const int64_t dims[4] = {d0, d1, d2, d3};
+    const unsigned long long mask = (1ull << hlog2) - 1ull;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < sd.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        bool bad = false;
+        unsigned long long key = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int c = sd.idx[e * D + k];
+            if (c < 0 || (int64_t)c >= dims[k]) bad = true;
+            key = key * (unsigned long long)dims[k] + (unsigned long long)(unsigned)c;
+        }
+        if (bad) {
+            set_err(err, ERRB_COORD);
+            continue;
+        }
+        unsigned long long h = hash_home(key, hlog2);
+        for (unsigned long long probe = 0;; ++probe) {
+            if (probe > mask) {
+                set_err(err, ERRB_HASH);
+                break;
+            }
+            const unsigned long long prev = atomicCAS(keys + h, kEmpty, key);
+            if (prev == kEmpty) break;
+            if (prev == key) {
+                set_err(err, ERRB_DUP);
+                break;
+            }
+            h = (h + 1ull) & mask;
+        }
+    }
+}
+
+cudaError_t launch_hash_build(const SliceDesc& sd, int ndim, const int64_t* dims, unsigned long long* keys, int hlog2,
+                              int* err, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t want = (sd.nnz + threads - 1) / threads;
+    const int blocks = (int)(want < 1 ? 1 : (want > 8 * num_sms() ? 8 * num_sms() : want));
+    const int64_t d3 = ndim > 3 ? dims[3] : 1, d2 = ndim > 2 ? dims[2] : 1;
+    switch (ndim) {
+        case 2: k_hash_build<2><<<blocks, threads, 0, st>>>(sd, dims[0], dims[1], d2, d3, keys, hlog2, err); break;
+        case 3: k_hash_build<3><<<blocks, threads, 0, st>>>(sd, dims[0], dims[1], d2, d3, keys, hlog2, err); break;
+        case 4: k_hash_build<4><<<blocks, threads, 0, st>>>(sd, dims[0], dims[1], d2, d3, keys, hlog2, err); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sgcp
