@@ -54,6 +54,8 @@ struct sgcp_ctx {
     double* lsq_work = nullptr;  // R*R + R
     SolverState* st_w = nullptr;
     SolverState* st_f = nullptr;
+    double* rates_w = nullptr;   // per-epoch learning rates of the temporal / factor ADAM iterations
+    double* rates_f = nullptr;
     int* err = nullptr;
     SliceDesc* slice_dev = nullptr;
 
@@ -319,6 +321,7 @@ DenseGradArgs<T> dense_args(sgcp_ctx* c, const SliceDesc* slice_dev, int want, c
 struct TStepSpec {
     void *s, *u, *v;
     SolverState* st;
+    const double* rate;
 };
 
 template <typename T>
@@ -328,6 +331,7 @@ TemporalStep<T> make_tstep(sgcp_ctx* c, const TStepSpec* ts) {
     t.u = (T*)ts->u;
     t.v = (T*)ts->v;
     t.st = ts->st;
+    t.rate = ts->rate;
     t.mu = c->P.mu;
     t.beta1 = c->P.beta1;
     t.beta2 = c->P.beta2;
@@ -437,14 +441,16 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
            "adam init");
         CK(launch_solver_init(sw, P.alpha_w, 1, c->stream, &c->launches), "solver init");
         CK(cudaMemsetAsync(c->gs, 0, R * esz, c->stream), "clear gs");
-        const TStepSpec tsw{c->s, c->s_u, c->s_v, sw};
+        TStepSpec tsw{c->s, c->s_u, c->s_v, sw, c->rates_w};
         sgcp_status st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s,
                                           Aptr, nullptr, nullptr, &sw->F_new, loss, nullptr, nullptr);
         if (st) return st;
         CK(launch_obj_finish_w<T>(sw, (const T*)c->s, R, P.mu, 1, c->err, nullptr, c->stream, &c->launches), "obj");
         for (int e = 0; e < P.kappa_w; ++e) {
-            CK(launch_epoch_begin(sw, P.tol_w, nullptr, c->stream, &c->launches), "epoch begin");
+            CK(launch_epoch_begin(sw, P.tol_w, c->rates_w, P.tau_w, P.beta1, P.beta2, c->stream, &c->launches),
+               "epoch begin");
             for (int it = 0; it < P.tau_w; ++it) {
+                tsw.rate = c->rates_w + it;
                 st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD, (uint32_t)(e * P.tau_w + it),
                                       SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs, nullptr, loss, nullptr, skip, 0,
                                       &tsw);
@@ -506,11 +512,12 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
     fu.beta2 = P.beta2;
     fu.eps = P.adam_eps;
     fu.lower = c->lower;
-    fu.st = sf;
     fu.skip = skip;
     for (int e = 0; e < P.kappa_f; ++e) {
-        CK(launch_epoch_begin(sf, P.tol_f, nullptr, c->stream, &c->launches), "epoch begin");
+        CK(launch_epoch_begin(sf, P.tol_f, c->rates_f, P.tau_f, P.beta1, P.beta2, c->stream, &c->launches),
+           "epoch begin");
         for (int it = 0; it < P.tau_f; ++it) {
+            fu.rate = c->rates_f + it;
             if (hist_possible) CK(fork(), "fork");
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
                                   SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip);
@@ -745,6 +752,8 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         (st = dalloc(c, &c->Bc, c->ndim * RR * c->esz)) || (st = dalloc(c, &c->Cc, c->ndim * RR * c->esz)) ||
         (st = dalloc_t(c, &c->lsq_work, (RR + c->R) * sizeof(double))) ||
         (st = dalloc_t(c, &c->st_w, sizeof(SolverState))) || (st = dalloc_t(c, &c->st_f, sizeof(SolverState))) ||
+        (st = dalloc_t(c, &c->rates_w, (P.tau_w > 0 ? P.tau_w : 1) * sizeof(double))) ||
+        (st = dalloc_t(c, &c->rates_f, (P.tau_f > 0 ? P.tau_f : 1) * sizeof(double))) ||
         (st = dalloc_t(c, &c->err, sizeof(int))) || (st = dalloc_t(c, &c->slice_dev, sizeof(SliceDesc))) ||
         (st = dalloc_t(c, &c->counts, c->nrows * sizeof(int32_t))) ||
         (st = dalloc_t(c, &c->hot, c->nrows * sizeof(int32_t))) ||

@@ -145,16 +145,18 @@ struct SolverState {
     int32_t epoch;     // epochs run
     int32_t done;      // set once the estimate is <= tol (Alg. 3/4 loop test)
     uint32_t accept;   // bit e = epoch e accepted
-    uint32_t ticket;   // last-block counter (row update, epoch end, fused temporal step)
+    uint32_t ticket;   // last-block counter (epoch end, fused temporal step)
     int32_t pad;
-    double b1pow;      // beta1^i
+    double b1pow;      // beta1^i, i = iterations accepted before the current epoch
     double b2pow;      // beta2^i
 };
 
-// ADAM bias-corrected learning rate for iteration i (Alg. 2 with exponent i+1):
-// alpha sqrt(1 - beta2^(i+1)) / (1 - beta1^(i+1)).
-__host__ __device__ inline double adam_rate(const SolverState& s, double beta1, double beta2) {
-    return s.alpha * sqrt(1.0 - s.b2pow * beta2) / (1.0 - s.b1pow * beta1);
+// ADAM bias-corrected learning rate of iteration i + j, i.e. the j-th
+// iteration of the current epoch (Alg. 2 with exponent i + j + 1):
+// alpha sqrt(1 - beta2^(i+j+1)) / (1 - beta1^(i+j+1)).  k_epoch_begin
+// evaluates it once per epoch for every j; the per-iteration kernels read it.
+__host__ __device__ inline double adam_rate(const SolverState& s, double beta1, double beta2, int j) {
+    return s.alpha * sqrt(1.0 - s.b2pow * pow(beta2, (double)(j + 1))) / (1.0 - s.b1pow * pow(beta1, (double)(j + 1)));
 }
 
 // Parameters of the temporal-weight ADAM step fused into the last block of a
@@ -164,7 +166,8 @@ struct TemporalStep {
     T* s;
     T* u;
     T* v;
-    SolverState* st;
+    SolverState* st;      // ticket only
+    const double* rate;   // bias-corrected learning rate of this iteration
     double mu, beta1, beta2, eps, lower;
 };
 
@@ -180,12 +183,10 @@ __device__ __forceinline__ bool last_block_ticket(SolverState* st) {
 }
 
 // Run by all threads of the elected last block of a temporal-gradient kernel:
-// g = gs + mu s, ADAM step on s with the bias-corrected rate, gs <- 0, i <- i + 1.
+// g = gs + mu s, ADAM step on s with the bias-corrected rate, gs <- 0.
 template <typename T>
 __device__ void temporal_step_tail(const TemporalStep<T>& ts, T* gs, int R) {
-    __shared__ double rate;
-    if (threadIdx.x == 0) rate = adam_rate(*ts.st, ts.beta1, ts.beta2);
-    __syncthreads();
+    const double rate = *ts.rate;
     for (int j = threadIdx.x; j < R; j += blockDim.x) {
         const T g = __ldcg(gs + j) + (T)ts.mu * ts.s[j];
         const T u = (T)ts.beta1 * ts.u[j] + (T)(1.0 - ts.beta1) * g;
@@ -199,11 +200,7 @@ __device__ void temporal_step_tail(const TemporalStep<T>& ts, T* gs, int R) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        SolverState* st = ts.st;
-        st->i += 1;
-        st->b1pow *= ts.beta1;
-        st->b2pow *= ts.beta2;
-        st->ticket = 0u;
+        ts.st->ticket = 0u;
         __threadfence();
     }
 }

@@ -133,7 +133,7 @@ struct FactorUpdateArgs {
     const int32_t* hist_len;  // device: history terms apply when *hist_len > 0
     double lam;
     double beta1, beta2, eps, lower;
-    SolverState* st;
+    const double* rate;       // bias-corrected learning rate of this iteration (see k_epoch_begin)
     const int32_t* skip;
 };
 
@@ -150,7 +150,9 @@ cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, 
 // Solver bookkeeping.
 cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
                                int64_t* launches);
-cudaError_t launch_epoch_begin(SolverState* st, double tol, int32_t* skip, cudaStream_t stream, int64_t* launches);
+// Alg. 3/4 loop test and the epoch's per-iteration learning rates rates[j], j < tau.
+cudaError_t launch_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2,
+                               cudaStream_t stream, int64_t* launches);
 template <typename T>
 cudaError_t launch_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
                              double decay, double beta1, double beta2, cudaStream_t stream, int64_t* launches);

@@ -46,7 +46,7 @@ void gram_geometry(int64_t max_dim, int* nblk, int64_t* rows_per_block) {
     *rows_per_block = rpb;
 }
 
-template <typename T>
+template <typename T, int TPT>
 __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (a.skip && *a.skip) return;
@@ -63,13 +63,13 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
     T* red = Vs + kGramStage * R;                     // [groups][R*R]
     const int tq = R / 4;                 // 4x4 output tiles per dimension
     const int tiles = tq * tq;
-    const int groups = tiles >= 256 ? 1 : 256 / tiles;
+    const int tpg = tiles >= 256 ? 256 : tiles;       // threads per row group
+    const int groups = 256 / tpg;
     const int tid = threadIdx.x;
-    const int grp = tid / (tiles < 256 ? tiles : 256);
-    T acc[4][4][4];                       // up to 4 tiles per thread (R = 128)
-    const int per = (tiles + 255) / 256;
+    const int grp = tid / tpg;
+    T acc[TPT][4][4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+    for (int t = 0; t < TPT; ++t)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -84,10 +84,9 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
         __syncthreads();
         if (grp < groups) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (t >= per) break;
-                const int tile = (tiles >= 256 ? tid + 256 * t : tid % tiles);
-                if (tile >= tiles) break;
+            for (int t = 0; t < TPT; ++t) {
+                const int tile = (tiles >= 256) ? tid + 256 * t : tid % tiles;
+                if (tile >= tiles) continue;
                 const int tl = tile / tq, tm = tile % tq;
                 for (int r = grp; r < nr; r += groups) {
                     T u[4], v[4];
@@ -109,10 +108,9 @@ __global__ void __launch_bounds__(256) k_gram(const GramArgs<T> a) {
     __syncthreads();
     if (grp < groups) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (t >= per) break;
-            const int tile = (tiles >= 256 ? tid + 256 * t : tid % tiles);
-            if (tile >= tiles) break;
+        for (int t = 0; t < TPT; ++t) {
+            const int tile = (tiles >= 256) ? tid + 256 * t : tid % tiles;
+            if (tile >= tiles) continue;
             const int tl = tile / tq, tm = tile % tq;
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -153,10 +151,16 @@ cudaError_t launch_gram(const GramArgs<T>& a, int64_t, cudaStream_t st, int64_t*
     const int tiles = (a.R / 4) * (a.R / 4);
     const int groups = tiles >= 256 ? 1 : 256 / tiles;
     const size_t smem = 2 * kGramStage * a.R * sizeof(T) + (size_t)groups * a.R * a.R * sizeof(T);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((unsigned)a.nblk, a.ndim, a.npairs);
-    k_gram<T><<<grid, 256, smem, st>>>(a);
+    if (tiles <= 256) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_gram<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_gram<T, 1><<<grid, 256, smem, st>>>(a);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_gram<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_gram<T, 4><<<grid, 256, smem, st>>>(a);
+    }
     dim3 rgrid((unsigned)((a.R * a.R + 7) / 8), a.ndim, a.npairs);
     k_gram_reduce<T><<<rgrid, 256, 0, st>>>(a);
     if (launches) *launches += 2;
@@ -219,30 +223,17 @@ cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const doubl
 // with the bias-corrected rate of iteration i; projection a <- max(a, l);
 // G <- 0 for the next gradient.  The last block advances i and beta^i.
 // ---------------------------------------------------------------------------
-// Warp-per-row layout: LPR = min(R, 32) lanes per row, lane l holds columns
-// l, l + 32, ... of its row; the matrix-vector products with B_k, C_k take the
-// row entries by shuffle and B_k, C_k from shared memory.
-template <typename T, int VPL>
-__global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T> a, int coef_in_smem) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double rate_s;
+// Warp-per-row layout: LPR = min(R, 32) lanes per row (a template parameter so
+// the matrix-vector loops unroll), lane l holds columns l, l + 32, ... of its
+// row; the products with B_k, C_k take the row entries by shuffle and the
+// coefficients through L1.
+template <typename T, int LPR, int VPL>
+__global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T> a) {
     if (a.skip && *a.skip) return;
+    constexpr int RPW = 32 / LPR;              // rows per warp
     const int R = a.R, RR = R * R;
-    const int LPR = R < 32 ? R : 32;           // lanes per row
-    const int RPW = 32 / LPR;                  // rows per warp
     const bool hist = a.B != nullptr && *a.hist_len > 0;
-    T* Bs = reinterpret_cast<T*>(smem_raw);    // [ndim][R][R] then C
-    if (hist && coef_in_smem) {
-        for (int i = threadIdx.x; i < a.ndim * RR; i += blockDim.x) {
-            Bs[i] = a.B[i];
-            Bs[a.ndim * RR + i] = a.C[i];
-        }
-    }
-    if (threadIdx.x == 0) rate_s = adam_rate(*a.st, a.beta1, a.beta2);
-    __syncthreads();
-    const T* Bsrc = coef_in_smem ? Bs : a.B;
-    const T* Csrc = coef_in_smem ? Bs + a.ndim * RR : a.C;
-    const T at = (T)rate_s;
+    const T at = (T)*a.rate;
     const T b1 = (T)a.beta1, b2 = (T)a.beta2, c1 = (T)(1.0 - a.beta1), c2 = (T)(1.0 - a.beta2);
     const T lam = (T)a.lam, eps = (T)a.eps, lower = (T)a.lower;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -253,8 +244,10 @@ __global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T>
         const int64_t row = rb + sub;
         const bool act = row < a.nrows;
         int k = 0;
-        while (k + 1 < a.ndim && row >= a.row_off[k + 1]) ++k;
-        T av[VPL], dv[VPL], bv[VPL], g[VPL];
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (q < a.ndim && row >= a.row_off[q]) k = q;
+        T av[VPL], dv[VPL], bv[VPL], g[VPL], uo[VPL], vo[VPL];
 #pragma unroll
         for (int c = 0; c < VPL; ++c) {
             const int j = l0 + 32 * c;
@@ -262,17 +255,21 @@ __global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T>
             const int64_t idx = row * R + j;
             av[c] = on ? a.A[idx] : T(0);
             bv[c] = on ? a.Abar[idx] : T(0);
+            g[c] = on ? a.G[idx] : T(0);
+            uo[c] = on ? a.u[idx] : T(0);
+            vo[c] = on ? a.v[idx] : T(0);
             dv[c] = av[c] - bv[c];
-            g[c] = on ? a.G[idx] + lam * av[c] : T(0);
+            g[c] += lam * av[c];
         }
         if (hist) {
-            const T* Bk = Bsrc + (int64_t)k * RR;
-            const T* Ck = Csrc + (int64_t)k * RR;
+            const T* Bk = a.B + (int64_t)k * RR;
+            const T* Ck = a.C + (int64_t)k * RR;
             T sb[VPL], sc[VPL];
 #pragma unroll
             for (int c = 0; c < VPL; ++c) sb[c] = sc[c] = T(0);
 #pragma unroll
             for (int lc = 0; lc < VPL; ++lc) {
+#pragma unroll
                 for (int ll = 0; ll < LPR; ++ll) {
                     const int l = ll + 32 * lc;
                     const T dl = __shfl_sync(SGCP_FULL_MASK, dv[lc], ll, LPR);
@@ -282,8 +279,8 @@ __global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T>
                         for (int c = 0; c < VPL; ++c) {
                             const int j = l0 + 32 * c;
                             if (j < R) {
-                                sb[c] += dl * Bk[l * R + j];
-                                sc[c] += bl * Ck[l * R + j];
+                                sb[c] += dl * __ldg(Bk + l * R + j);
+                                sc[c] += bl * __ldg(Ck + l * R + j);
                             }
                         }
                     }
@@ -297,8 +294,8 @@ __global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T>
             const int j = l0 + 32 * c;
             if (!act || j >= R) continue;
             const int64_t idx = row * R + j;
-            const T u = b1 * a.u[idx] + c1 * g[c];
-            const T v = b2 * a.v[idx] + c2 * g[c] * g[c];
+            const T u = b1 * uo[c] + c1 * g[c];
+            const T v = b2 * vo[c] + c2 * g[c] * g[c];
             T an = av[c] - at * u / (sqrt(v) + eps);
             if (an < lower) an = lower;
             a.u[idx] = u;
@@ -306,14 +303,6 @@ __global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T>
             a.A[idx] = an;
             a.G[idx] = T(0);
         }
-    }
-    if (last_block_ticket(a.st) && threadIdx.x == 0) {
-        SolverState* st = a.st;
-        st->i += 1;
-        st->b1pow *= a.beta1;
-        st->b2pow *= a.beta2;
-        st->ticket = 0u;
-        __threadfence();
     }
 }
 
@@ -333,29 +322,17 @@ cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, 
     if (a.R > 128) return cudaErrorInvalidValue;
     const int LPR = a.R < 32 ? a.R : 32;
     const int rows_per_block = 8 * (32 / LPR);
-    size_t smem = (a.B != nullptr) ? 2 * (size_t)a.ndim * a.R * a.R * sizeof(T) : 0;
-    int in_smem = 1;
-    if (smem > 160 * 1024) {
-        smem = 0;
-        in_smem = 0;
-    }
-    int64_t want = (a.nrows + rows_per_block - 1) / rows_per_block;
-    const int64_t cap = 2LL * solver_num_sms();
-    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    // one row group per warp, every row in flight at once
+    const int64_t want = (a.nrows + rows_per_block - 1) / rows_per_block;
+    const int blocks = (int)(want < 1 ? 1 : (want > 0x7fffffff ? 0x7fffffff : want));
     const int vpl = (a.R + 31) / 32;
-#define SGCP_FU(V)                                                                                          \
-    do {                                                                                                    \
-        if (smem > 48 * 1024)                                                                               \
-            cudaFuncSetAttribute(k_factor_update<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_factor_update<T, V><<<blocks, 256, smem, st>>>(a, in_smem);                                       \
-    } while (0)
-    switch (vpl) {
-        case 1: SGCP_FU(1); break;
-        case 2: SGCP_FU(2); break;
-        case 3: SGCP_FU(3); break;
-        default: SGCP_FU(4); break;
-    }
-#undef SGCP_FU
+    if (LPR == 4) k_factor_update<T, 4, 1><<<blocks, 256, 0, st>>>(a);
+    else if (LPR == 8) k_factor_update<T, 8, 1><<<blocks, 256, 0, st>>>(a);
+    else if (LPR == 16) k_factor_update<T, 16, 1><<<blocks, 256, 0, st>>>(a);
+    else if (LPR == 32 && vpl == 1) k_factor_update<T, 32, 1><<<blocks, 256, 0, st>>>(a);
+    else if (vpl == 2) k_factor_update<T, 32, 2><<<blocks, 256, 0, st>>>(a);
+    else if (vpl == 3) k_factor_update<T, 32, 3><<<blocks, 256, 0, st>>>(a);
+    else k_factor_update<T, 32, 4><<<blocks, 256, 0, st>>>(a);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -386,14 +363,20 @@ cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter,
 
 // Alg. 3/4 loop test "while F > tol": once it fails, every later kernel of
 // the solver call is skipped through st->done.
-__global__ void k_epoch_begin(SolverState* st, double tol) {
-    if (!st->done && !(st->F_cur > tol)) st->done = 1;
-    st->F_old = st->F_cur;
-    st->F_new = 0.0;
+__global__ void k_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2) {
+    const SolverState s0 = *st;
+    for (int j = threadIdx.x; j < tau; j += blockDim.x) rates[j] = adam_rate(s0, beta1, beta2, j);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!st->done && !(st->F_cur > tol)) st->done = 1;
+        st->F_old = st->F_cur;
+        st->F_new = 0.0;
+    }
 }
 
-cudaError_t launch_epoch_begin(SolverState* st, double tol, int32_t*, cudaStream_t stream, int64_t* launches) {
-    k_epoch_begin<<<1, 1, 0, stream>>>(st, tol);
+cudaError_t launch_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2,
+                               cudaStream_t stream, int64_t* launches) {
+    k_epoch_begin<<<1, 128, 0, stream>>>(st, tol, rates, tau, beta1, beta2);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -417,15 +400,15 @@ __global__ void k_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o
         }
     }
     if (last_block_ticket(st) && threadIdx.x == 0) {
-        if (passed) {
+        if (passed) {   // the epoch's tau iterations count; a rejected epoch's are rolled back (Alg. 3/4)
             st->F_cur = Fn;
             st->accept |= (st->epoch < 32) ? (1u << st->epoch) : 0u;
+            st->i += tau;
+            st->b1pow *= pow(beta1, (double)tau);
+            st->b2pow *= pow(beta2, (double)tau);
         } else {
             st->F_cur = Fo;
             st->alpha *= decay;
-            st->i -= tau;
-            st->b1pow = pow(beta1, (double)st->i);
-            st->b2pow = pow(beta2, (double)st->i);
         }
         st->epoch += 1;
         st->ticket = 0u;
