@@ -371,7 +371,11 @@ sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_de
             a.tstep_on = 1;
             a.tstep = make_tstep<float>(c, tstep);
         }
-        CK(launch_dense_grad<float>(a, c->stream, &c->launches), "dense gradient");
+        if (c->P.precision == SGCP_PREC_BF16_MTTKRP || c->P.precision == SGCP_PREC_F16_MTTKRP)
+            CK(launch_dense_grad_tc(a, c->P.precision == SGCP_PREC_BF16_MTTKRP, c->err, c->stream, &c->launches),
+               "dense tensor-core gradient");
+        else
+            CK(launch_dense_grad<float>(a, c->stream, &c->launches), "dense gradient");
     }
     return SGCP_OK;
 }
@@ -593,6 +597,7 @@ sgcp_status check_ready(sgcp_ctx* c) {
 }
 
 sgcp_status status_from_err(int bits) {
+    if (bits & ERRB_TIMEOUT) return SGCP_ERR_TIMEOUT;
     if (bits & (ERRB_COORD | ERRB_DUP)) return SGCP_ERR_DATA;
     if (bits & ERRB_SAMPLING) return SGCP_ERR_SAMPLING_LIMIT;
     if (bits & (ERRB_NUMERIC | ERRB_SOLVE)) return SGCP_ERR_NUMERIC;
@@ -668,7 +673,9 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     if (P.rank < 4 || P.rank > 128 || P.rank % 4 != 0) return SGCP_ERR_UNSUPPORTED;
     if (P.loss < 0 || P.loss > 3) return SGCP_ERR_ARG;
     if (P.precision < 0 || P.precision > 3) return SGCP_ERR_ARG;
-    if (P.precision == SGCP_PREC_BF16_MTTKRP || P.precision == SGCP_PREC_F16_MTTKRP) return SGCP_ERR_UNSUPPORTED;
+    if ((P.precision == SGCP_PREC_BF16_MTTKRP || P.precision == SGCP_PREC_F16_MTTKRP) &&
+        (P.ndim != 3 || P.rank % 16 != 0 || P.rank > 64))
+        return SGCP_ERR_UNSUPPORTED;   // the tensor-core dense kernel covers 3-way slices, R in {16, 32, 48, 64}
     if (P.optimizer != SGCP_OPT_ADAM) return SGCP_ERR_UNSUPPORTED;
     if (P.temporal == SGCP_TEMPORAL_LSQ && P.loss != SGCP_LOSS_GAUSSIAN) return SGCP_ERR_ARG;
     if (P.H < 0 || n_hist < 0 || n_hist > P.H || (n_hist > 0 && (!hist_t || !hist_s))) return SGCP_ERR_ARG;

@@ -19,7 +19,8 @@ enum ErrBits : int {
     ERRB_SAMPLING = 4,   // a zero-sample slot exhausted its attempts
     ERRB_NUMERIC = 8,    // non-finite objective
     ERRB_HASH = 16,      // nonzero hash table full (cannot happen at load <= 1/2)
-    ERRB_SOLVE = 32      // least-squares normal matrix not positive definite
+    ERRB_SOLVE = 32,     // least-squares normal matrix not positive definite
+    ERRB_TIMEOUT = 64    // a bounded wait inside a kernel gave up
 };
 
 // Purposes of the Philox counter (high byte of counter word 3).

@@ -90,6 +90,10 @@ cudaError_t launch_hash_build(const SliceDesc& sd, int ndim, const int64_t* dims
                               int* err, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dense_grad(const DenseGradArgs<T>& a, cudaStream_t st, int64_t* launches);
+// Tensor-core (tcgen05) dense gradient, 3-way slices, R % 16 == 0 and R <= 64;
+// bf16 selects BF16 MTTKRP operands, otherwise FP16.
+cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* err, cudaStream_t st,
+                                 int64_t* launches);
 
 // ---------------------------------------------------------------------------
 // Solver kernels (k_solver.cu)
