@@ -300,6 +300,95 @@ def cpu_baseline(cfg, slice0, budget_s=15.0):
             "sample": f"{n} FP64 oracle sampled-gradient evaluations (p + q = {cfg['p'] + cfg['q']}) of one slice"}
 
 
+# ----------------------------------------------------------------------------- dense workload (precision study)
+DENSE_SOLVER = dict(H=10, w=1.0, theta=1.0, kappa_w=20, kappa_f=5, tau_w=100, tau_f=100, alpha_w=10.0, alpha_f=1e-4)
+
+
+def run_native_dense(args, cfg, world, rank, local):
+    """256^3, R = 64 Gaussian slices (Table 2 Gaussian row): per-slice update time and the dense
+    gradient kernel's roofline for the FP32 CUDA-core or the BF16 / FP16 tensor-core path."""
+    import torch
+    import paper_2110_14514_gb300 as sg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = {"fp32": sg.PREC_F32, "bf16": sg.PREC_BF16_MTTKRP, "fp16": sg.PREC_F16_MTTKRP}[args.precision]
+    p = sg.params(cfg["dims"], cfg["rank"], cfg["loss"], precision=prec, seed=2000 + rank, **DENSE_SOLVER)
+    A0 = [torch.from_numpy(a).to(dev) for a in S.init_factors(cfg, stream=rank)]
+    n_sl = 2
+    host = [S.dense_slice(cfg, t + 1, stream=rank)[0] for t in range(n_sl)]
+    dsl = [torch.from_numpy(x).to(dev) for x in host]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = sg.Context(p, A0)
+    stream = ctx.stream
+    omega = int(np.prod(cfg["dims"]))
+    grads_per_step = DENSE_SOLVER["kappa_w"] * DENSE_SOLVER["tau_w"] + DENSE_SOLVER["kappa_f"] * DENSE_SOLVER["tau_f"]
+    for w in range(args.warmup):
+        ctx.step(X=dsl[w % n_sl])
+    ctx.check()
+    k0 = ctx.stats()["kernels_launched"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        with torch.cuda.stream(stream):
+            stream.wait_stream(torch.cuda.default_stream(dev))
+            ev[k][0].record(stream)
+            ctx.step(X=dsl[(args.warmup + k) % n_sl])
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctx.check()
+    launches = ctx.stats()["kernels_launched"] - k0
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    value = world * args.steps * grads_per_step * omega / total_s
+    # dominant kernel: one factor gradient over the slice, back to back behind a sleep kernel
+    A, _, _ = ctx.factors()
+    s0 = torch.full((cfg["rank"],), 1.0, device=dev)
+    G = [torch.zeros_like(a) for a in A]
+    nrep = 50
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ctx.gradient(s0, A, X=dsl[0], want=sg.WANT_FACTORS, G=G, accumulate=True)
+        torch.cuda._sleep(50_000_000)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(nrep):
+            ctx.gradient(s0, A, X=dsl[r % n_sl], want=sg.WANT_FACTORS, G=G, accumulate=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    kern_s = e0.elapsed_time(e1) / 1e3 / nrep
+    ctx.close()
+    peak, peak_kind = peaks()
+    R = cfg["rank"]
+    bytes_alg = 4 * omega                        # X read once; factors and G are < 0.2 MB
+    flops_alg = 6 * R * omega                    # m (2R) + T = Y A3 (2R) + G3 = Y' KR (2R)
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        tflops_peak = float(d["bf16_tflops"])
+    except Exception:
+        tflops_peak = 1900.0
+    return {
+        "metric": "dense GCP gradient entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16 MTTKRP / split-bf16 model, f32 accumulate",
+                  "fp16": "f16 MTTKRP / split-bf16 model, f32 accumulate"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"dense_gaussian_3way: 256^3 slices, R=64, gaussian, noise 1% RMS",
+                   "grads_per_step": grads_per_step, "solver": DENSE_SOLVER,
+                   "l2": "flushed between steps (256 MB write)", "precision": args.precision},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": bytes_alg / kern_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": bytes_alg / kern_s / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel_us": kern_s * 1e6,
+                     "tensor_tflops": flops_alg / kern_s / 1e12, "tensor_frac_of_bf16_peak": flops_alg / kern_s / 1e12 / tflops_peak},
+        "clocks": clk,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,11 +396,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "dense_gaussian_3way"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    cfg = S.workload(WORKLOAD)
+    cfg = S.workload(args.workload)
     if args.impl == "reference":
-        out = run_reference(args, cfg, world, rank)
+        out = run_reference(args, S.workload(WORKLOAD), world, rank)
+    elif args.workload != WORKLOAD:
+        out = run_native_dense(args, cfg, world, rank, local)
     else:
         out = run_native(args, cfg, world, rank, local)
     if out is not None and rank == 0:

@@ -11,9 +11,9 @@
 //   Y  = df/dm(X, M)     FP32 from TMEM, stored as the MTTKRP operand type
 //   T  = Y . A3          -> G1, G2, gs by SIMT reductions (as the FP32 kernel)
 //   G3 += Y' . KR        accumulated in TMEM over the block's tiles
-// All shared-memory operands use the K-major no-swizzle canonical layout:
-// element (r, k) of an (rows x K) tile at (r/8)*SBO + (k/8)*128 + (r%8)*16 +
-// (k%8)*2 bytes, SBO = K/8 * 128.  A block keeps one i3 block and walks a
+// All shared-memory operands use the no-swizzle canonical layout: element
+// (r, k) of an (rows x K) tile at (r/8)*SBO + (k/8)*128 + (r%8)*16 + (k%8)*2
+// bytes, SBO = K/8 * 128; transposed uses read the same tile MN-major.  A block keeps one i3 block and walks a
 // sub-box of n1 x n2 row tiles; G1 / G2 rows accumulate in shared memory and
 // G3 in TMEM, and everything is added to global memory once per block.
 // Every wait on an mbarrier is bounded; on timeout the kernel records
@@ -33,23 +33,29 @@ constexpr int kB1 = 8, kB2 = 16;
 constexpr int kCols = 128;      // i3 columns per tile
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 256;  // D1: [0,128), T: [128, 128+R), G3: [192, 192+R)
+constexpr int kXld = 132;       // row stride (floats) of the X tile in shared memory: 16-byte aligned, conflict-free
 constexpr long kWaitLimit = 1L << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t sbo) {
+// Shared-memory matrix descriptor, no swizzle.  LBO is the byte step between
+// core matrices along K, SBO the step along M (or N); this holds for both
+// K-major and MN-major operands (checked by measurement on GB300).
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;              // LBO: K-adjacent core matrices are contiguous
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;    // SBO: distance between 8-row groups
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
     return d;
 }
 
-// kind::f16 instruction descriptor: D = f32, A = B = (bf16 ? BF16 : F16), both K-major.
-__device__ __forceinline__ uint32_t make_idesc(int M, int N, bool bf16) {
+// kind::f16 instruction descriptor: D = f32, A = B = (bf16 ? BF16 : F16);
+// a_mn / b_mn select MN-major (transposed) operands.
+__device__ __forceinline__ uint32_t make_idesc(int M, int N, bool bf16, bool a_mn, bool b_mn) {
     const uint32_t ab = bf16 ? 1u : 0u;
-    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // byte offset of element (r, k) in a K-major canonical tile with K columns
@@ -102,21 +108,27 @@ struct Op<false> {
 
 }  // namespace
 
-// Shared-memory plan (bytes), R = rank (multiple of 16, <= 64):
-//   KRhi, KRlo   [128 rows][R]  bf16          GEMM1 A (M = rows, K = j)
-//   A3hi, A3lo   [128 i3][R]    bf16          GEMM1 B (N = i3, K = j)
-//   KRT          [R][128 rows]  op type       GEMM3 B (N = j, K = rows)
-//   A3T          [R][128 i3]    op type       GEMM2 B (N = j, K = i3)
-//   Yr           [128 rows][128 i3] op type   GEMM2 A (M = rows, K = i3)
-//   Yc           [128 i3][128 rows] op type   GEMM3 A (M = i3, K = rows)
-//   A1t, A1st    [8][R] f32, A2t [16][R] f32, sv [R] f32
-//   acc1 [S1][R], acc2 [S2][R], gsacc [R] f32
+// Shared-memory plan (bytes), R = rank (multiple of 16, <= 64).  Every tile is
+// stored once, K-major canonical in its natural orientation; the GEMMs that
+// need it transposed read it through an MN-major descriptor (the core matrices
+// of a K-major (rows x K) tile are exactly the core matrices of the MN-major
+// (K x rows) view), so no transposed copies are built:
+//   KRhi, KRlo   [128 rows][R]  bf16     GEMM1 A (K-major);  GEMM3 B (MN-major, bf16 mode)
+//   KR16         [128 rows][R]  fp16     GEMM3 B (MN-major, fp16 mode)
+//   A3hi, A3lo   [128 i3][R]    bf16     GEMM1 B (K-major);  GEMM2 B (MN-major, bf16 mode)
+//   A316         [128 i3][R]    fp16     GEMM2 B (MN-major, fp16 mode)
+//   Yr           [128 rows][128 i3] op   GEMM2 A (K-major);  GEMM3 A (MN-major);
+//                                        then reused as Ts [R][128] f32 (T staged for the
+//                                        G1 / G2 / gs reductions, rows XOR-swizzled by j)
+//   Xs           [128 rows][132] f32     X tile, bulk-copied (TMA) one tile ahead
+//   A1t, A1st    [8][64], A2t [16][64], sv [64], acc1 [S1][64], acc2 [S2][64], gsacc [64]  f32
 template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_dense3_tc(const DenseGradArgs<float> a, int n1, int n2, int nb1, int nb2, int* err) {
     using OT = typename Op<BF16>::T;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_x;
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
     __shared__ double fred[8];
@@ -135,16 +147,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool wantF = (a.want & SGCP_WANT_LOSS) != 0;
     const float ysc = a.y_scale ? *a.y_scale : 1.0f;
     const float* X = reinterpret_cast<const float*>(a.slice ? a.slice->vals : a.inline_slice.vals);
+    // rows of X are 16-byte aligned: bulk copies (else plain loads)
+    const bool xtma = (I3 % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
 
     unsigned char* p = sm;
     __nv_bfloat16* KRhi = reinterpret_cast<__nv_bfloat16*>(p); p += kRows * R * 2;
     __nv_bfloat16* KRlo = reinterpret_cast<__nv_bfloat16*>(p); p += kRows * R * 2;
     __nv_bfloat16* A3hi = reinterpret_cast<__nv_bfloat16*>(p); p += kCols * R * 2;
     __nv_bfloat16* A3lo = reinterpret_cast<__nv_bfloat16*>(p); p += kCols * R * 2;
-    OT* KRT = reinterpret_cast<OT*>(p); p += R * kRows * 2;
-    OT* A3T = reinterpret_cast<OT*>(p); p += R * kCols * 2;
+    __half* KR16 = reinterpret_cast<__half*>(p); p += BF16 ? 0 : kRows * R * 2;
+    __half* A316 = reinterpret_cast<__half*>(p); p += BF16 ? 0 : kCols * R * 2;
     OT* Yr = reinterpret_cast<OT*>(p); p += kRows * kCols * 2;
-    OT* Yc = reinterpret_cast<OT*>(p); p += kCols * kRows * 2;
+    float* Ts = reinterpret_cast<float*>(Yr);                       // aliases Yr after GEMM2 / GEMM3
+    float* Xs = reinterpret_cast<float*>(p); p += kRows * kXld * 4;
     float* A1t = reinterpret_cast<float*>(p); p += kB1 * 64 * 4;
     float* A1st = reinterpret_cast<float*>(p); p += kB1 * 64 * 4;
     float* A2t = reinterpret_cast<float*>(p); p += kB2 * 64 * 4;
@@ -162,19 +177,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         abort_flag = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_x)), "r"(kRows));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     for (int j = tid; j < 64; j += kThreads) sv[j] = j < R ? a.s[j] : 0.0f;
     for (int i = tid; i < (S1 + S2 + 1) * 64; i += kThreads) acc1[i] = 0.0f;
     __syncthreads();
-    for (int i = tid; i < kCols * R; i += kThreads) {
-        const int c = i / R, j = i - c * R;
-        const float v = (o3 + c < I3) ? a.A[2][(o3 + c) * R + j] : 0.0f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const float lo = v - __bfloat162float(hi);
-        A3hi[cano(c, j, R) >> 1] = hi;
-        A3lo[cano(c, j, R) >> 1] = __float2bfloat16_rn(lo);
-        A3T[cano(j, c, kCols) >> 1] = Op<BF16>::cvt(v);
+    // A3 panel: item = (i3 row, 8 consecutive j), 16-byte stores
+    for (int i = tid; i < kCols * (R / 8); i += kThreads) {
+        const int c = i / (R / 8), j8 = (i - c * (R / 8)) * 8;
+        const bool cv = o3 + c < I3;
+        uint32_t hi[4], lo[4], h16[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float v0 = cv ? a.A[2][(o3 + c) * R + j8 + 2 * q] : 0.0f;
+            const float v1 = cv ? a.A[2][(o3 + c) * R + j8 + 2 * q + 1] : 0.0f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+            const __half2 f = __floats2half2_rn(v0, v1);
+            hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+            lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+            h16[q] = *reinterpret_cast<const uint32_t*>(&f);
+        }
+        const uint32_t off = cano(c, j8, R);
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A3hi) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A3lo) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        if (!BF16)
+            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A316) + off) = make_uint4(h16[0], h16[1], h16[2], h16[3]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -182,11 +211,37 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = tmem_holder;
     const uint32_t tD1 = tmem, tT = tmem + 128, tG3 = tmem + 192;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t id_m = make_idesc(128, kCols, true);
-    const uint32_t id_t = make_idesc(128, R, BF16);
-    uint32_t phase = 0;
+    const uint32_t id_m = make_idesc(128, kCols, true, false, false);
+    const uint32_t id_2 = make_idesc(128, R, BF16, false, true);    // A = Y K-major, B = A3 MN-major
+    const uint32_t id_3 = make_idesc(128, R, BF16, true, true);     // A = Y' MN-major, B = KR MN-major
+    const uint32_t krmt = smem_u32(BF16 ? (const void*)KRhi : (const void*)KR16);
+    const uint32_t a3mt = smem_u32(BF16 ? (const void*)A3hi : (const void*)A316);
+    uint32_t phase = 0, phase_x = 0;
+    int pending_x = 0;                        // bulk copies issued and not yet waited for (uniform)
     float fsum = 0.0f;
     int tiles_done = 0;
+    // threads 0..127: each bulk-copies its X row of tile (a1, a2) into Xs; mbar_x counts the 128
+    // arrivals and the transferred bytes
+    auto issue_x = [&](int64_t a1, int64_t a2) {
+        const int64_t ncol = (I3 - o3) < kCols ? (I3 - o3) : kCols;
+        const uint32_t rowbytes = (uint32_t)ncol * 4;
+        const int r = tid;
+        const int64_t i1 = a1 + r / kB2, i2 = a2 + r % kB2;
+        if (i1 < I1 && i2 < I2) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_x)),
+                         "r"(rowbytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(Xs + r * kXld)), "l"(X + (i1 * I2 + i2) * I3 + o3), "r"(rowbytes),
+                         "r"(smem_u32(&mbar_x))
+                         : "memory");
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mbar_x)) : "memory");
+        }
+    };
+    if (xtma && o1 < I1 && o2 < I2) {
+        if (tid < kRows) issue_x(o1, o2);
+        pending_x = 1;
+    }
 
     for (int t1 = 0; t1 < n1; ++t1) {
         const int64_t i1b = o1 + (int64_t)t1 * kB1;
@@ -195,6 +250,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t i2b = o2 + (int64_t)t2 * kB2;
             if (i2b >= I2) break;
             if (abort_flag) break;
+            // next tile of this block (for the X prefetch)
+            int64_t n1b = i1b, n2b = i2b + kB2;
+            if (t2 + 1 >= n2 || n2b >= I2) {
+                n1b = i1b + kB1;
+                n2b = o2;
+                if (t1 + 1 >= n1) n1b = I1;   // none
+            }
             // ---- factor rows of the tile and the Khatri-Rao panel KR = (s * A1) (.) A2
             for (int i = tid; i < kB1 * R; i += kThreads) {
                 const int r = i / R, j = i - r * R;
@@ -207,13 +269,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 A2t[r * 64 + j] = (i2b + r < I2) ? a.A[1][(i2b + r) * R + j] : 0.0f;
             }
             __syncthreads();
-            for (int i = tid; i < kRows * R; i += kThreads) {
-                const int r = i / R, j = i - r * R;
-                const float v = A1st[(r / kB2) * 64 + j] * A2t[(r % kB2) * 64 + j];
-                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                KRhi[cano(r, j, R) >> 1] = hi;
-                KRlo[cano(r, j, R) >> 1] = __float2bfloat16_rn(v - __bfloat162float(hi));
-                KRT[cano(j, r, kRows) >> 1] = Op<BF16>::cvt(v);
+            for (int i = tid; i < kRows * (R / 8); i += kThreads) {
+                const int r = i / (R / 8), j8 = (i - r * (R / 8)) * 8;
+                const float* a1 = A1st + (r / kB2) * 64 + j8;
+                const float* a2 = A2t + (r % kB2) * 64 + j8;
+                uint32_t hi[4], lo[4], h16[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float v0 = a1[2 * q] * a2[2 * q], v1 = a1[2 * q + 1] * a2[2 * q + 1];
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+                    const __half2 f = __floats2half2_rn(v0, v1);
+                    hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+                    lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+                    h16[q] = *reinterpret_cast<const uint32_t*>(&f);
+                }
+                const uint32_t off = cano(r, j8, R);
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KRhi) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KRlo) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                if (!BF16)
+                    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KR16) + off) =
+                        make_uint4(h16[0], h16[1], h16[2], h16[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -221,13 +297,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;");
             // ---- GEMM1: M = KR A3' in three bf16 products
             if (tid == 0) {
-                const uint32_t sboR = (uint32_t)(R / 8) * 128;
+                const uint32_t sboR = (uint32_t)R * 16;
                 const uint32_t krh = smem_u32(KRhi), krl = smem_u32(KRlo), a3h = smem_u32(A3hi), a3l = smem_u32(A3lo);
                 const uint32_t Aop[3] = {krh, krh, krl}, Bop[3] = {a3h, a3l, a3h};
                 for (int sp = 0; sp < 3; ++sp)
                     for (int kk = 0; kk < R / 16; ++kk)
-                        mma(tD1, make_desc(Aop[sp] + kk * 256, sboR), make_desc(Bop[sp] + kk * 256, sboR), id_m,
-                            (sp > 0 || kk > 0) ? 1u : 0u);
+                        mma(tD1, make_desc(Aop[sp] + kk * 256, 128, sboR), make_desc(Bop[sp] + kk * 256, 128, sboR),
+                            id_m, (sp > 0 || kk > 0) ? 1u : 0u);
                 commit(&mbar);
             }
             if (!wait_phase(&mbar, phase)) {
@@ -241,49 +317,88 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
             if (abort_flag) break;
             // ---- Y = df/dm(X, M): thread = TMEM lane (row), half = which 64 columns
+            if (xtma) {
+                if (!wait_phase(&mbar_x, phase_x)) {
+                    if (tid == 0) set_err(err, ERRB_TIMEOUT);
+                    abort_flag = 1;
+                }
+                phase_x ^= 1u;
+                pending_x = 0;
+            }
             {
                 const int r = row;
                 const int64_t i1 = i1b + r / kB2, i2 = i2b + r % kB2;
                 const bool rv = i1 < I1 && i2 < I2;
-                const float* xrow = X + (i1 * I2 + i2) * I3;
+                const float* xrow = X + (i1 * I2 + i2) * I3 + o3;
+                const float* xs = Xs + r * kXld;
 #pragma unroll 1
                 for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
-                    float m[16];
+                    float m[16], x[16];
                     tmem_ld16(tD1 + lane_base + (uint32_t)c0, m);
+                    if (xtma) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int c = c0 + q;
-                        const int64_t i3 = o3 + c;
-                        const bool valid = rv && i3 < I3;
-                        const float x = valid ? __ldg(xrow + i3) : 0.0f;
-                        float y = 0.0f;
-                        if (valid) {
-                            y = loss_dfdm<float>(a.loss, x, m[q], a.eps) * ysc;
-                            if (wantF) {
-                                float f, yy;
-                                loss_eval<float>(a.loss, x, m[q], a.eps, f, yy);
-                                fsum += f * ysc;
-                            }
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 v = *reinterpret_cast<const float4*>(xs + c0 + 4 * q);
+                            x[4 * q] = v.x;
+                            x[4 * q + 1] = v.y;
+                            x[4 * q + 2] = v.z;
+                            x[4 * q + 3] = v.w;
                         }
-                        const OT yo = Op<BF16>::cvt(y);
-                        Yr[cano(r, c, kCols) >> 1] = yo;
-                        Yc[cano(c, r, kRows) >> 1] = yo;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) x[q] = (rv && o3 + c0 + q < I3) ? __ldg(xrow + c0 + q) : 0.0f;
                     }
+                    uint32_t packed[8];
+#pragma unroll
+                    for (int q = 0; q < 16; q += 2) {
+                        float y2[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const bool valid = rv && (o3 + c0 + q + e < I3);
+                            float y = 0.0f;
+                            if (valid) {
+                                y = loss_dfdm<float>(a.loss, x[q + e], m[q + e], a.eps) * ysc;
+                                if (wantF) {
+                                    float f, yy;
+                                    loss_eval<float>(a.loss, x[q + e], m[q + e], a.eps, f, yy);
+                                    fsum += f * ysc;
+                                }
+                            }
+                            y2[e] = y;
+                        }
+                        if (BF16) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(y2[0], y2[1]);
+                            packed[q / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                        } else {
+                            const __half2 h = __floats2half2_rn(y2[0], y2[1]);
+                            packed[q / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                        }
+                    }
+                    unsigned char* yb = reinterpret_cast<unsigned char*>(Yr);
+                    *reinterpret_cast<uint4*>(yb + cano(r, c0, kCols)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    *reinterpret_cast<uint4*>(yb + cano(r, c0 + 8, kCols)) = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;");
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;");
+            if (abort_flag) break;
+            // Xs is consumed: prefetch the next tile's X behind the rest of this tile
+            if (xtma && n1b < I1 && n2b < I2) {
+                if (tid < kRows) issue_x(n1b, n2b);
+                pending_x = 1;
+            }
             // ---- GEMM2: T = Y A3 ; GEMM3: G3 += Y' KR
             if (tid == 0) {
-                const uint32_t sbo128 = (uint32_t)(kCols / 8) * 128;
-                const uint32_t yr = smem_u32(Yr), yc = smem_u32(Yc), a3t = smem_u32(A3T), krt = smem_u32(KRT);
-                for (int kk = 0; kk < kCols / 16; ++kk)
-                    mma(tT, make_desc(yr + kk * 256, sbo128), make_desc(a3t + kk * 256, sbo128), id_t, kk > 0 ? 1u : 0u);
+                const uint32_t yr = smem_u32(Yr);
+                const uint32_t ldR = (uint32_t)R * 16;      // 8-row step of an R-wide tile
+                for (int kk = 0; kk < kCols / 16; ++kk)    // K = i3
+                    mma(tT, make_desc(yr + kk * 256, 128, 2048), make_desc(a3mt + kk * 2 * ldR, ldR, 128), id_2,
+                        kk > 0 ? 1u : 0u);
                 if (wantG)
-                    for (int kk = 0; kk < kRows / 16; ++kk)
-                        mma(tG3, make_desc(yc + kk * 256, sbo128), make_desc(krt + kk * 256, sbo128), id_t,
+                    for (int kk = 0; kk < kRows / 16; ++kk)   // K = rows
+                        mma(tG3, make_desc(yr + kk * 4096, 2048, 128), make_desc(krmt + kk * 2 * ldR, ldR, 128), id_3,
                             (tiles_done > 0 || kk > 0) ? 1u : 0u);
                 commit(&mbar);
             }
@@ -298,44 +413,48 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
             if (abort_flag) break;
             ++tiles_done;
-            // ---- G1, G2, gs from T (thread = row, half = which half of the R columns)
+            // ---- T to shared memory (Ts[j][row], consecutive rows in consecutive words)
             {
-                const int r = row;
-                const int i1l = r / kB2, i2l = r % kB2;
-                // column range of this thread's half: halves split R when R % 32 == 0, else half 0 takes all
                 const int cb = (R % 32 == 0) ? (R / 2) * half : (half ? R : 0);
                 const int ce = (R % 32 == 0) ? cb + R / 2 : R;
                 for (int c0 = cb; c0 < ce; c0 += 16) {
                     float tv[16];
                     tmem_ld16(tT + lane_base + (uint32_t)c0, tv);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int j = c0 + q;
-                        const bool jv = true;
-                        const float t = tv[q];
-                        const int jj = j;
-                        float v1 = t * A2t[i2l * 64 + jj];                 // -> G1[i1] (times s_j)
-                        float v2 = t * A1st[i1l * 64 + jj];                // -> G2[i2]
-                        float v3 = t * A1t[i1l * 64 + jj] * A2t[i2l * 64 + jj];   // -> gs
-                        // sum v1 over the 16 rows (i2) sharing i1: lanes 0-15 / 16-31 of the warp
-#pragma unroll
-                        for (int o = 8; o > 0; o >>= 1) v1 += __shfl_xor_sync(SGCP_FULL_MASK, v1, o);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v3 += __shfl_xor_sync(SGCP_FULL_MASK, v3, o);
-                        if (jv) {
-                            if (wantG && (lane & 15) == 0) acc1[(t1 * kB1 + i1l) * 64 + j] += v1 * sv[j];
-                            if (wantG) atomicAdd(&acc2[(t2 * kB2 + i2l) * 64 + j], v2);
-                            if (wantS && lane == 0) atomicAdd(&gsacc[j], v3);
-                        }
-                    }
+                    for (int q = 0; q < 16; ++q) Ts[(c0 + q) * 128 + (row ^ ((c0 + q) & 31))] = tv[q];
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            // ---- G1 (and gs) over the 16 i2 rows of each i1; G2 over the 8 i1 rows of each i2
+            for (int it = tid; it < kB1 * R; it += kThreads) {
+                const int j = it % R, i1l = it / R;
+                const float* tr = Ts + j * 128;
+                const int sw = j & 31;
+                float g1 = 0.0f;
+#pragma unroll
+                for (int i2l = 0; i2l < kB2; ++i2l) g1 += A2t[i2l * 64 + j] * tr[(i1l * kB2 + i2l) ^ sw];
+                if (wantG) acc1[(t1 * kB1 + i1l) * 64 + j] += sv[j] * g1;
+                if (wantS) atomicAdd(&gsacc[j], A1t[i1l * 64 + j] * g1);
+            }
+            if (wantG) {
+                for (int it = tid; it < kB2 * R; it += kThreads) {
+                    const int j = it % R, i2l = it / R;
+                    const float* tr = Ts + j * 128;
+                    const int sw = j & 31;
+                    float g2 = 0.0f;
+#pragma unroll
+                    for (int i1l = 0; i1l < kB1; ++i1l) g2 += A1st[i1l * 64 + j] * tr[(i1l * kB2 + i2l) ^ sw];
+                    acc2[(t2 * kB2 + i2l) * 64 + j] += g2;
+                }
+            }
             __syncthreads();
         }
         if (abort_flag) break;
     }
 
+    // ---- an aborted block still lets its own bulk copy land before shared memory is released
+    if (pending_x) wait_phase(&mbar_x, phase_x);
     // ---- flush: G3 from TMEM, G1 / G2 / gs from shared memory, the loss
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (wantG && tiles_done > 0 && !abort_flag) {
@@ -402,24 +521,31 @@ cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* 
     if (a.ndim != 3 || a.R % 16 != 0 || a.R > 64) return cudaErrorInvalidValue;
     const int64_t I1 = a.dims[0], I2 = a.dims[1], I3 = a.dims[2];
     const int64_t nb3 = (I3 + kCols - 1) / kCols;
-    // sub-box of n1 x n2 tiles: as large as possible while >= one block per SM
+    const int64_t t1 = (I1 + kB1 - 1) / kB1, t2 = (I2 + kB2 - 1) / kB2;
+    // sub-box of n1 x n2 tiles: minimise (waves x tiles per block), then prefer fewer blocks
+    const int64_t sms = tc_num_sms();
     int n1 = 1, n2 = 1;
-    auto nblocks = [&](int m1, int m2) {
-        return ((I1 + kB1 * m1 - 1) / (kB1 * m1)) * ((I2 + kB2 * m2 - 1) / (kB2 * m2)) * nb3;
-    };
-    const int64_t target = tc_num_sms();
-    for (;;) {
-        bool grew = false;
-        if (n1 < 8 && kB1 * n1 < I1 && nblocks(n1 * 2, n2) >= target) { n1 *= 2; grew = true; }
-        if (n2 < 4 && kB2 * n2 < I2 && nblocks(n1, n2 * 2) >= target) { n2 *= 2; grew = true; }
-        if (!grew) break;
-    }
-    const int nb1 = (int)((I1 + kB1 * n1 - 1) / (kB1 * n1)), nb2 = (int)((I2 + kB2 * n2 - 1) / (kB2 * n2));
+    int64_t best = -1;
+    for (int m1 = 1; m1 <= 4; m1 *= 2)
+        for (int m2 = 1; m2 <= 2; m2 *= 2) {
+            if (m1 > 1 && (m1 / 2) * kB1 >= I1) continue;
+            if (m2 > 1 && (m2 / 2) * kB2 >= I2) continue;
+            const int64_t blocks = ((t1 + m1 - 1) / m1) * ((t2 + m2 - 1) / m2) * nb3;
+            // tiles on the critical path plus a per-block start-up of about 3/4 of a tile
+            // (TMEM, the A3 panel, an unoverlapped first X copy); ties go to more tiles per block
+            const int64_t cost = ((blocks + sms - 1) / sms) * (m1 * m2 * 64 + 48) - m1 * m2;
+            if (best < 0 || cost < best) {
+                best = cost;
+                n1 = m1;
+                n2 = m2;
+            }
+        }
+    const int nb1 = (int)((t1 + n1 - 1) / n1), nb2 = (int)((t2 + n2 - 1) / n2);
     const int64_t blocks = (int64_t)nb1 * nb2 * nb3;
     const int R = a.R;
-    const size_t smem = (size_t)kRows * R * 2 * 2 + (size_t)kCols * R * 2 * 2 + (size_t)R * kRows * 2 +
-                        (size_t)R * kCols * 2 + (size_t)kRows * kCols * 2 * 2 + (size_t)(2 * kB1 + kB2 + 1) * 64 * 4 +
-                        (size_t)(kB1 * n1 + kB2 * n2 + 1) * 64 * 4 + 1024;
+    const size_t smem = (size_t)kRows * R * 2 * 2 + (size_t)kCols * R * 2 * 2 +
+                        (bf16 ? 0 : (size_t)(kRows + kCols) * R * 2) + (size_t)kRows * kCols * 2 + (size_t)kRows * kXld * 4 +
+                        (size_t)(2 * kB1 + kB2 + 1) * 64 * 4 + (size_t)(kB1 * n1 + kB2 * n2 + 1) * 64 * 4 + 1024;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     if (bf16) {
         cudaFuncSetAttribute(k_dense3_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
