@@ -1,6 +1,7 @@
 // C ABI of the streaming-GCP library: context state, slice loading, the
 // direct gradient entry point, and the OnlineGCP step (Alg. 1 loop body of
 // arXiv 2110.14514) enqueued as one captured CUDA graph per slice kind.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -81,6 +82,10 @@ struct sgcp_ctx {
 
     int64_t t = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [dense, sparse]
+    // L-BFGS work vectors (allocated at the first L-BFGS step)
+    void *lb_x = nullptr, *lb_g = nullptr, *lb_p = nullptr, *lb_d = nullptr;
+    std::vector<void*> lb_S, lb_Y;
+    double* lb_dot = nullptr;
     int64_t graph_kernels[2] = {0, 0};
 };
 
@@ -385,7 +390,7 @@ sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_de
 // enqueued on c->stream; captured into a graph by build_graph.
 // ---------------------------------------------------------------------------
 template <typename T>
-sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
+sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     const int R = c->R, d = c->ndim;
     const sgcp_params& P = c->P;
     const size_t esz = sizeof(T);
@@ -470,6 +475,7 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
         }
     }
 
+    if (!with_factor) return SGCP_OK;   // the L-BFGS factor solve runs after the graph
     // ---------------- factor matrices (Alg. 4) ----------------
     SolverState* sf = c->st_f;
     const int32_t* skip = &sf->done;
@@ -553,12 +559,220 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse) {
     return SGCP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Projected L-BFGS on the factor matrices of a dense slice (the paper's
+// conclusions ask for solvers other than SGD; this one follows Nocedal &
+// Wright, "Numerical Optimization", Alg. 7.4, with a backtracking Armijo line
+// search on the projected point).  The host drives the iteration; every
+// evaluation runs in the library's kernels: the dense loss + gradient, the
+// telescoped history objective, the history / lambda gradient terms.
+// ---------------------------------------------------------------------------
+template <typename T>
+sgcp_status lbfgs_factor(sgcp_ctx* c) {
+    const int d = c->ndim, R = c->R, m = c->P.lbfgs_mem;
+    const int64_t N = c->N;
+    const size_t nb = (size_t)N * sizeof(T);
+    cudaStream_t st = c->stream;
+    if (!c->lb_x) {
+        void** one[] = {&c->lb_x, &c->lb_g, &c->lb_p, &c->lb_d};
+        for (void** q : one)
+            if (sgcp_status e = dalloc(c, q, nb)) return e;
+        c->lb_S.assign(m + 1, nullptr);   // m live pairs + one candidate slot
+        c->lb_Y.assign(m + 1, nullptr);
+        for (int i = 0; i <= m; ++i) {
+            if (sgcp_status e = dalloc(c, &c->lb_S[i], nb)) return e;
+            if (sgcp_status e = dalloc(c, &c->lb_Y[i], nb)) return e;
+        }
+        if (sgcp_status e = dalloc_t(c, &c->lb_dot, 4 * sizeof(double))) return e;
+    }
+    T* x = (T*)c->lb_x;
+    T* g = (T*)c->lb_g;
+    T* pd = (T*)c->lb_p;
+    T* dv = (T*)c->lb_d;
+    T* A = (T*)c->A;
+    T* G = (T*)c->G;
+    const void* Aptr[4];
+    void* Gptr[4];
+    for (int k = 0; k < d; ++k) {
+        Aptr[k] = offs(c->A, c->row_off[k] * R, sizeof(T));
+        Gptr[k] = offs(c->G, c->row_off[k] * R, sizeof(T));
+    }
+    GramArgs<T> ga{};
+    ga.ndim = d;
+    ga.R = R;
+    for (int k = 0; k < 4; ++k) {
+        ga.dims[k] = c->dims[k];
+        ga.row_off[k] = c->row_off[k];
+    }
+    ga.A = A;
+    ga.Abar = (const T*)c->Abar;
+    ga.part = (T*)c->gpart;
+    ga.nblk = c->gram_nblk;
+    ga.rows_per_block = c->gram_rpb;
+    ga.out = c->grams;
+    FactorUpdateArgs<T> fu{};
+    fu.ndim = d;
+    fu.R = R;
+    fu.nrows = c->nrows;
+    for (int k = 0; k < 4; ++k) fu.row_off[k] = c->row_off[k];
+    fu.A = A;
+    fu.Abar = (const T*)c->Abar;
+    fu.G = G;
+    fu.u = (T*)c->u;
+    fu.v = (T*)c->v;
+    fu.B = c->P.H > 0 ? (const T*)c->Bc : nullptr;
+    fu.C = c->P.H > 0 ? (const T*)c->Cc : nullptr;
+    fu.hist_len = c->hist_len_dev;
+    fu.lam = c->P.lambda;
+    fu.beta1 = c->P.beta1;
+    fu.beta2 = c->P.beta2;
+    fu.eps = c->P.adam_eps;
+    fu.lower = c->lower;
+    fu.rate = c->rates_f;
+    fu.skip = nullptr;
+    fu.grad_only = 1;
+    SolverState* sf = c->st_f;
+    // F(A) into *F and the full gradient into G
+    auto eval = [&](double* F) -> sgcp_status {
+        CK(cudaMemsetAsync(c->G, 0, nb, st), "clear G");
+        CK(cudaMemsetAsync(&sf->F_new, 0, sizeof(double), st), "clear F");
+        sgcp_status e2 = enqueue_gradient(c, false, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, 0,
+                                          SGCP_WANT_FACTORS | SGCP_WANT_LOSS, c->s, Aptr, Gptr, nullptr, &sf->F_new,
+                                          c->P.loss, nullptr, nullptr);
+        if (e2) return e2;
+        GramArgs<T> g6 = ga;
+        g6.npairs = 6;
+        const int su[6] = {SEL_A, SEL_ABAR, SEL_ABAR, SEL_D, SEL_D, SEL_ABAR};
+        const int sv[6] = {SEL_A, SEL_ABAR, SEL_A, SEL_D, SEL_A, SEL_D};
+        for (int i = 0; i < 6; ++i) {
+            g6.sel_u[i] = su[i];
+            g6.sel_v[i] = sv[i];
+        }
+        CK(launch_gram<T>(g6, c->nrows, st, &c->launches), "gram6");
+        CK(launch_obj_finish_f(sf, d, R, c->grams, c->SH, c->hist_len_dev, c->P.lambda, 0, c->err, nullptr, st,
+                               &c->launches),
+           "objective");
+        if (c->P.H > 0) {
+            GramArgs<T> g2 = ga;
+            g2.npairs = 2;
+            g2.sel_u[0] = SEL_A;
+            g2.sel_v[0] = SEL_A;
+            g2.sel_u[1] = SEL_D;
+            g2.sel_v[1] = SEL_A;
+            CK(launch_gram<T>(g2, c->nrows, st, &c->launches), "gram2");
+            CK(launch_hist_coeffs<T>(d, R, c->grams, c->SH, c->hist_len_dev, (T*)c->Bc, (T*)c->Cc, nullptr, st,
+                                     &c->launches),
+               "hist coeffs");
+        }
+        CK(launch_factor_update<T>(fu, st, &c->launches), "gradient terms");
+        CK(cudaMemcpyAsync(F, &sf->F_new, sizeof(double), cudaMemcpyDeviceToHost, st), "read F");
+        CK(cudaStreamSynchronize(st), "sync");
+        return SGCP_OK;
+    };
+    auto dot = [&](const T* a, const T* b, double* out) -> sgcp_status {
+        CK(launch_dot<T>(a, b, N, c->lb_dot, st, &c->launches), "dot");
+        CK(cudaMemcpyAsync(out, c->lb_dot, sizeof(double), cudaMemcpyDeviceToHost, st), "read dot");
+        CK(cudaStreamSynchronize(st), "sync");
+        return SGCP_OK;
+    };
+    double F = 0.0;
+    CK(cudaMemcpyAsync(x, A, nb, cudaMemcpyDeviceToDevice, st), "copy x");
+    if (sgcp_status e = eval(&F)) return e;
+    CK(cudaMemcpyAsync(g, G, nb, cudaMemcpyDeviceToDevice, st), "copy g");
+    std::vector<int> order;          // ring slots, oldest first
+    std::vector<double> rho(m + 1, 0.0), alpha(m + 1, 0.0);
+    int iters = 0;
+    for (int it = 0; it < c->P.lbfgs_iters; ++it) {
+        // two-loop recursion: pd <- H g
+        CK(cudaMemcpyAsync(pd, g, nb, cudaMemcpyDeviceToDevice, st), "q <- g");
+        for (int q = (int)order.size() - 1; q >= 0; --q) {
+            const int sl = order[q];
+            double sq;
+            if (sgcp_status e = dot((const T*)c->lb_S[sl], pd, &sq)) return e;
+            alpha[sl] = rho[sl] * sq;
+            CK(launch_axpby<T>(pd, (const T*)c->lb_Y[sl], -alpha[sl], 1.0, N, st, &c->launches), "axpy");
+        }
+        double gamma;
+        if (!order.empty()) {
+            const int sl = order.back();
+            double sy, yy;
+            if (sgcp_status e = dot((const T*)c->lb_S[sl], (const T*)c->lb_Y[sl], &sy)) return e;
+            if (sgcp_status e = dot((const T*)c->lb_Y[sl], (const T*)c->lb_Y[sl], &yy)) return e;
+            gamma = sy / yy;
+        } else {
+            double gg;
+            if (sgcp_status e = dot(g, g, &gg)) return e;
+            gamma = 1.0 / std::max(std::sqrt(gg), 1e-300);
+        }
+        CK(launch_axpby<T>(pd, pd, gamma, 0.0, N, st, &c->launches), "scale");
+        for (size_t q = 0; q < order.size(); ++q) {
+            const int sl = order[q];
+            double yr;
+            if (sgcp_status e = dot((const T*)c->lb_Y[sl], pd, &yr)) return e;
+            const double beta = rho[sl] * yr;
+            CK(launch_axpby<T>(pd, (const T*)c->lb_S[sl], alpha[sl] - beta, 1.0, N, st, &c->launches), "axpy");
+        }
+        // direction -pd; backtracking on the projected point
+        double step = 1.0, Fn = 0.0;
+        bool accepted = false;
+        for (int ls = 0; ls < 30; ++ls) {
+            CK(launch_project_step<T>(A, x, pd, -step, c->lower, N, st, &c->launches), "trial point");
+            if (sgcp_status e = eval(&Fn)) return e;
+            CK(cudaMemcpyAsync(dv, A, nb, cudaMemcpyDeviceToDevice, st), "d <- a");
+            CK(launch_axpby<T>(dv, x, -1.0, 1.0, N, st, &c->launches), "d <- a - x");
+            double gd;
+            if (sgcp_status e = dot(g, dv, &gd)) return e;
+            if (Fn <= F + 1e-4 * gd) {
+                accepted = true;
+                break;
+            }
+            step *= 0.5;
+        }
+        if (!accepted) {
+            CK(cudaMemcpyAsync(A, x, nb, cudaMemcpyDeviceToDevice, st), "restore");
+            break;
+        }
+        // new pair s = a_new - x (in dv), y = g_new - g
+        int sl = 0;   // a slot not holding a live pair
+        while (std::find(order.begin(), order.end(), sl) != order.end()) ++sl;
+        T* S_ = (T*)c->lb_S[sl];
+        T* Y_ = (T*)c->lb_Y[sl];
+        CK(cudaMemcpyAsync(S_, dv, nb, cudaMemcpyDeviceToDevice, st), "s");
+        CK(cudaMemcpyAsync(Y_, G, nb, cudaMemcpyDeviceToDevice, st), "y");
+        CK(launch_axpby<T>(Y_, g, -1.0, 1.0, N, st, &c->launches), "y <- g_new - g");
+        double sy, ss, yy;
+        if (sgcp_status e = dot(S_, Y_, &sy)) return e;
+        if (sgcp_status e = dot(S_, S_, &ss)) return e;
+        if (sgcp_status e = dot(Y_, Y_, &yy)) return e;
+        if (sy > 1e-12 * std::sqrt(ss) * std::sqrt(yy)) {
+            if ((int)order.size() == m) order.erase(order.begin());
+            order.push_back(sl);
+            rho[sl] = 1.0 / sy;
+        }
+        CK(cudaMemcpyAsync(x, A, nb, cudaMemcpyDeviceToDevice, st), "x <- a");
+        CK(cudaMemcpyAsync(g, G, nb, cudaMemcpyDeviceToDevice, st), "g <- g_new");
+        F = Fn;
+        ++iters;
+    }
+    // report the final objective and iteration count like an epoch summary
+    SolverState hs{};
+    CK(cudaMemcpy(&hs, sf, sizeof(hs), cudaMemcpyDeviceToHost), "read state");
+    hs.F_cur = F;
+    hs.epoch = iters;
+    hs.accept = 0u;
+    hs.done = 0;
+    CK(cudaMemcpy(sf, &hs, sizeof(hs), cudaMemcpyHostToDevice), "write state");
+    CK(cudaMemsetAsync(c->G, 0, nb, st), "clear G");
+    return SGCP_OK;
+}
+
 sgcp_status build_graph(sgcp_ctx* c, bool sparse) {
     const int gi = sparse ? 1 : 0;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "begin capture");
     const int64_t before = c->launches;
-    sgcp_status st = c->f64 ? enqueue_step<double>(c, sparse) : enqueue_step<float>(c, sparse);
+    const bool adam = c->P.optimizer == SGCP_OPT_ADAM;
+    sgcp_status st = c->f64 ? enqueue_step<double>(c, sparse, adam) : enqueue_step<float>(c, sparse, adam);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     c->launches = before;
     if (st != SGCP_OK) {
@@ -676,7 +890,8 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     if ((P.precision == SGCP_PREC_BF16_MTTKRP || P.precision == SGCP_PREC_F16_MTTKRP) &&
         (P.ndim != 3 || P.rank % 16 != 0 || P.rank > 64))
         return SGCP_ERR_UNSUPPORTED;   // the tensor-core dense kernel covers 3-way slices, R in {16, 32, 48, 64}
-    if (P.optimizer != SGCP_OPT_ADAM) return SGCP_ERR_UNSUPPORTED;
+    if (P.optimizer != SGCP_OPT_ADAM && P.optimizer != SGCP_OPT_LBFGS) return SGCP_ERR_ARG;
+    if (P.optimizer == SGCP_OPT_LBFGS && (P.lbfgs_mem < 1 || P.lbfgs_mem > 64 || P.lbfgs_iters < 0)) return SGCP_ERR_ARG;
     if (P.temporal == SGCP_TEMPORAL_LSQ && P.loss != SGCP_LOSS_GAUSSIAN) return SGCP_ERR_ARG;
     if (P.H < 0 || n_hist < 0 || n_hist > P.H || (n_hist > 0 && (!hist_t || !hist_s))) return SGCP_ERR_ARG;
     if (P.kappa_w < 0 || P.kappa_f < 0 || P.tau_w < 0 || P.tau_f < 0 || P.kappa_w > 32 || P.kappa_f > 32)
@@ -893,6 +1108,12 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
         if (sgcp_status st = build_graph(c, sparse)) return st;
     CK(cudaGraphLaunch(c->graph[gi], c->stream), "graph launch");
     c->launches += c->graph_kernels[gi];
+    if (c->P.optimizer == SGCP_OPT_LBFGS) {
+        if (sparse) return fail(c, SGCP_ERR_UNSUPPORTED, "step: the L-BFGS factor solver needs dense slices");
+        sgcp_status st = c->f64 ? lbfgs_factor<double>(c) : lbfgs_factor<float>(c);
+        if (st) return st;
+        CK(cudaMemcpyAsync(c->Abar, c->A, (size_t)c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream), "Abar <- A");
+    }
     // reservoir update of the history window (Alg. 1), decided on the host from t alone
     if (c->P.H > 0) {
         int slot = -1;

@@ -139,6 +139,7 @@ struct FactorUpdateArgs {
     double beta1, beta2, eps, lower;
     const double* rate;       // bias-corrected learning rate of this iteration (see k_epoch_begin)
     const int32_t* skip;
+    int grad_only;            // 1: store the full gradient g in G and leave A, u, v untouched
 };
 
 template <typename T>
@@ -193,6 +194,18 @@ cudaError_t launch_write_desc(SliceDesc* dst, SliceDesc val, cudaStream_t stream
 template <typename T>
 cudaError_t launch_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_len, int slot, int64_t t, int len,
                                const T* s, cudaStream_t stream, int64_t* launches);
+
+// Vector kernels of the L-BFGS factor solver (vectors of n elements of T).
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, int64_t n, double* out, cudaStream_t stream, int64_t* launches);
+// y = alpha_host * x + beta * y  (alpha from the host)
+template <typename T>
+cudaError_t launch_axpby(T* y, const T* x, double alpha, double beta, int64_t n, cudaStream_t stream,
+                         int64_t* launches);
+// out = max(x + step * p, lower)
+template <typename T>
+cudaError_t launch_project_step(T* out, const T* x, const T* p, double step, double lower, int64_t n,
+                                cudaStream_t stream, int64_t* launches);
 
 // Small helpers.
 template <typename T>

@@ -294,6 +294,10 @@ __global__ void __launch_bounds__(256) k_factor_update(const FactorUpdateArgs<T>
             const int j = l0 + 32 * c;
             if (!act || j >= R) continue;
             const int64_t idx = row * R + j;
+            if (a.grad_only) {
+                a.G[idx] = g[c];
+                continue;
+            }
             const T u = b1 * uo[c] + c1 * g[c];
             const T v = b2 * vo[c] + c2 * g[c] * g[c];
             T an = av[c] - at * u / (sqrt(v) + eps);
@@ -657,6 +661,74 @@ cudaError_t launch_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_l
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// L-BFGS vector kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_dot(const T* a, const T* b, int64_t n, double* out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(SGCP_FULL_MASK, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        atomicAdd(out, t);
+    }
+}
+
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, int64_t n, double* out, cudaStream_t stream, int64_t* launches) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), stream);
+    if (e != cudaSuccess) return e;
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = 2LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_dot<T><<<blocks, 256, 0, stream>>>(a, b, n, out);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_axpby(T* y, const T* x, double alpha, double beta, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
+}
+
+template <typename T>
+cudaError_t launch_axpby(T* y, const T* x, double alpha, double beta, int64_t n, cudaStream_t stream,
+                         int64_t* launches) {
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = 4LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_axpby<T><<<blocks, 256, 0, stream>>>(y, x, alpha, beta, n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_project_step(T* out, const T* x, const T* p, double step, double lower, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[i] + step * (double)p[i];
+        out[i] = (T)(v < lower ? lower : v);
+    }
+}
+
+template <typename T>
+cudaError_t launch_project_step(T* out, const T* x, const T* p, double step, double lower, int64_t n,
+                                cudaStream_t stream, int64_t* launches) {
+    int64_t want = (n + 255) / 256;
+    const int64_t cap = 4LL * solver_num_sms();
+    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_project_step<T><<<blocks, 256, 0, stream>>>(out, x, p, step, lower, n);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_copy(T* dst, const T* src, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -689,6 +761,10 @@ cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, in
     template cudaError_t launch_lsq_solve<T>(int, int, const double*, const T*, double, double, T*, double*, int*,   \
                                              cudaStream_t, int64_t*);                                                 \
     template cudaError_t launch_copy<T>(T*, const T*, int64_t, cudaStream_t, int64_t*);                          \
+    template cudaError_t launch_dot<T>(const T*, const T*, int64_t, double*, cudaStream_t, int64_t*);              \
+    template cudaError_t launch_axpby<T>(T*, const T*, double, double, int64_t, cudaStream_t, int64_t*);           \
+    template cudaError_t launch_project_step<T>(T*, const T*, const T*, double, double, int64_t, cudaStream_t,     \
+                                                int64_t*);                                                           \
     template cudaError_t launch_hist_update<T>(int, T*, int64_t*, int32_t*, int, int64_t, int, const T*,            \
                                                cudaStream_t, int64_t*);
 

@@ -157,3 +157,35 @@ def test_checkpoint_resume_continues_the_trajectory(sg):
     for a, b in zip(Ar, Af):
         assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
     assert rel(sr.cpu().numpy(), sf.cpu().numpy()) < 1e-12
+
+
+def test_dense_2way_lbfgs_fp64_stream_matches_oracle(sg):
+    """Projected L-BFGS factor solver (two-loop recursion, Armijo backtracking) with the LSQ
+    temporal solve and a history window: FP64 on both sides."""
+    cfg = S.workload("dense_gaussian_2way")
+    A0 = S.init_factors(cfg)
+    slices = [{"X": S.dense_slice(cfg, t)[0]} for t in range(1, 5)]
+    kw = dict(H=2, lam=0.05, lbfgs_iters=8, lbfgs_mem=3, seed=4)
+    p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=sg.PREC_F64, temporal=sg.TEMPORAL_LSQ,
+                  optimizer=sg.OPT_LBFGS, **kw)
+    okw = dict(dims=cfg["dims"], rank=cfg["rank"], loss="gaussian", temporal="lsq", optimizer="lbfgs", **kw)
+    run_stream(sg, p, A0, slices, okw, tol=1e-8)
+
+
+def test_dense_3way_fp32_lbfgs_decreases_the_objective(sg):
+    dims, R = (30, 25, 20), 8
+    rng = np.random.default_rng(11)
+    At = [rng.random((n, R)) for n in dims]
+    A0 = [(a + 0.2 * rng.random(a.shape)).astype(np.float32) for a in At]
+    X = rng.poisson(np.einsum("ir,jr,kr,r->ijk", *At, rng.random(R) + 0.5)).astype(np.float32)
+    p = sg.params(dims, R, "poisson", optimizer=sg.OPT_LBFGS, lbfgs_iters=15, H=0, kappa_w=2, tau_w=10, alpha_w=0.05)
+    with sg.Context(p, [dev(a) for a in A0]) as ctx:
+        ctx.step(X=dev(X))
+        st = ctx.stats()
+        A1, s1, _ = ctx.factors()
+    Xo = solver.Slice(dims=dims, X=X.astype(np.float64))
+    P = solver.Params(dims=dims, rank=R, loss="poisson")
+    F0 = solver.full_objective(Xo, [a.astype(np.float64) for a in A0], s1.cpu().numpy(), A0, [], [], P)
+    F1 = solver.full_objective(Xo, [a.cpu().numpy().astype(np.float64) for a in A1], s1.cpu().numpy(), A0, [], [], P)
+    assert st["epochs_f"] >= 1 and F1 < F0
+    assert abs(st["F_f"] - F1) <= 1e-4 * abs(F1)
