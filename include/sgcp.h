@@ -287,6 +287,84 @@ sgcp_status sgcp_state_size(const sgcp_ctx* ctx, size_t* size);
 sgcp_status sgcp_state_export(sgcp_ctx* ctx, void* host_buf, size_t size);
 sgcp_status sgcp_state_import(sgcp_ctx* ctx, const void* host_buf, size_t size);
 
+/* ------------------------------------------------------------------------
+ * Batched streams.  Many independent streams, each its own OnlineGCP problem
+ * (its own dims, rank, loss and solver parameters), advanced together: one
+ * sgcp_batch_step call runs the loop body of Alg. 1 (Alg. 3 temporal ADAM
+ * epochs, Alg. 4 factor ADAM epochs with the history penalty, Alg. 2
+ * checkpoints, Abar <- A, reservoir update) for every stream in ONE
+ * persistent kernel launch, captured in a CUDA graph.  Blocks take work
+ * units (tile boxes of a slice gradient, Gram-matrix row chunks, factor-update
+ * row chunks) from per-stream phase counters, so streams of very different
+ * size advance independently and the GPU stays full.  Each stream computes
+ * what sgcp_step computes for it, up to the order of float additions.
+ *
+ * Limits per stream: dense 3-way slices, precision SGCP_PREC_F32, temporal
+ * solver SGCP_TEMPORAL_ADAM, optimizer SGCP_OPT_ADAM, rank R a multiple of 4
+ * with 4 <= R <= 64, kappa_w, kappa_f <= 32.
+ *
+ * Unit tile shapes come from an autotuner: for each key (shape bucket
+ * ceil(I_k / 32) per mode, R, loss) it times candidate shapes of the slice
+ * gradient unit and keeps the fastest; the table can be read back and passed
+ * to later batches.
+ * ------------------------------------------------------------------------ */
+typedef struct sgcp_batch sgcp_batch;
+
+typedef struct {
+    int32_t bucket[3];   /* ceil(I_k / 32), k = 1..3 */
+    int32_t rank;
+    int32_t loss;        /* sgcp_loss */
+    int32_t b1log;       /* tile of 2^b1log i1 rows x 2^(5 - b1log) i2 rows x 32 i3 columns, 1 <= b1log <= 4 */
+    int32_t n1, n2;      /* tiles per unit along i1 and i2: 2^b1log n1 <= 32, 2^(5 - b1log) n2 <= 32 */
+    float us;            /* measured time of one slice-gradient pass in microseconds (0 = not timed) */
+} sgcp_tune_entry;
+
+typedef struct {
+    int32_t autotune;              /* 1: time candidates for every key missing from the table */
+    int32_t tune_reps;             /* timed launches per candidate (best kept); default 3 */
+    const sgcp_tune_entry* table;  /* host array of known entries, or NULL */
+    int32_t n_table;
+    int32_t grid_blocks;           /* persistent blocks; 0 = every block that fits on the device */
+    int64_t spin_limit;            /* empty polls before a block gives up (SGCP_ERR_TIMEOUT); 0 = default 2^22 */
+} sgcp_batch_opts;
+
+sgcp_status sgcp_batch_opts_default(sgcp_batch_opts* opts);
+
+/* params: host array of n_streams parameter sets.  init_factors: host array
+ * of 3 * n_streams device pointers (stream s, mode k at [3 s + k]), each an
+ * I_k x R float matrix copied into the batch.  opts may be NULL (defaults).
+ * cuda_stream as in sgcp_create.  Streams start at t = 0 with empty history. */
+sgcp_status sgcp_batch_create(int32_t n_streams, const sgcp_params* params, const void* const* init_factors,
+                              const sgcp_batch_opts* opts, void* cuda_stream, sgcp_batch** out);
+void sgcp_batch_destroy(sgcp_batch* batch);
+const char* sgcp_batch_last_error(const sgcp_batch* batch);
+
+/* Advance every stream by one slice.  X: host array of n_streams pointers to
+ * dense float slices in C order (I_1 x I_2 x I_3 of that stream); device
+ * pointers when x_on_host = 0, host pointers when x_on_host = 1 (the call then
+ * copies them to library-owned device buffers on the batch stream).  The
+ * caller keeps device inputs alive until the step has completed.
+ * Asynchronous on the batch stream. */
+sgcp_status sgcp_batch_step(sgcp_batch* batch, const void* const* X, int32_t x_on_host);
+
+/* Stream s: copy its factor matrices (3 device pointers, entries may be NULL)
+ * and temporal weights (device, R floats, may be NULL); t_out (host) receives
+ * its last slice index.  Asynchronous on the batch stream. */
+sgcp_status sgcp_batch_factors(sgcp_batch* batch, int32_t s, void* const* A_out, void* s_out, int64_t* t_out);
+
+/* Synchronise; statistics of stream s after its last slice (as sgcp_stats). */
+sgcp_status sgcp_batch_stats(sgcp_batch* batch, int32_t s, sgcp_stats_t* out);
+
+/* Synchronise and return the latched device error status of the batch. */
+sgcp_status sgcp_batch_check(sgcp_batch* batch);
+
+/* The tuning table of the batch (known plus newly timed entries): up to cap
+ * entries to out (host); *n_out receives the table size. */
+sgcp_status sgcp_batch_tune_table(const sgcp_batch* batch, sgcp_tune_entry* out, int32_t cap, int32_t* n_out);
+
+/* The unit tile shape stream s runs with (its table entry). */
+sgcp_status sgcp_batch_unit_config(const sgcp_batch* batch, int32_t s, sgcp_tune_entry* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,16 @@ class sgcp_stats_t(ctypes.Structure):
                 ("kernels_launched", c_int64)]
 
 
+class sgcp_tune_entry(ctypes.Structure):
+    _fields_ = [("bucket", c_int32 * 3), ("rank", c_int32), ("loss", c_int32), ("b1log", c_int32),
+                ("n1", c_int32), ("n2", c_int32), ("us", ctypes.c_float)]
+
+
+class sgcp_batch_opts(ctypes.Structure):
+    _fields_ = [("autotune", c_int32), ("tune_reps", c_int32), ("table", POINTER(sgcp_tune_entry)),
+                ("n_table", c_int32), ("grid_blocks", c_int32), ("spin_limit", c_int64)]
+
+
 _PTRS = POINTER(c_void_p)
 
 # (name, restype, argtypes) of every entry point declared in include/sgcp.h
@@ -87,6 +97,17 @@ SIGNATURES = [
     ("sgcp_gradient_sparse_noalloc", c_int32, [POINTER(sgcp_params), c_int64, c_void_p, c_void_p, c_void_p, _PTRS,
                                                POINTER(sgcp_grad_opts), _PTRS, c_void_p, c_void_p, c_void_p,
                                                c_void_p]),
+    ("sgcp_batch_opts_default", c_int32, [POINTER(sgcp_batch_opts)]),
+    ("sgcp_batch_create", c_int32, [c_int32, POINTER(sgcp_params), _PTRS, POINTER(sgcp_batch_opts), c_void_p,
+                                    POINTER(c_void_p)]),
+    ("sgcp_batch_destroy", None, [c_void_p]),
+    ("sgcp_batch_last_error", c_char_p, [c_void_p]),
+    ("sgcp_batch_step", c_int32, [c_void_p, _PTRS, c_int32]),
+    ("sgcp_batch_factors", c_int32, [c_void_p, c_int32, _PTRS, c_void_p, POINTER(c_int64)]),
+    ("sgcp_batch_stats", c_int32, [c_void_p, c_int32, POINTER(sgcp_stats_t)]),
+    ("sgcp_batch_check", c_int32, [c_void_p]),
+    ("sgcp_batch_tune_table", c_int32, [c_void_p, POINTER(sgcp_tune_entry), c_int32, POINTER(c_int32)]),
+    ("sgcp_batch_unit_config", c_int32, [c_void_p, c_int32, POINTER(sgcp_tune_entry)]),
 ]
 
 
@@ -113,9 +134,14 @@ class SgcpError(RuntimeError):
         super().__init__(f"{name}: {msg}" if msg else name)
 
 
-def _check(status, ctx=None):
+def _check(status, ctx=None, batch=None):
     if status != OK:
-        msg = lib.sgcp_last_error(ctx).decode() if ctx else ""
+        if ctx:
+            msg = lib.sgcp_last_error(ctx).decode()
+        elif batch:
+            msg = lib.sgcp_batch_last_error(batch).decode()
+        else:
+            msg = ""
         raise SgcpError(status, msg)
 
 
@@ -310,3 +336,111 @@ class Context:
     def state_import(self, data):
         buf = ctypes.create_string_buffer(data, len(data))
         _check(lib.sgcp_state_import(self.h, buf, len(data)), self.h)
+
+
+def _entry_dict(e):
+    return {"bucket": tuple(e.bucket), "rank": e.rank, "loss": e.loss, "b1log": e.b1log, "n1": e.n1, "n2": e.n2,
+            "us": e.us}
+
+
+class Batch:
+    """Many independent streams advanced together (sgcp_batch_create ... sgcp_batch_destroy): one
+    persistent kernel per time step runs every stream's Alg. 1 loop body."""
+
+    def __init__(self, plist, init_factors, autotune=False, tune_reps=3, table=None, grid_blocks=0,
+                 spin_limit=0, stream=None):
+        import torch
+        self._torch = torch
+        self.n = len(plist)
+        self.plist = list(plist)
+        self.dims = [[p.dims[k] for k in range(3)] for p in plist]
+        self.R = [p.rank for p in plist]
+        for s, (p, A) in enumerate(zip(plist, init_factors)):
+            assert len(A) == 3
+            for a, n in zip(A, self.dims[s]):
+                assert a.is_cuda and a.dtype == torch.float32 and a.is_contiguous() and tuple(a.shape) == (n, p.rank)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = (sgcp_params * self.n)(*plist)
+        flat = [a for A in init_factors for a in A]
+        opts = sgcp_batch_opts()
+        _check(lib.sgcp_batch_opts_default(ctypes.byref(opts)))
+        opts.autotune = int(bool(autotune))
+        opts.tune_reps = int(tune_reps)
+        opts.grid_blocks = int(grid_blocks)
+        opts.spin_limit = int(spin_limit)
+        self._table = None
+        if table:
+            self._table = (sgcp_tune_entry * len(table))()
+            for i, e in enumerate(table):
+                t = self._table[i]
+                for k in range(3):
+                    t.bucket[k] = e["bucket"][k]
+                t.rank, t.loss, t.b1log, t.n1, t.n2, t.us = e["rank"], e["loss"], e["b1log"], e["n1"], e["n2"], e["us"]
+            opts.table = self._table
+            opts.n_table = len(table)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        out = c_void_p()
+        _check(lib.sgcp_batch_create(self.n, arr, _ptr_array(flat), ctypes.byref(opts),
+                                     c_void_p(self.stream.cuda_stream), ctypes.byref(out)))
+        self.h = out
+        self._keep = None
+        torch.cuda.current_stream().wait_stream(self.stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.sgcp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, X):
+        """X: one dense float32 slice per stream, all device tensors or all host (CPU) tensors."""
+        assert len(X) == self.n
+        on_host = not X[0].is_cuda
+        for x in X:
+            assert x.dtype == self._torch.float32 and x.is_contiguous() and x.is_cuda != on_host
+        self._keep = X
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+        st = lib.sgcp_batch_step(self.h, _ptr_array(X), int(on_host))
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+        _check(st, batch=self.h)
+
+    def factors(self, s):
+        torch = self._torch
+        A = [torch.empty((n, self.R[s]), dtype=torch.float32, device="cuda") for n in self.dims[s]]
+        sv = torch.empty(self.R[s], dtype=torch.float32, device="cuda")
+        t = c_int64()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        _check(lib.sgcp_batch_factors(self.h, s, _ptr_array(A), _ptr(sv), ctypes.byref(t)), batch=self.h)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return A, sv, t.value
+
+    def stats(self, s):
+        st = sgcp_stats_t()
+        _check(lib.sgcp_batch_stats(self.h, s, ctypes.byref(st)), batch=self.h)
+        return {f: getattr(st, f) for f, _ in sgcp_stats_t._fields_}
+
+    def check(self):
+        _check(lib.sgcp_batch_check(self.h), batch=self.h)
+
+    def tune_table(self):
+        n = c_int32()
+        _check(lib.sgcp_batch_tune_table(self.h, None, 0, ctypes.byref(n)), batch=self.h)
+        arr = (sgcp_tune_entry * max(n.value, 1))()
+        _check(lib.sgcp_batch_tune_table(self.h, arr, n.value, ctypes.byref(n)), batch=self.h)
+        return [_entry_dict(arr[i]) for i in range(n.value)]
+
+    def unit_config(self, s):
+        e = sgcp_tune_entry()
+        _check(lib.sgcp_batch_unit_config(self.h, s, ctypes.byref(e)), batch=self.h)
+        return _entry_dict(e)

@@ -796,12 +796,6 @@ sgcp_status build_graph(sgcp_ctx* c, bool sparse) {
     return SGCP_OK;
 }
 
-uint32_t reservoir_index(uint64_t seed, int64_t t) {
-    uint32_t ctr[4] = {0u, 0u, 0u, counter_word3(PUR_RESERVOIR, t)};
-    philox4x32_10(ctr, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
-    return 1u + bounded_u32(ctr[0], (uint32_t)t);
-}
-
 sgcp_status check_ready(sgcp_ctx* c) {
     if (!c) return SGCP_ERR_ARG;
     if (c->sticky != SGCP_OK) return SGCP_ERR_STATE;

@@ -206,6 +206,15 @@ __device__ void temporal_step_tail(const TemporalStep<T>& ts, T* gs, int R) {
     }
 }
 
+// Reservoir draw of Alg. 1 at step t (host): j = 1 + floor(u t / 2^32) in
+// [1, t] from the Philox block (0, 0, 0, purpose 4 | t); slot j - 1 is
+// overwritten when j <= H.
+inline uint32_t reservoir_index(uint64_t seed, int64_t t) {
+    uint32_t ctr[4] = {0u, 0u, 0u, counter_word3(PUR_RESERVOIR, t)};
+    philox4x32_10(ctr, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    return 1u + bounded_u32(ctr[0], (uint32_t)t);
+}
+
 // Hot-row privatisation limits of the sparse kernel.
 constexpr int kMaxHot = 64;
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "solver_dev.cuh"
 
 namespace sgcp {
 
@@ -98,8 +99,6 @@ cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* 
 // ---------------------------------------------------------------------------
 // Solver kernels (k_solver.cu)
 // ---------------------------------------------------------------------------
-// Which factor set a Gram pair uses.
-enum GramSel : int { SEL_A = 0, SEL_ABAR = 1, SEL_D = 2 };
 
 template <typename T>
 struct GramArgs {
@@ -210,5 +209,79 @@ cudaError_t launch_project_step(T* out, const T* x, const T* p, double step, dou
 // Small helpers.
 template <typename T>
 cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, int64_t* launches);
+
+}  // namespace sgcp
+
+namespace sgcp {
+
+// ---------------------------------------------------------------------------
+// Batched streams (k_batch.cu): many independent OnlineGCP streams with dense
+// 3-way FP32 slices, advanced by one persistent kernel per time step.
+// ---------------------------------------------------------------------------
+constexpr int kBatchMaxR = 64;      // largest rank of a batched stream
+constexpr int kBatchThreads = 256;
+constexpr int kBatchGramRows = 64;  // rows of one Gram-chunk unit
+constexpr int kBatchUpdRows = 32;   // rows of one factor-update unit
+
+// Per-stream description: read-only while a step runs.
+struct BatchStream {
+    int R, loss;
+    int P, PF0;                    // phases of one step; first factor phase
+    int dims[3], row_off[3], nrows, N;
+    int b1log, n1, n2;             // unit tile: 2^b1log i1 rows x 2^(5-b1log) i2 rows, n1 x n2 tiles per unit
+    int nb1, nb2, nb3, n_box;      // units of the slice gradient
+    int gch[3], n_gram;            // 64-row Gram chunks per mode
+    int uch[3], n_upd;             // 32-row factor-update chunks per mode
+    int kappa_w, tau_w, kappa_f, tau_f;
+    float eps, lower;
+    double tol_w, tol_f, alpha_w, alpha_f, beta1, beta2, adam_eps, decay, w, theta, lam, mu;
+    float *A, *Abar, *G, *u, *v, *u_o, *v_o, *a_o;     // N each (modes concatenated)
+    float *s, *s_u, *s_v, *s_uo, *s_vo, *s_ao, *gs;    // R each
+    float* s_hist;                 // [H][R]
+    int64_t* h_dev;                // [H]
+    int32_t* hist_len;
+    double* SH;                    // [R][R]
+    double* grams;                 // [6][3][R][R]
+    float* gpart;                  // [n_gram][6][R][R] Gram-chunk partial sums
+    float *Bc, *Cc;                // [3][R][R] history coefficients
+    SolverState *st_w, *st_f;
+    double *rates_w, *rates_f;     // [tau_w], [tau_f]
+};
+
+// Per-stream inputs of one step (written before each launch).
+struct BatchStepEntry {
+    const float* X;                // dense slice, C order
+    int64_t t;                     // time index of the slice
+    int32_t slot, len;             // history slot to overwrite after the step (-1 = none), new window length
+    int32_t hist_on;               // window non-empty during this step
+    int32_t pad;
+};
+
+// Per-stream scheduling words.
+struct BatchCtl {
+    unsigned long long claim;      // (phase << 32) | next unclaimed unit
+    int32_t done;                  // units of the current phase completed
+    int32_t pad;
+};
+
+struct BatchArgs {
+    const BatchStream* S;
+    const BatchStepEntry* E;
+    BatchCtl* ctl;
+    const int32_t* order;          // streams in scheduling priority order
+    int nS;
+    int* finished;                 // streams that completed the step
+    int* err;
+    long long spin_limit;          // empty polls before a block gives up (ERRB_TIMEOUT)
+};
+
+size_t batch_smem_bytes();
+int batch_blocks_per_sm();
+cudaError_t launch_batch_begin(BatchStepEntry* dE, const BatchStepEntry* host_entries, int n, BatchCtl* ctl, int nS,
+                               int* finished, cudaStream_t st, int64_t* launches);
+cudaError_t launch_batch_step(const BatchArgs& a, int grid, cudaStream_t st, int64_t* launches);
+// Autotuner timing launch: blocks x (factor-gradient unit blockIdx % n_box) of one stream description.
+cudaError_t launch_batch_units(const BatchStream* S_dev, const BatchStepEntry* E_dev, int n_box, int blocks,
+                               cudaStream_t st);
 
 }  // namespace sgcp

@@ -25,11 +25,6 @@ namespace sgcp {
 // over its rows (element type T); k_gram_reduce adds the partials in double.
 // No atomics, so results do not depend on scheduling.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T gsel(int sel, const T* A, const T* Ab, int64_t i) {
-    return sel == SEL_A ? A[i] : (sel == SEL_ABAR ? Ab[i] : A[i] - Ab[i]);
-}
-
 constexpr int kGramStage = 32;   // rows staged in shared memory at a time
 constexpr int kGramMaxBlocks = 512;
 
@@ -175,39 +170,10 @@ template <typename T>
 __global__ void k_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
                               T* B, T* C, const int32_t* skip) {
     if (skip && *skip) return;
-    const bool on = *hist_len > 0;
     const int RR = R * R;
-    const double* P = grams;
-    const double* E = grams + (int64_t)ndim * RR;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= RR) return;
-    T p[4], e[4];
-    for (int n = 0; n < ndim; ++n) {
-        p[n] = (T)P[n * RR + i];
-        e[n] = (T)E[n * RR + i];
-    }
-    const T sh = (T)SH[i];
-    for (int k = 0; k < ndim; ++k) {
-        if (!on) {
-            B[k * RR + i] = T(0);
-            C[k * RR + i] = T(0);
-            continue;
-        }
-        T gam = T(1), dgam = T(0);
-        // telescoping: prod P - prod Q = sum_m (prod_{before} Q)(E_m)(prod_{after} P), Q = P - E
-        for (int m = 0; m < ndim; ++m) {
-            if (m == k) continue;
-            gam *= p[m];
-            T term = e[m];
-            for (int n = 0; n < ndim; ++n) {
-                if (n == k || n == m) continue;
-                term *= (n < m) ? (p[n] - e[n]) : p[n];
-            }
-            dgam += term;
-        }
-        B[k * RR + i] = gam * sh;
-        C[k * RR + i] = dgam * sh;
-    }
+    hist_coeff_elem<T>(ndim, RR, grams, grams + (int64_t)ndim * RR, SH, i, *hist_len > 0, B, C);
 }
 
 template <typename T>
@@ -345,17 +311,7 @@ cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, 
 // Solver bookkeeping
 // ---------------------------------------------------------------------------
 __global__ void k_solver_init(SolverState* st, double alpha, int reset_counter) {
-    st->alpha = alpha;
-    st->epoch = 0;
-    st->done = 0;
-    st->accept = 0u;
-    st->ticket = 0u;
-    st->F_new = 0.0;
-    if (reset_counter) {
-        st->i = 0;
-        st->b1pow = 1.0;
-        st->b2pow = 1.0;
-    }
+    solver_init_state(st, alpha, reset_counter);
 }
 
 cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
@@ -368,14 +324,7 @@ cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter,
 // Alg. 3/4 loop test "while F > tol": once it fails, every later kernel of
 // the solver call is skipped through st->done.
 __global__ void k_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2) {
-    const SolverState s0 = *st;
-    for (int j = threadIdx.x; j < tau; j += blockDim.x) rates[j] = adam_rate(s0, beta1, beta2, j);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!st->done && !(st->F_cur > tol)) st->done = 1;
-        st->F_old = st->F_cur;
-        st->F_new = 0.0;
-    }
+    epoch_begin_block(st, tol, rates, tau, beta1, beta2);
 }
 
 cudaError_t launch_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2,
@@ -390,31 +339,11 @@ template <typename T>
 __global__ void k_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
                             double decay, double beta1, double beta2) {
     if (st->done) return;
-    const double Fn = st->F_new, Fo = st->F_old;
-    const bool passed = !(Fn > Fo) && isfinite(Fn);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (passed) {
-            u_o[i] = u[i];
-            v_o[i] = v[i];
-            a_o[i] = a[i];
-        } else {
-            u[i] = u_o[i];
-            v[i] = v_o[i];
-            a[i] = a_o[i];
-        }
-    }
+    const bool passed = epoch_passed(st);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        epoch_end_elem(passed, i, a, u, v, a_o, u_o, v_o);
     if (last_block_ticket(st) && threadIdx.x == 0) {
-        if (passed) {   // the epoch's tau iterations count; a rejected epoch's are rolled back (Alg. 3/4)
-            st->F_cur = Fn;
-            st->accept |= (st->epoch < 32) ? (1u << st->epoch) : 0u;
-            st->i += tau;
-            st->b1pow *= pow(beta1, (double)tau);
-            st->b2pow *= pow(beta2, (double)tau);
-        } else {
-            st->F_cur = Fo;
-            st->alpha *= decay;
-        }
-        st->epoch += 1;
+        epoch_end_state(st, passed, tau, decay, beta1, beta2);
         st->ticket = 0u;
         __threadfence();
     }
@@ -478,64 +407,10 @@ cudaError_t launch_obj_finish_w(SolverState* st, const T* s, int R, double mu, i
     return cudaGetLastError();
 }
 
-// History objective 1/2 sum_h w_h ||Mbar_h - M_h||^2 in telescoped form:
-// M_h - Mbar_h = sum_k [[s_h; Abar^(1..k-1), D^(k), A^(k+1..d)]], so
-// ||.||^2 = sum_{k,l} s_h' (*_n Gram(U_kn, U_ln)) s_h with U_kn = Abar (n < k),
-// D (n = k), A (n > k); summed over h through S_H.
-__device__ __forceinline__ int which_mat(int k, int n) { return n < k ? SEL_ABAR : (n == k ? SEL_D : SEL_A); }
-
-// grams layout: pair index p in [(A,A), (Abar,Abar), (Abar,A), (D,D), (D,A), (Abar,D)].
-__device__ __forceinline__ double gram_entry(const double* grams, int ndim, int R, int n, int u, int v, int l, int m) {
-    // returns Gram(u, v)[l][m] for mode n, using Gram(v, u)[m][l] when only the transpose is stored
-    int p = -1;
-    bool tr = false;
-    if (u == SEL_A && v == SEL_A) p = 0;
-    else if (u == SEL_ABAR && v == SEL_ABAR) p = 1;
-    else if (u == SEL_ABAR && v == SEL_A) p = 2;
-    else if (u == SEL_A && v == SEL_ABAR) { p = 2; tr = true; }
-    else if (u == SEL_D && v == SEL_D) p = 3;
-    else if (u == SEL_D && v == SEL_A) p = 4;
-    else if (u == SEL_A && v == SEL_D) { p = 4; tr = true; }
-    else if (u == SEL_ABAR && v == SEL_D) p = 5;
-    else { p = 5; tr = true; }   // (D, Abar)
-    const double* g = grams + ((int64_t)p * ndim + n) * R * R;
-    return tr ? g[m * R + l] : g[l * R + m];
-}
-
 __global__ void k_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
                                const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip) {
     if (skip && *skip) return;
-    __shared__ double red[32];
-    double acc = 0.0, reg = 0.0;
-    const bool hist = *hist_len > 0;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-        const int l = i / R, m = i % R;
-        if (hist) {
-            double tot = 0.0;
-            for (int k = 0; k < ndim; ++k)
-                for (int kk = 0; kk < ndim; ++kk) {
-                    double prod = 1.0;
-                    for (int n = 0; n < ndim; ++n)
-                        prod *= gram_entry(grams, ndim, R, n, which_mat(k, n), which_mat(kk, n), l, m);
-                    tot += prod;
-                }
-            acc += SH[i] * tot;
-        }
-        if (l == m)
-            for (int n = 0; n < ndim; ++n) reg += grams[((int64_t)0 * ndim + n) * R * R + i];
-    }
-    double v = 0.5 * acc + 0.5 * lam * reg;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(SGCP_FULL_MASK, v, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
-        const double F = st->F_new + tot;
-        st->F_new = F;
-        if (!isfinite(F)) set_err(err, ERRB_NUMERIC);
-        if (set_cur) st->F_cur = F;
-    }
+    obj_finish_f_block(st, ndim, R, grams, SH, *hist_len > 0, lam, set_cur, err);
 }
 
 cudaError_t launch_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
@@ -552,15 +427,8 @@ __global__ void k_history_SH(int R, const T* s_hist, const int64_t* h_dev, const
                              const SliceDesc* slice, double w, double theta, double* SH) {
     const int n = *hist_len;
     const int64_t t = slice->t;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-        const int l = i / R, m = i % R;
-        double acc = 0.0;
-        for (int h = 0; h < n; ++h) {
-            const double wh = w * pow(theta, (double)(t - h_dev[h]));
-            acc += wh * (double)s_hist[h * R + l] * (double)s_hist[h * R + m];
-        }
-        SH[i] = acc;
-    }
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x)
+        SH[i] = history_SH_elem<T>(R, s_hist, h_dev, n, t, w, theta, i);
 }
 
 template <typename T>

@@ -43,6 +43,8 @@ def test_struct_layout_matches_c(sg, tmp_path):
         'printf("%zu %zu %zu %zu\\n", sizeof(sgcp_params), sizeof(sgcp_slice), sizeof(sgcp_grad_opts), sizeof(sgcp_stats_t));\n'
         'printf("%zu %zu %zu %zu %zu\\n", offsetof(sgcp_params, lambda), offsetof(sgcp_params, p_obj), '
         "offsetof(sgcp_params, zero_attempt_cap), offsetof(sgcp_params, seed), offsetof(sgcp_stats_t, kernels_launched));\n"
+        'printf("%zu %zu %zu %zu\\n", sizeof(sgcp_tune_entry), sizeof(sgcp_batch_opts), offsetof(sgcp_tune_entry, us), '
+        "offsetof(sgcp_batch_opts, spin_limit));\n"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
@@ -50,9 +52,11 @@ def test_struct_layout_matches_c(sg, tmp_path):
     sizes = [int(x) for x in out]
     assert sizes[:4] == [ctypes.sizeof(sg.sgcp_params), ctypes.sizeof(sg.sgcp_slice),
                          ctypes.sizeof(sg.sgcp_grad_opts), ctypes.sizeof(sg.sgcp_stats_t)]
-    assert sizes[4:] == [sg.sgcp_params.lambda_.offset, sg.sgcp_params.p_obj.offset,
-                         sg.sgcp_params.zero_attempt_cap.offset, sg.sgcp_params.seed.offset,
-                         sg.sgcp_stats_t.kernels_launched.offset]
+    assert sizes[4:9] == [sg.sgcp_params.lambda_.offset, sg.sgcp_params.p_obj.offset,
+                          sg.sgcp_params.zero_attempt_cap.offset, sg.sgcp_params.seed.offset,
+                          sg.sgcp_stats_t.kernels_launched.offset]
+    assert sizes[9:] == [ctypes.sizeof(sg.sgcp_tune_entry), ctypes.sizeof(sg.sgcp_batch_opts),
+                         sg.sgcp_tune_entry.us.offset, sg.sgcp_batch_opts.spin_limit.offset]
 
 
 def test_defaults_follow_table_2(sg):
@@ -86,3 +90,28 @@ def test_no_cpu_fallback_when_cuda_is_missing(sg):
     arr = (ctypes.c_void_p * 3)()
     p = sg.params((10, 20, 30), 8)
     assert sg.sgcp_create(ctypes.byref(p), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_CUDA
+
+
+def test_batch_argument_errors_are_synchronous_without_a_gpu(sg):
+    """sgcp_batch_create validates every stream before touching the device."""
+    out = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 6)(*([1] * 6))   # non-NULL placeholders: never dereferenced on these paths
+    def create(plist, opts=None):
+        pa = (sg.sgcp_params * len(plist))(*plist)
+        return sg.sgcp_batch_create(len(plist), pa, arr, ctypes.byref(opts) if opts else None, None,
+                                    ctypes.byref(out))
+    good = sg.params((40, 50, 60), 16)
+    assert create([good, sg.params((40, 50), 16)]) == sg.ERR_UNSUPPORTED           # 2-way slice
+    assert create([good, sg.params((40, 50, 60), 80)]) == sg.ERR_UNSUPPORTED       # rank above 64
+    assert create([good, sg.params((40, 50, 60), 16, precision=sg.PREC_F64)]) == sg.ERR_UNSUPPORTED
+    assert create([good, sg.params((40, 50, 60), 16, optimizer=sg.OPT_LBFGS)]) == sg.ERR_UNSUPPORTED
+    assert create([good, sg.params((40, 50, 60), 16, kappa_f=33)]) == sg.ERR_ARG
+    opts = sg.sgcp_batch_opts()
+    assert sg.sgcp_batch_opts_default(ctypes.byref(opts)) == sg.OK
+    assert (opts.autotune, opts.tune_reps, opts.grid_blocks, opts.spin_limit) == (0, 3, 0, 0)
+    bad_entry = (sg.sgcp_tune_entry * 1)()
+    bad_entry[0].b1log, bad_entry[0].n1, bad_entry[0].n2 = 5, 1, 1             # tile row split out of range
+    opts.table, opts.n_table = bad_entry, 1
+    assert create([good], opts) == sg.ERR_ARG
+    assert sg.sgcp_batch_create(0, None, arr, None, None, ctypes.byref(out)) == sg.ERR_ARG
+    assert sg.sgcp_batch_check(None) == sg.ERR_ARG
