@@ -25,7 +25,11 @@ import sys
 import threading
 import time
 
-import numpy as np
+# The oracle baselines run on one host core: keep numpy's BLAS pools at one thread.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -389,6 +393,146 @@ def run_native_dense(args, cfg, world, rank, local):
     }
 
 
+# ----------------------------------------------------------------------------- batched streams
+BATCH_SOLVER = dict(H=10, w=1.0, theta=0.9, kappa_w=5, tau_w=20, kappa_f=5, tau_f=20, alpha_w=0.05, alpha_f=1e-3)
+
+
+def batched_flops_per_step(shapes, sol):
+    """Algorithmic FP32 flops of one batched step: per slice entry 2R for a loss pass (model),
+    4R for a gradient-of-s pass (model + T = Y A3), 6R for a factor-gradient pass (model + T + G3)."""
+    loss_passes = 2 + sol["kappa_w"] + sol["kappa_f"]
+    tgrad_passes = sol["kappa_w"] * sol["tau_w"]
+    fgrad_passes = sol["kappa_f"] * sol["tau_f"]
+    flops = entries = 0
+    for dims, R, _ in shapes:
+        om = int(np.prod(dims))
+        flops += om * R * (2 * loss_passes + 4 * tgrad_passes + 6 * fgrad_passes)
+        entries += om * (loss_passes + tgrad_passes + fgrad_passes)
+    return flops, entries
+
+
+def run_native_batched(args, cfg, world, rank, local):
+    """64 independent dense streams of uneven shape (I_k ~ U{32..160}, R ~ U{8..64}, Gaussian / Poisson):
+    one sgcp_batch_step per time step (one persistent kernel), against the same streams stepped one
+    after another through single-stream contexts."""
+    import torch
+    import paper_2110_14514_gb300 as sg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shapes = S.batched_stream_shapes(cfg)
+    n = len(shapes)
+    scfg = [S.batched_stream_cfg(cfg, s) for s in range(n)]
+    plist = [sg.params(c["dims"], c["rank"], c["loss"], seed=3000 + 97 * rank + s, **BATCH_SOLVER)
+             for s, c in enumerate(scfg)]
+    A0 = [[torch.from_numpy(a).to(dev) for a in S.init_factors(c, stream=rank)] for c in scfg]
+    n_sl = 2
+    host = [[torch.from_numpy(S.dense_slice(c, t + 1, stream=rank)[0]).pin_memory() for c in scfg]
+            for t in range(n_sl)]
+    dsl = [[x.to(dev) for x in h] for h in host]
+    t0 = time.time()
+    b = sg.Batch(plist, A0, autotune=True, tune_reps=2)
+    tune_s = time.time() - t0
+    flops, entries = batched_flops_per_step(shapes, BATCH_SOLVER)
+    for w in range(args.warmup):
+        b.step(dsl[w % n_sl])
+    b.check()
+    k0 = b.stats(0)["kernels_launched"]
+    stream = b.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+        b.step(dsl[(args.warmup + k) % n_sl])
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    b.check()
+    launches = b.stats(0)["kernels_launched"] - k0
+    step_s = [a.elapsed_time(c) / 1e3 for a, c in ev]
+    total_s = sum(step_s)
+    value = world * args.steps * entries / total_s
+    # end to end: host slices copied inside the call, per-stream objectives read back
+    e2e_steps = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    d2h = 0
+    for k in range(e2e_steps):
+        b.step(host[k % n_sl])
+        Fs = [b.stats(s)["F_f"] for s in range(n)]
+        d2h += n * 8
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    h2d = sum(int(np.prod(d)) * 4 for d, _, _ in shapes)
+    table = b.tune_table()
+    b.close()
+    # the same streams, one single-stream context after another (plain FP32 sgcp_step)
+    ctxs = [sg.Context(p, A) for p, A in zip(plist, A0)]
+    for c, x in zip(ctxs, dsl[0]):
+        c.step(X=x)
+    torch.cuda.synchronize()
+    seq_steps = 2
+    ts = time.perf_counter()
+    for k in range(seq_steps):
+        for c, x in zip(ctxs, dsl[(k + 1) % n_sl]):
+            c.step(X=x)
+        torch.cuda.synchronize()
+    seq_s = (time.perf_counter() - ts) / seq_steps
+    for c in ctxs:
+        c.close()
+    sm_clock = clk.get("sm_max_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = n_sm * 128 * 2 * sm_clock * 1e6 / 1e12
+    achieved = flops / (total_s / args.steps) / 1e12
+    out = {
+        "metric": "batched GCP gradient entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched_streams: 64 dense streams, I_k ~ U{32..160}, R ~ U{8..64}, "
+                               "Gaussian (even) / Poisson (odd)",
+                   "solver": BATCH_SOLVER, "entries_per_step": entries,
+                   "l2": "inputs larger than L2 (sum of slices %.0f MB, re-read by every pass)" % (h2d / 1e6),
+                   "sequential_ms_per_step": 1e3 * seq_s,
+                   "speedup_vs_sequential": seq_s / (total_s / args.steps),
+                   "autotune_s": tune_s, "tune_keys": len(table)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_kind": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flop x {sm_clock:.0f} MHz"},
+        "e2e": {"value": e2e_steps * entries / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h // e2e_steps},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = batched_cpu_baseline(scfg)
+    return out
+
+
+def batched_cpu_baseline(scfg, budget_s=12.0):
+    """The oracle's dense gradient (FP64 numpy) on whole slices of the batch's streams, in stream
+    order until the time budget is spent."""
+    from oracle import gcp
+    t0 = time.perf_counter()
+    ent = 0
+    done = 0
+    for c in scfg:
+        X, _ = S.dense_slice(c, 1)
+        A = S.init_factors(c)
+        sv = np.ones(c["rank"])
+        gcp.dense_gradient(X.astype(np.float64), sv, [a.astype(np.float64) for a in A], c["loss"])
+        ent += X.size
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": ent / el, "unit": "entries/s", "cores": 1, "kind": "oracle",
+            "sample": f"full FP64 oracle gradients of {done} stream slices (one pass each)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,13 +540,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "dense_gaussian_3way"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "dense_gaussian_3way", "batched_streams"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
     args = ap.parse_args()
     world, rank, local = dist_setup()
     cfg = S.workload(args.workload)
     if args.impl == "reference":
         out = run_reference(args, S.workload(WORKLOAD), world, rank)
+    elif args.workload == "batched_streams":
+        out = run_native_batched(args, cfg, world, rank, local)
     elif args.workload != WORKLOAD:
         out = run_native_dense(args, cfg, world, rank, local)
     else:
