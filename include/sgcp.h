@@ -314,8 +314,8 @@ typedef struct {
     int32_t bucket[3];   /* ceil(I_k / 32), k = 1..3 */
     int32_t rank;
     int32_t loss;        /* sgcp_loss */
-    int32_t b1log;       /* tile of 2^b1log i1 rows x 2^(5 - b1log) i2 rows x 32 i3 columns, 1 <= b1log <= 4 */
-    int32_t n1, n2;      /* tiles per unit along i1 and i2: 2^b1log n1 <= 32, 2^(5 - b1log) n2 <= 32 */
+    int32_t b1log;       /* tile of 2^b1log i1 rows x 2^(6 - b1log) i2 rows x 32 i3 columns, 2 <= b1log <= 4 */
+    int32_t n1, n2;      /* tiles per unit along i1 and i2: 2^b1log n1 <= 32, 2^(6 - b1log) n2 <= 32 */
     float us;            /* measured time of one slice-gradient pass in microseconds (0 = not timed) */
 } sgcp_tune_entry;
 

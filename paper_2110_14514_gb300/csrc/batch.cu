@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "dense_tile.cuh"
 #include "internal.h"
 #include "sgcp.h"
 
@@ -73,7 +74,7 @@ void set_geometry(BatchStream& S, int b1log, int n1, int n2) {
     S.b1log = b1log;
     S.n1 = n1;
     S.n2 = n2;
-    const int S1 = (1 << b1log) * n1, S2 = (32 >> b1log) * n2;
+    const int S1 = (1 << b1log) * n1, S2 = (64 >> b1log) * n2;
     S.nb1 = ceil_div(S.dims[0], S1);
     S.nb2 = ceil_div(S.dims[1], S2);
     S.nb3 = ceil_div(S.dims[2], 32);
@@ -87,17 +88,18 @@ bool same_key(const sgcp_tune_entry& e, const BatchStream& S) {
 }
 
 bool valid_shape(int b1log, int n1, int n2) {
-    return b1log >= 1 && b1log <= 4 && n1 >= 1 && n2 >= 1 && (1 << b1log) * n1 <= 32 && (32 >> b1log) * n2 <= 32;
+    return b1log >= 2 && b1log <= 4 && n1 >= 1 && n2 >= 1 && (1 << b1log) * n1 <= kBoxMaxS &&
+           (64 >> b1log) * n2 <= kBoxMaxS;
 }
 
-// Default shape without timing: 4 x 8 tiles, boxes up to 32 x 32 rows.
+// Default shape without timing: 8 x 8 tiles, boxes up to 32 x 32 rows.
 sgcp_tune_entry default_entry(const BatchStream& S) {
     sgcp_tune_entry e{};
     for (int k = 0; k < 3; ++k) e.bucket[k] = ceil_div(S.dims[k], 32);
     e.rank = S.R;
     e.loss = S.loss;
-    e.b1log = 2;
-    e.n1 = std::min(8, ceil_div(S.dims[0], 4));
+    e.b1log = 3;
+    e.n1 = std::min(4, ceil_div(S.dims[0], 8));
     e.n2 = std::min(4, ceil_div(S.dims[1], 8));
     e.us = 0.f;
     return e;
@@ -254,10 +256,10 @@ sgcp_status autotune(sgcp_batch* b, int reps) {
         if (known) continue;
         sgcp_tune_entry best = default_entry(S);
         best.us = -1.f;
-        for (int b1log = 1; b1log <= 4; ++b1log)
+        for (int b1log = 2; b1log <= 4; ++b1log)
             for (int S1 : {8, 16, 32})
                 for (int S2 : {8, 16, 32}) {
-                    const int n1 = S1 >> b1log, n2 = (S2 << b1log) >> 5;
+                    const int n1 = S1 >> b1log, n2 = (S2 << b1log) >> 6;
                     if (n1 < 1 || n2 < 1 || !valid_shape(b1log, n1, n2)) continue;
                     if (S1 > 2 * ((S.dims[0] + 7) / 8 * 8) || S2 > 2 * ((S.dims[1] + 7) / 8 * 8)) continue;
                     sgcp_tune_entry c = best;

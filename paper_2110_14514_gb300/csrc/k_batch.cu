@@ -18,6 +18,8 @@
 //   after the last tail          Abar <- A, history slot <- s_t
 // A solver whose loop test fails (F <= tol) jumps to the next solver.
 //
+// Gradient units are boxes of 64-row x 32-column tiles (dense_tile.cuh).
+//
 // Scheduling.  A stream's claim word holds (phase << 32 | next unit); a block
 // takes a unit with one atomicAdd.  The block that completes the phase's last
 // unit runs the tail and publishes the next phase.  So streams advance
@@ -26,6 +28,7 @@
 // another block may have written during the launch is read through L2
 // (ld.global.cg), and each block fences its writes before it counts a unit
 // done, so the tail and the next phase see them.
+#include "dense_tile.cuh"
 #include "internal.h"
 #include "sgcp.h"
 
@@ -83,235 +86,46 @@ __device__ __forceinline__ int units_of(const BatchStream& S, const BatchStepEnt
     }
 }
 
-// ---------------------------------------------------------------------------
-// Shared-memory plan of one block (floats): the gradient-unit panels; Gram and
-// update units reuse the front of the same buffer.
-// ---------------------------------------------------------------------------
-constexpr int kLD = kBatchMaxR + 1;
-constexpr int kOffA3 = 0;                          // [32][kLD]
-constexpr int kOffKR = kOffA3 + 32 * kLD;          // [32][kLD]
-constexpr int kOffT = kOffKR + 32 * kLD;           // [32][kLD]
-constexpr int kOffY = kOffT + 32 * kLD;            // [32][33]
-constexpr int kOffA1 = kOffY + 32 * 33;            // [16][64]
-constexpr int kOffA1s = kOffA1 + 16 * kBatchMaxR;  // [16][64]
-constexpr int kOffA2 = kOffA1s + 16 * kBatchMaxR;  // [16][64]
-constexpr int kOffS = kOffA2 + 16 * kBatchMaxR;    // [64]
-constexpr int kOffAcc1 = kOffS + kBatchMaxR;       // [32][64]
-constexpr int kOffAcc2 = kOffAcc1 + 32 * kBatchMaxR;   // [32][64]
-constexpr int kOffRed = kOffAcc2 + 32 * kBatchMaxR;    // 8 doubles
-constexpr int kSmemFloats = kOffRed + 16;
-static_assert(kOffRed % 2 == 0, "double alignment");
+// Shared memory of one block (floats): the gradient-unit plan of dense_tile.cuh;
+// Gram and update units reuse the front of the same buffer.
+constexpr int kSmemFloats = kBoxSmemFloats;
 static_assert(2 * kBatchGramRows * kBatchMaxR + kBatchMaxR * kBatchMaxR <= kSmemFloats, "Gram unit staging");
 static_assert(2 * kBatchMaxR * kBatchMaxR <= kSmemFloats, "update unit coefficients");
 
-// Block-wide double sum; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(SGCP_FULL_MASK, v, off);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double tot = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < kBatchThreads / 32; ++i) tot += red[i];
-    return tot;
-}
-
-// ---------------------------------------------------------------------------
-// Gradient unit: a box of n1 x n2 tiles of 32 (i1, i2) rows sharing one block
-// of 32 i3 columns (the dense tile algebra of the single-stream kernel:
-// KR = (s.A1) x A2 panel, M = KR A3', Y = df/dm, T = Y A3 shared by modes 1
-// and 2, G3 += Y' KR), with the loss, the gradient of s or the factor
-// gradients selected by the phase.
-// ---------------------------------------------------------------------------
+// Gradient unit u of a stream: one box of the slice (dense_tile.cuh) with the
+// loss, the gradient of s or the factor gradients selected by the phase.
 __device__ void box_unit(const BatchStream& S, const float* __restrict__ X, int kind, SolverState* st_obj, int u,
                          float* sm) {
     const int R = S.R;
-    const int lb1 = S.b1log, lb2 = 5 - lb1, B1 = 1 << lb1, B2 = 1 << lb2;
-    const int S1 = B1 * S.n1, S2 = B2 * S.n2;
+    const int B1 = 1 << S.b1log, B2 = 64 >> S.b1log;
     const int nb12 = S.nb1 * S.nb2;
     const int b3 = u / nb12, rem = u - b3 * nb12;
     const int bb1 = rem / S.nb2, bb2 = rem - bb1 * S.nb2;
-    const int I1 = S.dims[0], I2 = S.dims[1], I3 = S.dims[2];
-    const int o1 = bb1 * S1, o2 = bb2 * S2, o3 = b3 * 32;
-    const bool wantG = kind == PH_FGRAD, wantS = kind == PH_TGRAD;
-    const bool wantF = kind == PH_LOSS_W || kind == PH_LOSS_F;
-    const float* A1 = S.A;
-    const float* A2 = S.A + (int64_t)S.row_off[1] * R;
-    const float* A3 = S.A + (int64_t)S.row_off[2] * R;
-    float* A3s = sm + kOffA3;
-    float* KR = sm + kOffKR;
-    float* Ts = sm + kOffT;
-    float* Ys = sm + kOffY;
-    float* A1t = sm + kOffA1;
-    float* A1st = sm + kOffA1s;
-    float* A2t = sm + kOffA2;
-    float* sv = sm + kOffS;
-    float* acc1 = sm + kOffAcc1;
-    float* acc2 = sm + kOffAcc2;
-    double* red = reinterpret_cast<double*>(sm + kOffRed);
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-
-    for (int i = tid; i < 32 * kLD; i += kBatchThreads) {
-        const int r = i / kLD, j = i - r * kLD;
-        A3s[i] = (j < R && o3 + r < I3) ? __ldcg(A3 + (int64_t)(o3 + r) * R + j) : 0.f;
-    }
-    for (int j = tid; j < kBatchMaxR; j += kBatchThreads) sv[j] = j < R ? __ldcg(S.s + j) : 0.f;
-    if (wantG)
-        for (int i = tid; i < 64 * kBatchMaxR; i += kBatchThreads) acc1[i] = 0.f;   // acc1 and acc2 are adjacent
-
-    float g3[2][4], gsr = 0.f, fsum = 0.f;
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) g3[r][c] = 0.f;
-
-    for (int t1 = 0; t1 < S.n1; ++t1) {
-        const int i1b = o1 + t1 * B1;
-        if (i1b >= I1) break;
-        for (int t2 = 0; t2 < S.n2; ++t2) {
-            const int i2b = o2 + t2 * B2;
-            if (i2b >= I2) break;
-            __syncthreads();   // previous tile done with the panels
-            for (int i = tid; i < B1 * kBatchMaxR; i += kBatchThreads) {
-                const int r = i >> 6, j = i & 63;
-                const float v = (j < R && i1b + r < I1) ? __ldcg(A1 + (int64_t)(i1b + r) * R + j) : 0.f;
-                A1t[i] = v;
-                A1st[i] = v * sv[j];
-            }
-            for (int i = tid; i < B2 * kBatchMaxR; i += kBatchThreads) {
-                const int r = i >> 6, j = i & 63;
-                A2t[i] = (j < R && i2b + r < I2) ? __ldcg(A2 + (int64_t)(i2b + r) * R + j) : 0.f;
-            }
-            for (int i = tid; i < 32 * 32; i += kBatchThreads) {
-                const int row = i >> 5, col = i & 31;
-                const int i1 = i1b + (row >> lb2), i2 = i2b + (row & (B2 - 1)), i3 = o3 + col;
-                Ys[row * 33 + col] =
-                    (i1 < I1 && i2 < I2 && i3 < I3) ? __ldg(X + ((int64_t)i1 * I2 + i2) * I3 + i3) : 0.f;
-            }
-            __syncthreads();
-            for (int i = tid; i < 32 * kBatchMaxR; i += kBatchThreads) {
-                const int row = i >> 6, j = i & 63;
-                KR[row * kLD + j] = A1st[(row >> lb2) * kBatchMaxR + j] * A2t[(row & (B2 - 1)) * kBatchMaxR + j];
-            }
-            __syncthreads();
-            {   // M and Y: thread owns rows {ty, ty+16} x cols {tx, tx+16}
-                float m[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-                for (int j = 0; j < R; ++j) {
-                    const float k0 = KR[ty * kLD + j], k1 = KR[(ty + 16) * kLD + j];
-                    const float c0 = A3s[tx * kLD + j], c1 = A3s[(tx + 16) * kLD + j];
-                    m[0][0] += k0 * c0;
-                    m[0][1] += k0 * c1;
-                    m[1][0] += k1 * c0;
-                    m[1][1] += k1 * c1;
-                }
-#pragma unroll
-                for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        const int row = ty + 16 * rr, col = tx + 16 * cc;
-                        const int i1 = i1b + (row >> lb2), i2 = i2b + (row & (B2 - 1)), i3 = o3 + col;
-                        const bool valid = i1 < I1 && i2 < I2 && i3 < I3;
-                        const float x = Ys[row * 33 + col];
-                        if (wantF) {
-                            float f, y;
-                            loss_eval<float>(S.loss, x, m[rr][cc], S.eps, f, y);
-                            if (valid) fsum += f;
-                        } else {
-                            const float y = loss_dfdm<float>(S.loss, x, m[rr][cc], S.eps);
-                            Ys[row * 33 + col] = valid ? y : 0.f;
-                        }
-                    }
-            }
-            if (wantF) continue;
-            __syncthreads();
-            // T = Y . A3 (rows {ty, ty+16}, cols tx + 16c) and G3 += Y' . KR
-            float tv[2][4];
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) tv[r][c] = 0.f;
-            if (wantG) {
-                for (int k = 0; k < 32; ++k) {
-                    const float y0 = Ys[ty * 33 + k], y1 = Ys[(ty + 16) * 33 + k];
-                    const float z0 = Ys[k * 33 + ty], z1 = Ys[k * 33 + ty + 16];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int j = tx + 16 * c;
-                        const float a3 = A3s[k * kLD + j], kr = KR[k * kLD + j];
-                        tv[0][c] += y0 * a3;
-                        tv[1][c] += y1 * a3;
-                        g3[0][c] += z0 * kr;
-                        g3[1][c] += z1 * kr;
-                    }
-                }
-            } else {
-                for (int k = 0; k < 32; ++k) {
-                    const float y0 = Ys[ty * 33 + k], y1 = Ys[(ty + 16) * 33 + k];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float a3 = A3s[k * kLD + tx + 16 * c];
-                        tv[0][c] += y0 * a3;
-                        tv[1][c] += y1 * a3;
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) Ts[(ty + 16 * r) * kLD + tx + 16 * c] = tv[r][c];
-            __syncthreads();
-            if (wantG) {
-                for (int i = tid; i < B1 * R; i += kBatchThreads) {
-                    const int il = i / R, j = i - il * R;
-                    float acc = 0.f;
-                    for (int i2l = 0; i2l < B2; ++i2l) acc += A2t[i2l * kBatchMaxR + j] * Ts[(il * B2 + i2l) * kLD + j];
-                    acc1[(t1 * B1 + il) * kBatchMaxR + j] += sv[j] * acc;
-                }
-                for (int i = tid; i < B2 * R; i += kBatchThreads) {
-                    const int il = i / R, j = i - il * R;
-                    float acc = 0.f;
-                    for (int i1l = 0; i1l < B1; ++i1l) acc += A1st[i1l * kBatchMaxR + j] * Ts[(i1l * B2 + il) * kLD + j];
-                    acc2[(t2 * B2 + il) * kBatchMaxR + j] += acc;
-                }
-            }
-            if (wantS && tid < R) {
-                float acc = 0.f;
-                for (int row = 0; row < 32; ++row)
-                    acc += A1t[(row >> lb2) * kBatchMaxR + tid] * A2t[(row & (B2 - 1)) * kBatchMaxR + tid] *
-                           Ts[row * kLD + tid];
-                gsr += acc;
-            }
-        }
-    }
-    __syncthreads();
-    if (wantG) {
-        float* G1 = S.G;
-        float* G2 = S.G + (int64_t)S.row_off[1] * R;
-        float* G3 = S.G + (int64_t)S.row_off[2] * R;
-        for (int i = tid; i < S1 * R; i += kBatchThreads) {
-            const int r = i / R, j = i - r * R;
-            const float v = acc1[r * kBatchMaxR + j];
-            if (o1 + r < I1 && v != 0.f) atomicAdd(G1 + (int64_t)(o1 + r) * R + j, v);
-        }
-        for (int i = tid; i < S2 * R; i += kBatchThreads) {
-            const int r = i / R, j = i - r * R;
-            const float v = acc2[r * kBatchMaxR + j];
-            if (o2 + r < I2 && v != 0.f) atomicAdd(G2 + (int64_t)(o2 + r) * R + j, v);
-        }
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i3 = o3 + ty + 16 * r, j = tx + 16 * c;
-                if (i3 < I3 && j < R && g3[r][c] != 0.f) atomicAdd(G3 + (int64_t)i3 * R + j, g3[r][c]);  // KR carries s
-            }
-    }
-    if (wantS && tid < R && gsr != 0.f) atomicAdd(S.gs + tid, gsr);
-    if (wantF) {
-        const double tot = block_sum((double)fsum, red);
-        if (tid == 0 && tot != 0.0) atomicAdd(&st_obj->F_new, tot);
-    }
+    BoxGeom g;
+    g.R = R;
+    g.loss = S.loss;
+    g.eps = S.eps;
+    g.I1 = S.dims[0];
+    g.I2 = S.dims[1];
+    g.I3 = S.dims[2];
+    g.lb1 = S.b1log;
+    g.n1 = S.n1;
+    g.n2 = S.n2;
+    g.o1 = bb1 * B1 * S.n1;
+    g.o2 = bb2 * B2 * S.n2;
+    g.o3 = b3 * 32;
+    g.A1 = S.A;
+    g.A2 = S.A + (int64_t)S.row_off[1] * R;
+    g.A3 = S.A + (int64_t)S.row_off[2] * R;
+    g.s = S.s;
+    g.X = X;
+    g.G1 = S.G;
+    g.G2 = S.G + (int64_t)S.row_off[1] * R;
+    g.G3 = S.G + (int64_t)S.row_off[2] * R;
+    g.gs = S.gs;
+    g.f = st_obj ? &st_obj->F_new : nullptr;
+    const int want = kind == PH_FGRAD ? BOX_FACTORS : (kind == PH_TGRAD ? BOX_TEMPORAL : BOX_LOSS);
+    dense_box_any(g, want, sm);
 }
 
 // Gram pair list of a unit: npairs = 1 -> (A,A); 2 -> (A,A), (D,A);

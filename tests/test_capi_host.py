@@ -110,7 +110,7 @@ def test_batch_argument_errors_are_synchronous_without_a_gpu(sg):
     assert sg.sgcp_batch_opts_default(ctypes.byref(opts)) == sg.OK
     assert (opts.autotune, opts.tune_reps, opts.grid_blocks, opts.spin_limit) == (0, 3, 0, 0)
     bad_entry = (sg.sgcp_tune_entry * 1)()
-    bad_entry[0].b1log, bad_entry[0].n1, bad_entry[0].n2 = 5, 1, 1             # tile row split out of range
+    bad_entry[0].b1log, bad_entry[0].n1, bad_entry[0].n2 = 1, 1, 1             # tile row split out of range
     opts.table, opts.n_table = bad_entry, 1
     assert create([good], opts) == sg.ERR_ARG
     assert sg.sgcp_batch_create(0, None, arr, None, None, ctypes.byref(out)) == sg.ERR_ARG

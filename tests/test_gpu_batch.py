@@ -101,7 +101,7 @@ def test_autotuned_unit_shapes_keep_parity(sg):
     table, cfg = run_and_compare(sg, streams, 2, tol=2e-4, batch_kw=dict(autotune=True, tune_reps=2))
     assert len(table) == 3 and all(e["us"] > 0 for e in table)
     for e in cfg:
-        assert 1 <= e["b1log"] <= 4 and (1 << e["b1log"]) * e["n1"] <= 32 and (32 >> e["b1log"]) * e["n2"] <= 32
+        assert 2 <= e["b1log"] <= 4 and (1 << e["b1log"]) * e["n1"] <= 32 and (64 >> e["b1log"]) * e["n2"] <= 32
     # a later batch reuses the table without timing again
     streams2 = make_streams(1, seed=8, shapes=SHAPES[:3])
     table2, cfg2 = run_and_compare(sg, streams2, 1, tol=2e-4, batch_kw=dict(table=table))
@@ -113,7 +113,7 @@ def test_single_shape_choice_across_tiles(sg):
     schedule, not arithmetic): compare each against the oracle."""
     streams = make_streams(1, seed=9, shapes=[((45, 37, 40), 8, "gaussian")])
     key = dict(bucket=(2, 2, 2), rank=8, loss=0, us=0.0)
-    for b1log, n1, n2 in [(1, 1, 1), (2, 8, 4), (3, 2, 1), (4, 2, 4)]:
+    for b1log, n1, n2 in [(2, 1, 1), (2, 8, 2), (3, 2, 1), (4, 2, 8)]:
         run_and_compare(sg, streams, 1, tol=2e-4, batch_kw=dict(table=[dict(key, b1log=b1log, n1=n1, n2=n2)]))
 
 
