@@ -9,15 +9,24 @@
 //                        hi/lo splits (Henry, Tang, Heinecke, ARITH 2019), so
 //                        m keeps ~16 bits and y = df/dm(x, m) stays accurate
 //   Y  = df/dm(X, M)     FP32 from TMEM, stored as the MTTKRP operand type
-//   T  = Y . A3          -> G1, G2, gs by SIMT reductions (as the FP32 kernel)
-//   G3 += Y' . KR        accumulated in TMEM over the block's tiles
+//   T  = Y . A3          -> G1, G2, gs by SIMT reductions (float4 atomics per tile)
+//   G3 += Y' . KR        accumulated in TMEM while the i3 block stays the same
 // All shared-memory operands use the no-swizzle canonical layout: element
 // (r, k) of an (rows x K) tile at (r/8)*SBO + (k/8)*128 + (r%8)*16 + (k%8)*2
-// bytes, SBO = K/8 * 128; transposed uses read the same tile MN-major.  A block keeps one i3 block and walks a
-// sub-box of n1 x n2 row tiles; G1 / G2 rows accumulate in shared memory and
-// G3 in TMEM, and everything is added to global memory once per block.
+// bytes, SBO = K/8 * 128; transposed uses read the same tile MN-major.
+//
+// Persistent schedule: one block of 512 threads per SM takes a contiguous run
+// of tiles (i3 block major, then i1, then i2).  The model product of the next
+// tile runs on the tensor core while this tile's loss epilogue, T read-back
+// and reductions run on the CUDA cores: two TMEM model accumulators and two
+// KR panels alternate, the next X tile arrives by cp.async.bulk and the next
+// factor rows by cp.async behind the current tile's work.  Per tile:
+//   wait M(t), X(t) -> stage rows(t+1) -> epilogue(t): Y -> copy X(t+1) ->
+//   issue T, G3 (t) -> build KR(t+1) -> issue M(t+1) -> wait T -> reductions(t)
+// A change of i3 block drains the tensor core first (the A3 panel changes).
 // Every wait on an mbarrier is bounded; on timeout the kernel records
-// ERRB_TIMEOUT in the error word, stops issuing work, and frees its TMEM.
+// ERRB_TIMEOUT in the error word, stops issuing work, lets its own copies land
+// and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,8 +40,8 @@ namespace {
 constexpr int kRows = 128;      // (i1, i2) rows per tile
 constexpr int kB1 = 8, kB2 = 16;
 constexpr int kCols = 128;      // i3 columns per tile
-constexpr int kThreads = 256;
-constexpr int kTmemCols = 256;  // D1: [0,128), T: [128, 128+R), G3: [192, 192+R)
+constexpr int kThreads = 512;
+constexpr int kTmemCols = 512;  // D1 x 2: [0, 256), T: [256, 256 + R), G3: [320, 320 + R)
 constexpr int kXld = 132;       // row stride (floats) of the X tile in shared memory: 16-byte aligned, conflict-free
 constexpr long kWaitLimit = 1L << 26;
 
@@ -106,69 +115,91 @@ struct Op<false> {
     static __device__ __forceinline__ T cvt(float x) { return __float2half_rn(x); }
 };
 
-}  // namespace
 
-// Shared-memory plan (bytes), R = rank (multiple of 16, <= 64).  Every tile is
-// stored once, K-major canonical in its natural orientation; the GEMMs that
-// need it transposed read it through an MN-major descriptor (the core matrices
-// of a K-major (rows x K) tile are exactly the core matrices of the MN-major
-// (K x rows) view), so no transposed copies are built:
-//   KRhi, KRlo   [128 rows][R]  bf16     GEMM1 A (K-major);  GEMM3 B (MN-major, bf16 mode)
-//   KR16         [128 rows][R]  fp16     GEMM3 B (MN-major, fp16 mode)
-//   A3hi, A3lo   [128 i3][R]    bf16     GEMM1 B (K-major);  GEMM2 B (MN-major, bf16 mode)
-//   A316         [128 i3][R]    fp16     GEMM2 B (MN-major, fp16 mode)
-//   Yr           [128 rows][128 i3] op   GEMM2 A (K-major);  GEMM3 A (MN-major);
-//                                        then reused as Ts [R][128] f32 (T staged for the
-//                                        G1 / G2 / gs reductions, rows XOR-swizzled by j)
-//   Xs           [128 rows][132] f32     X tile, bulk-copied (TMA) one tile ahead
-//   A1t, A1st    [8][64], A2t [16][64], sv [64], acc1 [S1][64], acc2 [S2][64], gsacc [64]  f32
-template <bool BF16>
+// Shared-memory plan (bytes), R = rank (multiple of 16, <= 64), in this order:
+//   KRh[0], KRh[1] [128 rows][R] bf16   GEMM1 A hi (K-major); GEMM3 B (MN-major) in bf16 mode
+//                                       (fp16 mode keeps one KRh)
+//   KRl            [128 rows][R] bf16   GEMM1 A lo
+//   KR3[0], KR3[1] [128 rows][R] fp16   GEMM3 B in fp16 mode
+//   A3hi, A3lo     [128 i3][R]   bf16   GEMM1 B (K-major); GEMM2 B (MN-major) in bf16 mode
+//   A316           [128 i3][R]   fp16   GEMM2 B in fp16 mode
+//   Yr             [128 rows][128 i3] op  GEMM2 A (K-major), GEMM3 A (MN-major);
+//                                       then Ts [128 rows][R + 4] f32 (T for the reductions)
+//   Xs             [128 rows][132] f32  X tile (cp.async.bulk, one row per thread)
+//   stage          [2][24 rows][64] f32 A1 rows (8) and A2 rows (16) of a tile (cp.async)
+//   sv [64], gsacc [64] f32
+struct TcPlan {
+    int KRh0, KRh1, KRl, KR30, KR31, A3hi, A3lo, A316, Yr, Xs, stage, sv, gsacc, total;
+};
+
+__host__ __device__ inline TcPlan tc_plan(int R, bool bf16) {
+    TcPlan p{};
+    const int kr = kRows * R * 2, a3 = kCols * R * 2;
+    int o = 0;
+    p.KRh0 = o; o += kr;
+    p.KRh1 = bf16 ? o : p.KRh0; o += bf16 ? kr : 0;
+    p.KRl = o; o += kr;
+    p.KR30 = o; o += bf16 ? 0 : kr;
+    p.KR31 = o; o += bf16 ? 0 : kr;
+    if (bf16) p.KR30 = p.KR31 = -1;
+    p.A3hi = o; o += a3;
+    p.A3lo = o; o += a3;
+    p.A316 = bf16 ? -1 : o; o += bf16 ? 0 : a3;
+    p.Yr = o;
+    const int yb = kRows * kCols * 2, tb = kRows * (R + 4) * 4;
+    o += (yb > tb ? yb : tb);
+    o = (o + 1023) & ~1023;
+    p.Xs = o; o += kRows * kXld * 4;
+    p.stage = o; o += 2 * 24 * 64 * 4;
+    p.sv = o; o += 64 * 4;
+    p.gsacc = o; o += 64 * 4;
+    p.total = o;
+    return p;
+}
+
+template <bool BF16, int LOSS>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_dense3_tc(const DenseGradArgs<float> a, int n1, int n2, int nb1, int nb2, int* err) {
+    k_dense3_tc(const DenseGradArgs<float> a, int t1n, int t2n, int ntiles, int* err) {
     using OT = typename Op<BF16>::T;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ __align__(8) uint64_t mbar_x;
+    __shared__ __align__(8) uint64_t mbar1, mbar2, mbar_x;
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
-    __shared__ double fred[8];
+    __shared__ double fred[kThreads / 32];
     if (a.skip && *a.skip) return;
     const int R = a.R;
-    const int S1 = kB1 * n1, S2 = kB2 * n2;
+    const TcPlan P = tc_plan(R, BF16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = tid & 127, half = tid >> 7;       // TMEM lane of this thread and its column half
+    const int quarter = warp & 3, cq = warp >> 2;     // TMEM lane quarter and column quarter of this warp
+    const int row = 32 * quarter + lane;              // TMEM lane = tile row of this thread
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
     const int64_t I1 = a.dims[0], I2 = a.dims[1], I3 = a.dims[2];
-    const int bid = blockIdx.x;
-    const int b3 = bid / (nb1 * nb2), rem = bid - b3 * nb1 * nb2;
-    const int bb1 = rem / nb2, bb2 = rem - bb1 * nb2;
-    const int64_t o1 = (int64_t)bb1 * S1, o2 = (int64_t)bb2 * S2, o3 = (int64_t)b3 * kCols;
     const bool wantG = (a.want & SGCP_WANT_FACTORS) != 0;
     const bool wantS = (a.want & SGCP_WANT_TEMPORAL) != 0;
     const bool wantF = (a.want & SGCP_WANT_LOSS) != 0;
+    const bool g23 = wantG || wantS;
     const float ysc = a.y_scale ? *a.y_scale : 1.0f;
     const float* X = reinterpret_cast<const float*>(a.slice ? a.slice->vals : a.inline_slice.vals);
-    // rows of X are 16-byte aligned: bulk copies (else plain loads)
     const bool xtma = (I3 % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    // this block's run of tiles
+    const int tb = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
+    const int te = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
 
-    unsigned char* p = sm;
-    __nv_bfloat16* KRhi = reinterpret_cast<__nv_bfloat16*>(p); p += kRows * R * 2;
-    __nv_bfloat16* KRlo = reinterpret_cast<__nv_bfloat16*>(p); p += kRows * R * 2;
-    __nv_bfloat16* A3hi = reinterpret_cast<__nv_bfloat16*>(p); p += kCols * R * 2;
-    __nv_bfloat16* A3lo = reinterpret_cast<__nv_bfloat16*>(p); p += kCols * R * 2;
-    __half* KR16 = reinterpret_cast<__half*>(p); p += BF16 ? 0 : kRows * R * 2;
-    __half* A316 = reinterpret_cast<__half*>(p); p += BF16 ? 0 : kCols * R * 2;
-    OT* Yr = reinterpret_cast<OT*>(p); p += kRows * kCols * 2;
-    float* Ts = reinterpret_cast<float*>(Yr);                       // aliases Yr after GEMM2 / GEMM3
-    float* Xs = reinterpret_cast<float*>(p); p += kRows * kXld * 4;
-    float* A1t = reinterpret_cast<float*>(p); p += kB1 * 64 * 4;
-    float* A1st = reinterpret_cast<float*>(p); p += kB1 * 64 * 4;
-    float* A2t = reinterpret_cast<float*>(p); p += kB2 * 64 * 4;
-    float* sv = reinterpret_cast<float*>(p); p += 64 * 4;
-    float* acc1 = reinterpret_cast<float*>(p); p += S1 * 64 * 4;
-    float* acc2 = reinterpret_cast<float*>(p); p += S2 * 64 * 4;
-    float* gsacc = reinterpret_cast<float*>(p);
+    __nv_bfloat16* KRh[2] = {reinterpret_cast<__nv_bfloat16*>(sm + P.KRh0), reinterpret_cast<__nv_bfloat16*>(sm + P.KRh1)};
+    __nv_bfloat16* KRl = reinterpret_cast<__nv_bfloat16*>(sm + P.KRl);
+    __half* KR3[2] = {BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.KR30),
+                      BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.KR31)};
+    __nv_bfloat16* A3hi = reinterpret_cast<__nv_bfloat16*>(sm + P.A3hi);
+    __nv_bfloat16* A3lo = reinterpret_cast<__nv_bfloat16*>(sm + P.A3lo);
+    __half* A316 = BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.A316);
+    OT* Yr = reinterpret_cast<OT*>(sm + P.Yr);
+    float* Ts = reinterpret_cast<float*>(sm + P.Yr);
+    float* Xs = reinterpret_cast<float*>(sm + P.Xs);
+    float* stage = reinterpret_cast<float*>(sm + P.stage);   // [2][24][64]
+    float* sv = reinterpret_cast<float*>(sm + P.sv);
+    float* gsacc = reinterpret_cast<float*>(sm + P.gsacc);
+    const int ldT = R + 4;
 
-    // ---- set-up: TMEM, mbarrier, accumulators, the block's A3 panels
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                      "r"(kTmemCols));
@@ -176,314 +207,408 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (tid == 0) {
         abort_flag = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar1)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar2)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_x)), "r"(kRows));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    for (int j = tid; j < 64; j += kThreads) sv[j] = j < R ? a.s[j] : 0.0f;
-    for (int i = tid; i < (S1 + S2 + 1) * 64; i += kThreads) acc1[i] = 0.0f;
-    __syncthreads();
-    // A3 panel: item = (i3 row, 8 consecutive j), 16-byte stores
-    for (int i = tid; i < kCols * (R / 8); i += kThreads) {
-        const int c = i / (R / 8), j8 = (i - c * (R / 8)) * 8;
-        const bool cv = o3 + c < I3;
-        uint32_t hi[4], lo[4], h16[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float v0 = cv ? a.A[2][(o3 + c) * R + j8 + 2 * q] : 0.0f;
-            const float v1 = cv ? a.A[2][(o3 + c) * R + j8 + 2 * q + 1] : 0.0f;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
-            const __half2 f = __floats2half2_rn(v0, v1);
-            hi[q] = *reinterpret_cast<const uint32_t*>(&h);
-            lo[q] = *reinterpret_cast<const uint32_t*>(&l);
-            h16[q] = *reinterpret_cast<const uint32_t*>(&f);
-        }
-        const uint32_t off = cano(c, j8, R);
-        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A3hi) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A3lo) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        if (!BF16)
-            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A316) + off) = make_uint4(h16[0], h16[1], h16[2], h16[3]);
+    for (int j = tid; j < 64; j += kThreads) {
+        sv[j] = j < R ? a.s[j] : 0.0f;
+        gsacc[j] = 0.0f;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
-    const uint32_t tD1 = tmem, tT = tmem + 128, tG3 = tmem + 192;
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t tT = tmem + 256, tG3 = tmem + 320;
     const uint32_t id_m = make_idesc(128, kCols, true, false, false);
     const uint32_t id_2 = make_idesc(128, R, BF16, false, true);    // A = Y K-major, B = A3 MN-major
     const uint32_t id_3 = make_idesc(128, R, BF16, true, true);     // A = Y' MN-major, B = KR MN-major
-    const uint32_t krmt = smem_u32(BF16 ? (const void*)KRhi : (const void*)KR16);
-    const uint32_t a3mt = smem_u32(BF16 ? (const void*)A3hi : (const void*)A316);
-    uint32_t phase = 0, phase_x = 0;
-    int pending_x = 0;                        // bulk copies issued and not yet waited for (uniform)
-    float fsum = 0.0f;
-    int tiles_done = 0;
-    // threads 0..127: each bulk-copies its X row of tile (a1, a2) into Xs; mbar_x counts the 128
-    // arrivals and the transferred bytes
-    auto issue_x = [&](int64_t a1, int64_t a2) {
-        const int64_t ncol = (I3 - o3) < kCols ? (I3 - o3) : kCols;
-        const uint32_t rowbytes = (uint32_t)ncol * 4;
-        const int r = tid;
-        const int64_t i1 = a1 + r / kB2, i2 = a2 + r % kB2;
-        if (i1 < I1 && i2 < I2) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_x)),
-                         "r"(rowbytes) : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(Xs + r * kXld)), "l"(X + (i1 * I2 + i2) * I3 + o3), "r"(rowbytes),
-                         "r"(smem_u32(&mbar_x))
-                         : "memory");
-        } else {
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mbar_x)) : "memory");
+    const uint32_t sboR = (uint32_t)R * 16;                         // 8-row step of an R-wide tile
+
+    struct TileIx {
+        int b3;
+        int64_t i1b, i2b, o3;
+    };
+    auto decode = [&](int t) {
+        TileIx x;
+        const int i2t = t % t2n, rest = t / t2n;
+        const int i1t = rest % t1n;
+        x.b3 = rest / t1n;
+        x.i1b = (int64_t)i1t * kB1;
+        x.i2b = (int64_t)i2t * kB2;
+        x.o3 = (int64_t)x.b3 * kCols;
+        return x;
+    };
+    // A1 (8 rows) and A2 (16 rows) of a tile into stage[buf] by cp.async, zero-filled outside the slice
+    auto stage_rows = [&](const TileIx& x, int buf) {
+        const int per = R / 4;                    // 16-byte chunks per row
+        const int n = 24 * per;
+        for (int i = tid; i < n; i += kThreads) {
+            const int r = i / per, c = (i - r * per) * 4;
+            const bool is1 = r < kB1;
+            const int64_t gr = is1 ? x.i1b + r : x.i2b + (r - kB1);
+            const bool ok = is1 ? gr < I1 : gr < I2;
+            const float* src = (is1 ? a.A[0] : a.A[1]) + (ok ? gr * R + c : 0);
+            const uint32_t dst = smem_u32(stage + (buf * 24 + r) * 64 + c);
+            const uint32_t bytes = ok ? 16u : 0u;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // A3 panel of an i3 block: item = (i3 row, 8 consecutive j), 16-byte stores
+    auto build_a3 = [&](int64_t o3) {
+        for (int i = tid; i < kCols * (R / 8); i += kThreads) {
+            const int c = i / (R / 8), j8 = (i - c * (R / 8)) * 8;
+            const bool cv = o3 + c < I3;
+            uint32_t hi[4], lo[4], h16[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float v0 = cv ? __ldg(a.A[2] + (o3 + c) * R + j8 + 2 * q) : 0.0f;
+                const float v1 = cv ? __ldg(a.A[2] + (o3 + c) * R + j8 + 2 * q + 1) : 0.0f;
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+                const __half2 f = __floats2half2_rn(v0, v1);
+                hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+                lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+                h16[q] = *reinterpret_cast<const uint32_t*>(&f);
+            }
+            const uint32_t off = cano(c, j8, R);
+            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A3hi) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A3lo) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            if (!BF16)
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(A316) + off) =
+                    make_uint4(h16[0], h16[1], h16[2], h16[3]);
         }
     };
-    if (xtma && o1 < I1 && o2 < I2) {
-        if (tid < kRows) issue_x(o1, o2);
-        pending_x = 1;
-    }
+    // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16)
+    auto build_kr = [&](int sbuf, int kbuf) {
+        const float* A1 = stage + sbuf * 24 * 64;
+        const float* A2 = A1 + kB1 * 64;
+        __nv_bfloat16* kh = KRh[kbuf];
+        for (int i = tid; i < kRows * (R / 8); i += kThreads) {
+            const int r = i / (R / 8), j8 = (i - r * (R / 8)) * 8;
+            const float* a1 = A1 + (r / kB2) * 64 + j8;
+            const float* a2 = A2 + (r % kB2) * 64 + j8;
+            uint32_t hi[4], lo[4], h16[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float v0 = sv[j8 + 2 * q] * a1[2 * q] * a2[2 * q];
+                const float v1 = sv[j8 + 2 * q + 1] * a1[2 * q + 1] * a2[2 * q + 1];
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
+                const __half2 f = __floats2half2_rn(v0, v1);
+                hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+                lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+                h16[q] = *reinterpret_cast<const uint32_t*>(&f);
+            }
+            const uint32_t off = cano(r, j8, R);
+            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(kh) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KRl) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            if (!BF16)
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KR3[kbuf]) + off) =
+                    make_uint4(h16[0], h16[1], h16[2], h16[3]);
+        }
+    };
+    // operand writes by every thread -> visible to the tensor core
+    auto publish_smem = [&]() {
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    };
+    auto issue_gemm1 = [&](int dbuf, int kbuf) {
+        if (tid == 0) {
+            const uint32_t krh = smem_u32(KRh[kbuf]), krl = smem_u32(KRl), a3h = smem_u32(A3hi), a3l = smem_u32(A3lo);
+            const uint32_t Aop[3] = {krh, krh, krl}, Bop[3] = {a3h, a3l, a3h};
+            const uint32_t d = tmem + (uint32_t)dbuf * 128;
+            for (int sp = 0; sp < 3; ++sp)
+                for (int kk = 0; kk < R / 16; ++kk)
+                    mma(d, make_desc(Aop[sp] + kk * 256, 128, sboR), make_desc(Bop[sp] + kk * 256, 128, sboR), id_m,
+                        (sp > 0 || kk > 0) ? 1u : 0u);
+            commit(&mbar1);
+        }
+    };
+    auto issue_gemm23 = [&](int kbuf, bool g3acc) {
+        if (tid == 0) {
+            const uint32_t yr = smem_u32(Yr);
+            const uint32_t a3mt = smem_u32(BF16 ? (const void*)A3hi : (const void*)A316);
+            const uint32_t krmt = smem_u32(BF16 ? (const void*)KRh[kbuf] : (const void*)KR3[kbuf]);
+            for (int kk = 0; kk < kCols / 16; ++kk)    // K = i3
+                mma(tT, make_desc(yr + kk * 256, 128, 2048), make_desc(a3mt + kk * 2 * sboR, sboR, 128), id_2,
+                    kk > 0 ? 1u : 0u);
+            if (wantG)
+                for (int kk = 0; kk < kRows / 16; ++kk)   // K = rows
+                    mma(tG3, make_desc(yr + kk * 4096, 2048, 128), make_desc(krmt + kk * 2 * sboR, sboR, 128), id_3,
+                        (g3acc || kk > 0) ? 1u : 0u);
+            commit(&mbar2);
+        }
+    };
+    // threads 0..127 bulk-copy their X row of a tile; mbar_x counts the 128 arrivals and the bytes
+    auto issue_x = [&](const TileIx& x) {
+        if (tid < kRows) {
+            const int64_t ncol = (I3 - x.o3) < kCols ? (I3 - x.o3) : kCols;
+            const uint32_t rowbytes = (uint32_t)ncol * 4;
+            const int64_t i1 = x.i1b + tid / kB2, i2 = x.i2b + tid % kB2;
+            if (i1 < I1 && i2 < I2) {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_x)),
+                             "r"(rowbytes) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(smem_u32(Xs + tid * kXld)), "l"(X + (i1 * I2 + i2) * I3 + x.o3), "r"(rowbytes),
+                             "r"(smem_u32(&mbar_x))
+                             : "memory");
+            } else {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mbar_x)) : "memory");
+            }
+        }
+    };
+    auto fail = [&]() {
+        if (tid == 0) {
+            abort_flag = 1;
+            set_err(err, ERRB_TIMEOUT);
+        }
+    };
 
-    for (int t1 = 0; t1 < n1; ++t1) {
-        const int64_t i1b = o1 + (int64_t)t1 * kB1;
-        if (i1b >= I1) break;
-        for (int t2 = 0; t2 < n2; ++t2) {
-            const int64_t i2b = o2 + (int64_t)t2 * kB2;
-            if (i2b >= I2) break;
-            if (abort_flag) break;
-            // next tile of this block (for the X prefetch)
-            int64_t n1b = i1b, n2b = i2b + kB2;
-            if (t2 + 1 >= n2 || n2b >= I2) {
-                n1b = i1b + kB1;
-                n2b = o2;
-                if (t1 + 1 >= n1) n1b = I1;   // none
-            }
-            // ---- factor rows of the tile and the Khatri-Rao panel KR = (s * A1) (.) A2
-            for (int i = tid; i < kB1 * R; i += kThreads) {
-                const int r = i / R, j = i - r * R;
-                const float v = (i1b + r < I1) ? a.A[0][(i1b + r) * R + j] : 0.0f;
-                A1t[r * 64 + j] = v;
-                A1st[r * 64 + j] = v * sv[j];
-            }
-            for (int i = tid; i < kB2 * R; i += kThreads) {
-                const int r = i / R, j = i - r * R;
-                A2t[r * 64 + j] = (i2b + r < I2) ? a.A[1][(i2b + r) * R + j] : 0.0f;
-            }
-            __syncthreads();
-            for (int i = tid; i < kRows * (R / 8); i += kThreads) {
-                const int r = i / (R / 8), j8 = (i - r * (R / 8)) * 8;
-                const float* a1 = A1st + (r / kB2) * 64 + j8;
-                const float* a2 = A2t + (r % kB2) * 64 + j8;
-                uint32_t hi[4], lo[4], h16[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float v0 = a1[2 * q] * a2[2 * q], v1 = a1[2 * q + 1] * a2[2 * q + 1];
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                    const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
-                    const __half2 f = __floats2half2_rn(v0, v1);
-                    hi[q] = *reinterpret_cast<const uint32_t*>(&h);
-                    lo[q] = *reinterpret_cast<const uint32_t*>(&l);
-                    h16[q] = *reinterpret_cast<const uint32_t*>(&f);
-                }
-                const uint32_t off = cano(r, j8, R);
-                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KRhi) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KRlo) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                if (!BF16)
-                    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KR16) + off) =
-                        make_uint4(h16[0], h16[1], h16[2], h16[3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            // ---- GEMM1: M = KR A3' in three bf16 products
-            if (tid == 0) {
-                const uint32_t sboR = (uint32_t)R * 16;
-                const uint32_t krh = smem_u32(KRhi), krl = smem_u32(KRlo), a3h = smem_u32(A3hi), a3l = smem_u32(A3lo);
-                const uint32_t Aop[3] = {krh, krh, krl}, Bop[3] = {a3h, a3l, a3h};
-                for (int sp = 0; sp < 3; ++sp)
-                    for (int kk = 0; kk < R / 16; ++kk)
-                        mma(tD1, make_desc(Aop[sp] + kk * 256, 128, sboR), make_desc(Bop[sp] + kk * 256, 128, sboR),
-                            id_m, (sp > 0 || kk > 0) ? 1u : 0u);
-                commit(&mbar);
-            }
-            if (!wait_phase(&mbar, phase)) {
-                if (tid == 0) {
-                    abort_flag = 1;
-                    set_err(err, ERRB_TIMEOUT);
-                }
-            }
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            __syncthreads();
-            if (abort_flag) break;
-            // ---- Y = df/dm(X, M): thread = TMEM lane (row), half = which 64 columns
-            if (xtma) {
-                if (!wait_phase(&mbar_x, phase_x)) {
-                    if (tid == 0) set_err(err, ERRB_TIMEOUT);
-                    abort_flag = 1;
-                }
-                phase_x ^= 1u;
-                pending_x = 0;
-            }
-            {
-                const int r = row;
-                const int64_t i1 = i1b + r / kB2, i2 = i2b + r % kB2;
-                const bool rv = i1 < I1 && i2 < I2;
-                const float* xrow = X + (i1 * I2 + i2) * I3 + o3;
-                const float* xs = Xs + r * kXld;
+    float fsum = 0.0f;
+    uint32_t ph1 = 0, ph2 = 0, phx = 0;
+    int pending_x = 0;
+    bool g3_started = false;
+    int b3_open = -1;            // i3 block whose G3 sits in TMEM
+    TileIx cur{};
+    if (tb < te) {
+        cur = decode(tb);
+        build_a3(cur.o3);
+        stage_rows(cur, 0);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        build_kr(0, 0);
+        publish_smem();
+        issue_gemm1(0, 0);
+        if (xtma) {
+            issue_x(cur);
+            pending_x = 1;
+        }
+    }
+    for (int t = tb, k = 0; t < te; ++t, ++k) {
+        const int cb = k & 1;
+        const bool has_next = t + 1 < te;
+        const TileIx nxt = has_next ? decode(t + 1) : cur;
+        // ---- wait for M(t) and X(t)
+        if (!wait_phase(&mbar1, ph1)) fail();
+        ph1 ^= 1u;
+        if (xtma) {
+            if (!wait_phase(&mbar_x, phx)) fail();
+            phx ^= 1u;
+            pending_x = 0;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (abort_flag) break;
+        if (has_next) stage_rows(nxt, (k + 1) & 1);
+        // ---- epilogue: Y = df/dm(X, M) for columns [32 cq, 32 cq + 32) of this thread's row
+        {
+            const int64_t i1 = cur.i1b + row / kB2, i2 = cur.i2b + row % kB2;
+            const bool rv = i1 < I1 && i2 < I2;
+            const bool interior = cur.i1b + kB1 <= I1 && cur.i2b + kB2 <= I2 && cur.o3 + kCols <= I3 && xtma;
+            const float* xrow = X + (i1 * I2 + i2) * I3 + cur.o3;
+            const float* xs = Xs + row * kXld;
+            const uint32_t dcol = tmem + (uint32_t)cb * 128 + lane_base;
+            unsigned char* yb = reinterpret_cast<unsigned char*>(Yr);
 #pragma unroll 1
-                for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
-                    float m[16], x[16];
-                    tmem_ld16(tD1 + lane_base + (uint32_t)c0, m);
-                    if (xtma) {
+            for (int h = 0; h < 2; ++h) {
+                const int c0 = 32 * cq + 16 * h;
+                float m[16], x[16], y[16];
+                tmem_ld16(dcol + (uint32_t)c0, m);
+                if (xtma) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float4 v = *reinterpret_cast<const float4*>(xs + c0 + 4 * q);
-                            x[4 * q] = v.x;
-                            x[4 * q + 1] = v.y;
-                            x[4 * q + 2] = v.z;
-                            x[4 * q + 3] = v.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) x[q] = (rv && o3 + c0 + q < I3) ? __ldg(xrow + c0 + q) : 0.0f;
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v = *reinterpret_cast<const float4*>(xs + c0 + 4 * q);
+                        x[4 * q] = v.x;
+                        x[4 * q + 1] = v.y;
+                        x[4 * q + 2] = v.z;
+                        x[4 * q + 3] = v.w;
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) x[q] = (rv && cur.o3 + c0 + q < I3) ? __ldg(xrow + c0 + q) : 0.0f;
+                }
+                if (interior) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        y[q] = loss_dfdm<float>(LOSS, x[q], m[q], a.eps) * ysc;
+                        if (wantF) {
+                            float f, yy;
+                            loss_eval<float>(LOSS, x[q], m[q], a.eps, f, yy);
+                            fsum += f * ysc;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const bool valid = rv && (cur.o3 + c0 + q < I3);
+                        y[q] = valid ? loss_dfdm<float>(LOSS, x[q], m[q], a.eps) * ysc : 0.0f;
+                        if (wantF && valid) {
+                            float f, yy;
+                            loss_eval<float>(LOSS, x[q], m[q], a.eps, f, yy);
+                            fsum += f * ysc;
+                        }
+                    }
+                }
+                if (g23) {
                     uint32_t packed[8];
 #pragma unroll
                     for (int q = 0; q < 16; q += 2) {
-                        float y2[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const bool valid = rv && (o3 + c0 + q + e < I3);
-                            float y = 0.0f;
-                            if (valid) {
-                                y = loss_dfdm<float>(a.loss, x[q + e], m[q + e], a.eps) * ysc;
-                                if (wantF) {
-                                    float f, yy;
-                                    loss_eval<float>(a.loss, x[q + e], m[q + e], a.eps, f, yy);
-                                    fsum += f * ysc;
-                                }
-                            }
-                            y2[e] = y;
-                        }
                         if (BF16) {
-                            const __nv_bfloat162 h = __floats2bfloat162_rn(y2[0], y2[1]);
-                            packed[q / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                            const __nv_bfloat162 hh = __floats2bfloat162_rn(y[q], y[q + 1]);
+                            packed[q / 2] = *reinterpret_cast<const uint32_t*>(&hh);
                         } else {
-                            const __half2 h = __floats2half2_rn(y2[0], y2[1]);
-                            packed[q / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                            const __half2 hh = __floats2half2_rn(y[q], y[q + 1]);
+                            packed[q / 2] = *reinterpret_cast<const uint32_t*>(&hh);
                         }
                     }
-                    unsigned char* yb = reinterpret_cast<unsigned char*>(Yr);
-                    *reinterpret_cast<uint4*>(yb + cano(r, c0, kCols)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    *reinterpret_cast<uint4*>(yb + cano(r, c0 + 8, kCols)) = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    *reinterpret_cast<uint4*>(yb + cano(row, c0, kCols)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    *reinterpret_cast<uint4*>(yb + cano(row, c0 + 8, kCols)) = make_uint4(packed[4], packed[5], packed[6], packed[7]);
                 }
             }
-            asm volatile("fence.proxy.async.shared::cta;");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (abort_flag) break;
-            // Xs is consumed: prefetch the next tile's X behind the rest of this tile
-            if (xtma && n1b < I1 && n2b < I2) {
-                if (tid < kRows) issue_x(n1b, n2b);
-                pending_x = 1;
-            }
-            // ---- GEMM2: T = Y A3 ; GEMM3: G3 += Y' KR
-            if (tid == 0) {
-                const uint32_t yr = smem_u32(Yr);
-                const uint32_t ldR = (uint32_t)R * 16;      // 8-row step of an R-wide tile
-                for (int kk = 0; kk < kCols / 16; ++kk)    // K = i3
-                    mma(tT, make_desc(yr + kk * 256, 128, 2048), make_desc(a3mt + kk * 2 * ldR, ldR, 128), id_2,
-                        kk > 0 ? 1u : 0u);
-                if (wantG)
-                    for (int kk = 0; kk < kRows / 16; ++kk)   // K = rows
-                        mma(tG3, make_desc(yr + kk * 4096, 2048, 128), make_desc(krmt + kk * 2 * ldR, ldR, 128), id_3,
-                            (tiles_done > 0 || kk > 0) ? 1u : 0u);
-                commit(&mbar);
-            }
-            if (!wait_phase(&mbar, phase)) {
-                if (tid == 0) {
-                    abort_flag = 1;
-                    set_err(err, ERRB_TIMEOUT);
-                }
-            }
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            __syncthreads();
-            if (abort_flag) break;
-            ++tiles_done;
-            // ---- T to shared memory (Ts[j][row], consecutive rows in consecutive words)
-            {
-                const int cb = (R % 32 == 0) ? (R / 2) * half : (half ? R : 0);
-                const int ce = (R % 32 == 0) ? cb + R / 2 : R;
-                for (int c0 = cb; c0 < ce; c0 += 16) {
-                    float tv[16];
-                    tmem_ld16(tT + lane_base + (uint32_t)c0, tv);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) Ts[(c0 + q) * 128 + (row ^ ((c0 + q) & 31))] = tv[q];
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            // ---- G1 (and gs) over the 16 i2 rows of each i1; G2 over the 8 i1 rows of each i2
-            for (int it = tid; it < kB1 * R; it += kThreads) {
-                const int j = it % R, i1l = it / R;
-                const float* tr = Ts + j * 128;
-                const int sw = j & 31;
-                float g1 = 0.0f;
-#pragma unroll
-                for (int i2l = 0; i2l < kB2; ++i2l) g1 += A2t[i2l * 64 + j] * tr[(i1l * kB2 + i2l) ^ sw];
-                if (wantG) acc1[(t1 * kB1 + i1l) * 64 + j] += sv[j] * g1;
-                if (wantS) atomicAdd(&gsacc[j], A1t[i1l * 64 + j] * g1);
-            }
-            if (wantG) {
-                for (int it = tid; it < kB2 * R; it += kThreads) {
-                    const int j = it % R, i2l = it / R;
-                    const float* tr = Ts + j * 128;
-                    const int sw = j & 31;
-                    float g2 = 0.0f;
-#pragma unroll
-                    for (int i1l = 0; i1l < kB1; ++i1l) g2 += A1st[i1l * 64 + j] * tr[(i1l * kB2 + i2l) ^ sw];
-                    acc2[(t2 * kB2 + i2l) * 64 + j] += g2;
-                }
-            }
-            __syncthreads();
         }
+        publish_smem();
+        // ---- X of the next tile behind the rest of this one (Xs is consumed)
+        if (xtma && has_next) {
+            issue_x(nxt);
+            pending_x = 1;
+        }
+        // ---- T = Y A3 and G3 += Y' KR of this tile
+        if (g23) {
+            issue_gemm23(cb, g3_started);
+            if (wantG) {
+                g3_started = true;
+                b3_open = cur.b3;
+            }
+        }
+        const bool new_b3 = has_next && nxt.b3 != cur.b3;
+        bool t_ready = false;
+        auto read_t = [&]() {   // T from TMEM to Ts[row][j] (Yr is consumed once T and G3 are done)
+            if (16 * cq < R) {
+                float tv[16];
+                tmem_ld16(tT + lane_base + (uint32_t)(16 * cq), tv);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<float4*>(Ts + row * ldT + 16 * cq + 4 * q) =
+                        make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
+            }
+        };
+        auto flush_g3 = [&](int b3) {   // G3 rows of an i3 block: TMEM -> global
+            if (16 * cq < R) {
+                const int64_t i3 = (int64_t)b3 * kCols + row;
+                float g[16];
+                tmem_ld16(tG3 + lane_base + (uint32_t)(16 * cq), g);
+                if (i3 < I3)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        atomicAdd(reinterpret_cast<float4*>(a.G[2] + i3 * R + 16 * cq + 4 * q),
+                                  make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
+            }
+        };
+        if (new_b3) {   // the A3 panel changes: drain the tensor core first
+            if (g23) {
+                if (!wait_phase(&mbar2, ph2)) fail();
+                ph2 ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                read_t();
+                t_ready = true;
+            }
+            if (wantG && g3_started) {
+                flush_g3(b3_open);
+                g3_started = false;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            build_a3(nxt.o3);
+        }
+        // ---- KR and the model product of the next tile
+        if (has_next) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            build_kr((k + 1) & 1, (k + 1) & 1);
+            publish_smem();
+            issue_gemm1((k + 1) & 1, (k + 1) & 1);
+        }
+        // ---- T of this tile, then the G1 / G2 / gs reductions
+        if (g23) {
+            if (!t_ready) {
+                if (!wait_phase(&mbar2, ph2)) fail();
+                ph2 ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                read_t();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            const float* A1 = stage + cb * 24 * 64;
+            const float* A2 = A1 + kB1 * 64;
+            const int per = R / 4;
+            for (int it = tid; it < (kB1 + kB2) * per; it += kThreads) {
+                const int rr = it / per, j = (it - rr * per) * 4;
+                const float4 s4 = *reinterpret_cast<const float4*>(sv + j);
+                if (rr < kB1) {   // G1 row i1l (and gs): sum over the 16 i2 rows
+                    const int i1l = rr;
+                    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+                    for (int i2l = 0; i2l < kB2; ++i2l) {
+                        const float4 w = *reinterpret_cast<const float4*>(A2 + i2l * 64 + j);
+                        const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
+                        g.x = fmaf(w.x, tv.x, g.x);
+                        g.y = fmaf(w.y, tv.y, g.y);
+                        g.z = fmaf(w.z, tv.z, g.z);
+                        g.w = fmaf(w.w, tv.w, g.w);
+                    }
+                    if (wantS) {
+                        const float4 a1 = *reinterpret_cast<const float4*>(A1 + i1l * 64 + j);
+                        atomicAdd(gsacc + j, a1.x * g.x);
+                        atomicAdd(gsacc + j + 1, a1.y * g.y);
+                        atomicAdd(gsacc + j + 2, a1.z * g.z);
+                        atomicAdd(gsacc + j + 3, a1.w * g.w);
+                    }
+                    if (wantG && cur.i1b + i1l < I1)
+                        atomicAdd(reinterpret_cast<float4*>(a.G[0] + (cur.i1b + i1l) * R + j),
+                                  make_float4(s4.x * g.x, s4.y * g.y, s4.z * g.z, s4.w * g.w));
+                } else if (wantG) {   // G2 row i2l: sum over the 8 i1 rows of (s A1) T
+                    const int i2l = rr - kB1;
+                    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int i1l = 0; i1l < kB1; ++i1l) {
+                        const float4 w = *reinterpret_cast<const float4*>(A1 + i1l * 64 + j);
+                        const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
+                        g.x = fmaf(s4.x * w.x, tv.x, g.x);
+                        g.y = fmaf(s4.y * w.y, tv.y, g.y);
+                        g.z = fmaf(s4.z * w.z, tv.z, g.z);
+                        g.w = fmaf(s4.w * w.w, tv.w, g.w);
+                    }
+                    if (cur.i2b + i2l < I2) atomicAdd(reinterpret_cast<float4*>(a.G[1] + (cur.i2b + i2l) * R + j), g);
+                }
+            }
+        }
+        __syncthreads();   // Ts (= Yr) and the stage buffer of this tile are free
         if (abort_flag) break;
+        cur = nxt;
     }
 
-    // ---- an aborted block still lets its own bulk copy land before shared memory is released
-    if (pending_x) wait_phase(&mbar_x, phase_x);
-    // ---- flush: G3 from TMEM, G1 / G2 / gs from shared memory, the loss
+    // ---- an aborted block still lets its own copies land before shared memory is released
+    if (pending_x) wait_phase(&mbar_x, phx);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (wantG && tiles_done > 0 && !abort_flag) {
-        const int c = row;                    // i3 row of the G3 accumulator
-        const int64_t i3 = o3 + c;
-        const int cb = (R % 32 == 0) ? (R / 2) * half : (half ? R : 0);
-        const int ce = (R % 32 == 0) ? cb + R / 2 : R;
-        for (int j0 = cb; j0 < ce; j0 += 16) {
+    if (wantG && g3_started && !abort_flag) {
+        if (16 * cq < R) {
+            const int64_t i3 = (int64_t)b3_open * kCols + row;
             float g[16];
-            tmem_ld16(tG3 + lane_base + (uint32_t)j0, g);
+            tmem_ld16(tG3 + lane_base + (uint32_t)(16 * cq), g);
             if (i3 < I3)
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (g[q] != 0.0f) atomicAdd(a.G[2] + i3 * R + j0 + q, g[q]);
+                for (int q = 0; q < 4; ++q)
+                    atomicAdd(reinterpret_cast<float4*>(a.G[2] + i3 * R + 16 * cq + 4 * q),
+                              make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
         }
     }
     __syncthreads();
-    if (wantG) {
-        for (int i = tid; i < S1 * R; i += kThreads) {
-            const int r = i / R, j = i - r * R;
-            const float v = acc1[r * 64 + j];
-            if (o1 + r < I1 && v != 0.0f) atomicAdd(a.G[0] + (o1 + r) * R + j, v);
-        }
-        for (int i = tid; i < S2 * R; i += kThreads) {
-            const int r = i / R, j = i - r * R;
-            const float v = acc2[r * 64 + j];
-            if (o2 + r < I2 && v != 0.0f) atomicAdd(a.G[1] + (o2 + r) * R + j, v);
-        }
-    }
     if (wantS)
         for (int j = tid; j < R; j += kThreads)
             if (gsacc[j] != 0.0f) atomicAdd(a.gs + j, gsacc[j]);
@@ -516,46 +641,42 @@ static int tc_num_sms() {
     return n;
 }
 
+template <bool BF16, int LOSS>
+static cudaError_t run_tc(const DenseGradArgs<float>& a, int t1n, int t2n, int ntiles, int grid, size_t smem, int* err,
+                          cudaStream_t st) {
+    cudaFuncSetAttribute(k_dense3_tc<BF16, LOSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_dense3_tc<BF16, LOSS><<<grid, kThreads, smem, st>>>(a, t1n, t2n, ntiles, err);
+    return cudaGetLastError();
+}
+
+template <bool BF16>
+static cudaError_t run_tc_loss(const DenseGradArgs<float>& a, int t1n, int t2n, int ntiles, int grid, size_t smem,
+                               int* err, cudaStream_t st) {
+    switch (a.loss) {
+        case LOSS_GAUSSIAN: return run_tc<BF16, LOSS_GAUSSIAN>(a, t1n, t2n, ntiles, grid, smem, err, st);
+        case LOSS_POISSON: return run_tc<BF16, LOSS_POISSON>(a, t1n, t2n, ntiles, grid, smem, err, st);
+        case LOSS_ODDS: return run_tc<BF16, LOSS_ODDS>(a, t1n, t2n, ntiles, grid, smem, err, st);
+        case LOSS_LOGIT: return run_tc<BF16, LOSS_LOGIT>(a, t1n, t2n, ntiles, grid, smem, err, st);
+        default: return run_tc<BF16, LOSS_IDENTITY_X>(a, t1n, t2n, ntiles, grid, smem, err, st);
+    }
+}
+
+}  // namespace
+
 cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* err, cudaStream_t st,
                                  int64_t* launches) {
     if (a.ndim != 3 || a.R % 16 != 0 || a.R > 64) return cudaErrorInvalidValue;
     const int64_t I1 = a.dims[0], I2 = a.dims[1], I3 = a.dims[2];
     const int64_t nb3 = (I3 + kCols - 1) / kCols;
     const int64_t t1 = (I1 + kB1 - 1) / kB1, t2 = (I2 + kB2 - 1) / kB2;
-    // sub-box of n1 x n2 tiles: minimise (waves x tiles per block), then prefer fewer blocks
-    const int64_t sms = tc_num_sms();
-    int n1 = 1, n2 = 1;
-    int64_t best = -1;
-    for (int m1 = 1; m1 <= 4; m1 *= 2)
-        for (int m2 = 1; m2 <= 2; m2 *= 2) {
-            if (m1 > 1 && (m1 / 2) * kB1 >= I1) continue;
-            if (m2 > 1 && (m2 / 2) * kB2 >= I2) continue;
-            const int64_t blocks = ((t1 + m1 - 1) / m1) * ((t2 + m2 - 1) / m2) * nb3;
-            // tiles on the critical path plus a per-block start-up of about 3/4 of a tile
-            // (TMEM, the A3 panel, an unoverlapped first X copy); ties go to more tiles per block
-            const int64_t cost = ((blocks + sms - 1) / sms) * (m1 * m2 * 64 + 48) - m1 * m2;
-            if (best < 0 || cost < best) {
-                best = cost;
-                n1 = m1;
-                n2 = m2;
-            }
-        }
-    const int nb1 = (int)((t1 + n1 - 1) / n1), nb2 = (int)((t2 + n2 - 1) / n2);
-    const int64_t blocks = (int64_t)nb1 * nb2 * nb3;
-    const int R = a.R;
-    const size_t smem = (size_t)kRows * R * 2 * 2 + (size_t)kCols * R * 2 * 2 +
-                        (bf16 ? 0 : (size_t)(kRows + kCols) * R * 2) + (size_t)kRows * kCols * 2 + (size_t)kRows * kXld * 4 +
-                        (size_t)(2 * kB1 + kB2 + 1) * 64 * 4 + (size_t)(kB1 * n1 + kB2 * n2 + 1) * 64 * 4 + 1024;
-    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-    if (bf16) {
-        cudaFuncSetAttribute(k_dense3_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_dense3_tc<true><<<(unsigned)blocks, kThreads, smem, st>>>(a, n1, n2, nb1, nb2, err);
-    } else {
-        cudaFuncSetAttribute(k_dense3_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_dense3_tc<false><<<(unsigned)blocks, kThreads, smem, st>>>(a, n1, n2, nb1, nb2, err);
-    }
+    const int64_t ntiles = t1 * t2 * nb3;
+    if (ntiles > 0x7fffffff || t1 > 0x7fffffff || t2 > 0x7fffffff) return cudaErrorInvalidValue;
+    const int grid = (int)(ntiles < tc_num_sms() ? ntiles : tc_num_sms());
+    const size_t smem = (size_t)tc_plan(a.R, bf16).total + 1024;
     if (launches) *launches += 1;
-    return cudaGetLastError();
+    if (grid <= 0) return cudaSuccess;
+    return bf16 ? run_tc_loss<true>(a, (int)t1, (int)t2, (int)ntiles, grid, smem, err, st)
+                : run_tc_loss<false>(a, (int)t1, (int)t2, (int)ntiles, grid, smem, err, st);
 }
 
 }  // namespace sgcp
