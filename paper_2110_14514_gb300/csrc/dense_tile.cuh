@@ -20,10 +20,9 @@
 #pragma once
 
 #include "common.cuh"
+#include "sgcp.h"
 
 namespace sgcp {
-
-enum BoxWant : int { BOX_LOSS = 1, BOX_TEMPORAL = 2, BOX_FACTORS = 3 };
 
 constexpr int kBoxThreads = 256;
 constexpr int kBoxMaxS = 32;   // largest box extent along i1 and along i2 (rows)
@@ -69,6 +68,7 @@ struct BoxGeom {
     float* G3;
     float* gs;
     double* f;
+    float ysc;            // multiplies every y and f (1 unless a caller scales the loss)
 };
 
 template <int N>
@@ -120,6 +120,7 @@ __device__ __forceinline__ double box_block_sum(double v, double* red) {
     return tot;
 }
 
+// want: SGCP_WANT_* bits (factor gradients, gradient of s, loss), any combination.
 // Factor, s and slice reads go through L2 (ld.global.cg) for the factors and s,
 // which a persistent caller may have rewritten from another SM, and through the
 // read-only path for X, which no kernel writes while it is read.
@@ -149,7 +150,9 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
     float* acc1 = sm + L::ACC1;
     float* acc2 = sm + L::ACC2;
     double* red = reinterpret_cast<double*>(sm + L::RED);
-    const bool wantF = want == BOX_LOSS, wantS = want == BOX_TEMPORAL, wantG = want == BOX_FACTORS;
+    const bool wantF = (want & SGCP_WANT_LOSS) != 0, wantS = (want & SGCP_WANT_TEMPORAL) != 0;
+    const bool wantG = (want & SGCP_WANT_FACTORS) != 0, wantY = wantG || wantS;
+    const float ysc = g.ysc;
 
     for (int i = tid; i < 32 * RT; i += kBoxThreads) {
         const int c = i / RT, j = i - c * RT;
@@ -237,13 +240,13 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                     if (wantF) {
                         float f, yy;
                         loss_eval<float>(g.loss, x, m[i][c], g.eps, f, yy);
-                        if (valid) fsum += f;
-                        y[i][c] = 0.f;
+                        if (valid) fsum += f * ysc;
+                        y[i][c] = valid ? yy * ysc : 0.f;
                     } else {
-                        y[i][c] = valid ? loss_dfdm<float>(g.loss, x, m[i][c], g.eps) : 0.f;
+                        y[i][c] = valid ? loss_dfdm<float>(g.loss, x, m[i][c], g.eps) * ysc : 0.f;
                     }
                 }
-            if (wantF) continue;
+            if (!wantY) continue;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float v[2] = {y[i][0], y[i][1]};

@@ -124,7 +124,8 @@ __device__ void box_unit(const BatchStream& S, const float* __restrict__ X, int 
     g.G3 = S.G + (int64_t)S.row_off[2] * R;
     g.gs = S.gs;
     g.f = st_obj ? &st_obj->F_new : nullptr;
-    const int want = kind == PH_FGRAD ? BOX_FACTORS : (kind == PH_TGRAD ? BOX_TEMPORAL : BOX_LOSS);
+    g.ysc = 1.0f;
+    const int want = kind == PH_FGRAD ? SGCP_WANT_FACTORS : (kind == PH_TGRAD ? SGCP_WANT_TEMPORAL : SGCP_WANT_LOSS);
     dense_box_any(g, want, sm);
 }
 

@@ -17,10 +17,76 @@
 // keeps the sub-box's G rows in shared memory / registers and adds them to
 // global memory once, so the global atomics per entry are
 // (S1 + S2 + 32) R / (S1 S2 32).
+#include "dense_tile.cuh"
 #include "internal.h"
 #include "sgcp.h"
 
 namespace sgcp {
+
+// FP32 3-way slices with R <= 64 run the register-tiled box of dense_tile.cuh:
+// one block per box of n1 x n2 tiles of 64 (i1, i2) rows sharing 32 i3 columns.
+template <int RT>
+__global__ void __launch_bounds__(kBoxThreads, 2) k_dense3_box(const DenseGradArgs<float> a, int lb1, int n1, int n2,
+                                                                int nb1, int nb2) {
+    extern __shared__ __align__(16) float box_sm[];
+    if (a.skip && *a.skip) return;
+    const int bid = blockIdx.x;
+    const int b3 = bid / (nb1 * nb2), rem = bid - b3 * nb1 * nb2;
+    const int bb1 = rem / nb2, bb2 = rem - bb1 * nb2;
+    const int R = a.R;
+    BoxGeom g;
+    g.R = R;
+    g.loss = a.loss;
+    g.eps = a.eps;
+    g.I1 = (int)a.dims[0];
+    g.I2 = (int)a.dims[1];
+    g.I3 = (int)a.dims[2];
+    g.lb1 = lb1;
+    g.n1 = n1;
+    g.n2 = n2;
+    g.o1 = bb1 * (1 << lb1) * n1;
+    g.o2 = bb2 * (64 >> lb1) * n2;
+    g.o3 = b3 * 32;
+    g.A1 = a.A[0];
+    g.A2 = a.A[1];
+    g.A3 = a.A[2];
+    g.s = a.s;
+    g.X = reinterpret_cast<const float*>(a.slice ? a.slice->vals : a.inline_slice.vals);
+    g.G1 = a.G[0];
+    g.G2 = a.G[1];
+    g.G3 = a.G[2];
+    g.gs = a.gs;
+    g.f = a.f;
+    g.ysc = a.y_scale ? *a.y_scale : 1.0f;
+    dense_box<RT>(g, a.want, box_sm);
+    if (a.tstep_on && last_block_ticket(a.tstep.st)) temporal_step_tail<float>(a.tstep, a.gs, R);
+}
+
+static int box_num_sms();
+
+template <int RT>
+static cudaError_t run_box(const DenseGradArgs<float>& a, cudaStream_t st) {
+    const int64_t I1 = a.dims[0], I2 = a.dims[1], I3 = a.dims[2];
+    const int lb1 = 3;                      // 8 i1 x 8 i2 rows per tile
+    const int64_t nb3 = (I3 + 31) / 32;
+    // the largest boxes (fewest G1 / G2 atomics) that still give two blocks per SM
+    int n1 = 1, n2 = 1;
+    auto nblocks = [&](int m1, int m2) { return ((I1 + 8 * m1 - 1) / (8 * m1)) * ((I2 + 8 * m2 - 1) / (8 * m2)) * nb3; };
+    const int64_t target = 2 * box_num_sms();
+    for (;;) {
+        bool grew = false;
+        if (8 * n1 * 2 <= kBoxMaxS && 8 * n1 < I1 && nblocks(n1 * 2, n2) >= target) { n1 *= 2; grew = true; }
+        if (8 * n2 * 2 <= kBoxMaxS && 8 * n2 < I2 && nblocks(n1, n2 * 2) >= target) { n2 *= 2; grew = true; }
+        if (!grew) break;
+    }
+    const int nb1 = (int)((I1 + 8 * n1 - 1) / (8 * n1)), nb2 = (int)((I2 + 8 * n2 - 1) / (8 * n2));
+    const int64_t blocks = (int64_t)nb1 * nb2 * nb3;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)TileLayout<RT>::TOTAL * sizeof(float);
+    cudaFuncSetAttribute(k_dense3_box<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_dense3_box<RT><<<(unsigned)blocks, kBoxThreads, smem, st>>>(a, lb1, n1, n2, nb1, nb2);
+    return cudaGetLastError();
+}
 
 template <typename T, int B1, int B2, int RMAX>
 struct DenseCfg {
@@ -276,9 +342,26 @@ static cudaError_t dense_rank(const DenseGradArgs<T>& a, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+static int box_num_sms() { return dense_num_sms(); }
+
+template <typename T>
+static bool dense_box_path(const DenseGradArgs<T>&, cudaStream_t, cudaError_t*) {
+    return false;
+}
+template <>
+bool dense_box_path<float>(const DenseGradArgs<float>& a, cudaStream_t st, cudaError_t* e) {
+    if (a.ndim != 3 || a.R > 64) return false;
+    *e = a.R <= 16 ? run_box<16>(a, st) : (a.R <= 32 ? run_box<32>(a, st) : run_box<64>(a, st));
+    return true;
+}
+
 template <typename T>
 cudaError_t launch_dense_grad(const DenseGradArgs<T>& a, cudaStream_t st, int64_t* launches) {
     if (launches) *launches += 1;
+    {
+        cudaError_t e = cudaSuccess;
+        if (dense_box_path<T>(a, st, &e)) return e;
+    }
     if (a.ndim == 2) {
         // (I1, I2) viewed as (I1, 1, I2): rows are i1 only, columns i2.
         DenseGradArgs<T> b = a;
