@@ -41,6 +41,7 @@ constexpr int kRows = 128;      // (i1, i2) rows per tile
 constexpr int kB1 = 8, kB2 = 16;
 constexpr int kCols = 128;      // i3 columns per tile
 constexpr int kThreads = 512;
+constexpr int kStageLd = 68;    // row stride (floats) of the staged factor rows: 16-byte rows, spread banks
 constexpr int kTmemCols = 512;  // D1 x 2: [0, 256), T: [256, 256 + R), G3: [320, 320 + R)
 constexpr int kXld = 132;       // row stride (floats) of the X tile in shared memory: 16-byte aligned, conflict-free
 constexpr long kWaitLimit = 1L << 26;
@@ -150,7 +151,7 @@ __host__ __device__ inline TcPlan tc_plan(int R, bool bf16) {
     o += (yb > tb ? yb : tb);
     o = (o + 1023) & ~1023;
     p.Xs = o; o += kRows * kXld * 4;
-    p.stage = o; o += 2 * 24 * 64 * 4;
+    p.stage = o; o += 2 * 24 * kStageLd * 4;
     p.sv = o; o += 64 * 4;
     p.gsacc = o; o += 64 * 4;
     p.total = o;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t gr = is1 ? x.i1b + r : x.i2b + (r - kB1);
             const bool ok = is1 ? gr < I1 : gr < I2;
             const float* src = (is1 ? a.A[0] : a.A[1]) + (ok ? gr * R + c : 0);
-            const uint32_t dst = smem_u32(stage + (buf * 24 + r) * 64 + c);
+            const uint32_t dst = smem_u32(stage + (buf * 24 + r) * kStageLd + c);
             const uint32_t bytes = ok ? 16u : 0u;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
         }
@@ -258,8 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     // A3 panel of an i3 block: item = (i3 row, 8 consecutive j), 16-byte stores
     auto build_a3 = [&](int64_t o3) {
-        for (int i = tid; i < kCols * (R / 8); i += kThreads) {
-            const int c = i / (R / 8), j8 = (i - c * (R / 8)) * 8;
+        const int nj = R / 8;
+        for (int i = tid; i < kCols * nj; i += kThreads) {
+            const int rlo = i & 7, rest = i >> 3;
+            const int j8 = (rest % nj) * 8, c = (rest / nj) * 8 + rlo;
             const bool cv = o3 + c < I3;
             uint32_t hi[4], lo[4], h16[4];
 #pragma unroll
@@ -282,19 +285,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     };
     // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16)
+    // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16).
+    // A warp covers 8 consecutive rows x 4 chunks of 8 j, so its 16-byte stores hit distinct banks.
     auto build_kr = [&](int sbuf, int kbuf) {
-        const float* A1 = stage + sbuf * 24 * 64;
-        const float* A2 = A1 + kB1 * 64;
+        const float* A1 = stage + sbuf * 24 * kStageLd;
+        const float* A2 = A1 + kB1 * kStageLd;
         __nv_bfloat16* kh = KRh[kbuf];
-        for (int i = tid; i < kRows * (R / 8); i += kThreads) {
-            const int r = i / (R / 8), j8 = (i - r * (R / 8)) * 8;
-            const float* a1 = A1 + (r / kB2) * 64 + j8;
-            const float* a2 = A2 + (r % kB2) * 64 + j8;
+        const int nj = R / 8;
+        for (int i = tid; i < kRows * nj; i += kThreads) {
+            const int rlo = i & 7, rest = i >> 3;
+            const int j8 = (rest % nj) * 8, r = (rest / nj) * 8 + rlo;
+            float s8[8], a18[8], a28[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float4 sq = *reinterpret_cast<const float4*>(sv + j8 + 4 * h);
+                const float4 aq = *reinterpret_cast<const float4*>(A1 + (r / kB2) * kStageLd + j8 + 4 * h);
+                const float4 bq = *reinterpret_cast<const float4*>(A2 + (r % kB2) * kStageLd + j8 + 4 * h);
+                s8[4 * h] = sq.x, s8[4 * h + 1] = sq.y, s8[4 * h + 2] = sq.z, s8[4 * h + 3] = sq.w;
+                a18[4 * h] = aq.x, a18[4 * h + 1] = aq.y, a18[4 * h + 2] = aq.z, a18[4 * h + 3] = aq.w;
+                a28[4 * h] = bq.x, a28[4 * h + 1] = bq.y, a28[4 * h + 2] = bq.z, a28[4 * h + 3] = bq.w;
+            }
             uint32_t hi[4], lo[4], h16[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float v0 = sv[j8 + 2 * q] * a1[2 * q] * a2[2 * q];
-                const float v1 = sv[j8 + 2 * q + 1] * a1[2 * q + 1] * a2[2 * q + 1];
+                const float v0 = s8[2 * q] * a18[2 * q] * a28[2 * q];
+                const float v1 = s8[2 * q + 1] * a18[2 * q + 1] * a28[2 * q + 1];
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
                 const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
                 const __half2 f = __floats2half2_rn(v0, v1);
@@ -543,8 +558,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
-            const float* A1 = stage + cb * 24 * 64;
-            const float* A2 = A1 + kB1 * 64;
+            const float* A1 = stage + cb * 24 * kStageLd;
+            const float* A2 = A1 + kB1 * kStageLd;
             const int per = R / 4;
             for (int it = tid; it < (kB1 + kB2) * per; it += kThreads) {
                 const int rr = it / per, j = (it - rr * per) * 4;
@@ -554,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
                     for (int i2l = 0; i2l < kB2; ++i2l) {
-                        const float4 w = *reinterpret_cast<const float4*>(A2 + i2l * 64 + j);
+                        const float4 w = *reinterpret_cast<const float4*>(A2 + i2l * kStageLd + j);
                         const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
                         g.x = fmaf(w.x, tv.x, g.x);
                         g.y = fmaf(w.y, tv.y, g.y);
@@ -562,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         g.w = fmaf(w.w, tv.w, g.w);
                     }
                     if (wantS) {
-                        const float4 a1 = *reinterpret_cast<const float4*>(A1 + i1l * 64 + j);
+                        const float4 a1 = *reinterpret_cast<const float4*>(A1 + i1l * kStageLd + j);
                         atomicAdd(gsacc + j, a1.x * g.x);
                         atomicAdd(gsacc + j + 1, a1.y * g.y);
                         atomicAdd(gsacc + j + 2, a1.z * g.z);
@@ -576,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int i1l = 0; i1l < kB1; ++i1l) {
-                        const float4 w = *reinterpret_cast<const float4*>(A1 + i1l * 64 + j);
+                        const float4 w = *reinterpret_cast<const float4*>(A1 + i1l * kStageLd + j);
                         const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
                         g.x = fmaf(s4.x * w.x, tv.x, g.x);
                         g.y = fmaf(s4.y * w.y, tv.y, g.y);
@@ -672,7 +687,7 @@ cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* 
     const int64_t ntiles = t1 * t2 * nb3;
     if (ntiles > 0x7fffffff || t1 > 0x7fffffff || t2 > 0x7fffffff) return cudaErrorInvalidValue;
     const int grid = (int)(ntiles < tc_num_sms() ? ntiles : tc_num_sms());
-    const size_t smem = (size_t)tc_plan(a.R, bf16).total + 1024;
+    const size_t smem = (size_t)tc_plan(a.R, bf16).total;
     if (launches) *launches += 1;
     if (grid <= 0) return cudaSuccess;
     return bf16 ? run_tc_loss<true>(a, (int)t1, (int)t2, (int)ntiles, grid, smem, err, st)
