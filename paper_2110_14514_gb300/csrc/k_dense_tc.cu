@@ -42,6 +42,8 @@ constexpr int kB1 = 8, kB2 = 16;
 constexpr int kCols = 128;      // i3 columns per tile
 constexpr int kThreads = 512;
 constexpr int kStageLd = 68;    // row stride (floats) of the staged factor rows: 16-byte rows, spread banks
+constexpr int kXBase = kThreads - kRows;   // first of the threads that copy X rows
+constexpr int kKrLo = 32, kKrCnt = kXBase - 32;   // threads that build the next KR panel beside the MMA issue
 constexpr int kTmemCols = 512;  // D1 x 2: [0, 256), T: [256, 256 + R), G3: [320, 320 + R)
 constexpr int kXld = 132;       // row stride (floats) of the X tile in shared memory: 16-byte aligned, conflict-free
 constexpr long kWaitLimit = 1L << 26;
@@ -287,12 +289,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16)
     // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16).
     // A warp covers 8 consecutive rows x 4 chunks of 8 j, so its 16-byte stores hit distinct banks.
-    auto build_kr = [&](int sbuf, int kbuf) {
+    auto build_kr = [&](int sbuf, int kbuf, int lo, int cnt) {   // by threads lo .. lo + cnt - 1
+        if (tid < lo || tid >= lo + cnt) return;
         const float* A1 = stage + sbuf * 24 * kStageLd;
         const float* A2 = A1 + kB1 * kStageLd;
         __nv_bfloat16* kh = KRh[kbuf];
         const int nj = R / 8;
-        for (int i = tid; i < kRows * nj; i += kThreads) {
+        for (int i = tid - lo; i < kRows * nj; i += cnt) {
             const int rlo = i & 7, rest = i >> 3;
             const int j8 = (rest % nj) * 8, r = (rest / nj) * 8 + rlo;
             float s8[8], a18[8], a28[8];
@@ -361,15 +364,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     // threads 0..127 bulk-copy their X row of a tile; mbar_x counts the 128 arrivals and the bytes
     auto issue_x = [&](const TileIx& x) {
-        if (tid < kRows) {
+        const int xr = tid - kXBase;     // the last 128 threads copy one X row each
+        if (xr >= 0 && xr < kRows) {
             const int64_t ncol = (I3 - x.o3) < kCols ? (I3 - x.o3) : kCols;
             const uint32_t rowbytes = (uint32_t)ncol * 4;
-            const int64_t i1 = x.i1b + tid / kB2, i2 = x.i2b + tid % kB2;
+            const int64_t i1 = x.i1b + xr / kB2, i2 = x.i2b + xr % kB2;
             if (i1 < I1 && i2 < I2) {
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_x)),
                              "r"(rowbytes) : "memory");
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(Xs + tid * kXld)), "l"(X + (i1 * I2 + i2) * I3 + x.o3), "r"(rowbytes),
+                             ::"r"(smem_u32(Xs + xr * kXld)), "l"(X + (i1 * I2 + i2) * I3 + x.o3), "r"(rowbytes),
                              "r"(smem_u32(&mbar_x))
                              : "memory");
             } else {
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         stage_rows(cur, 0);
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-        build_kr(0, 0);
+        build_kr(0, 0, 0, kThreads);
         publish_smem();
         issue_gemm1(0, 0);
         if (xtma) {
@@ -486,13 +490,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's rows of the next tile have landed
         publish_smem();
-        // ---- X of the next tile behind the rest of this one (Xs is consumed)
-        if (xtma && has_next) {
-            issue_x(nxt);
-            pending_x = 1;
-        }
-        // ---- T = Y A3 and G3 += Y' KR of this tile
+        // ---- three roles side by side (Xs and Y are settled): thread 0 issues T = Y A3 and
+        // G3 += Y' KR of this tile, the last 128 threads copy X of the next tile, warps 1 .. 11
+        // build the next KR panel (the MMA and copy issue block their threads for ~1-2 K cycles)
+        const bool new_b3 = has_next && nxt.b3 != cur.b3;
         if (g23) {
             issue_gemm23(cb, g3_started);
             if (wantG) {
@@ -500,7 +503,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 b3_open = cur.b3;
             }
         }
-        const bool new_b3 = has_next && nxt.b3 != cur.b3;
+        if (xtma && has_next) {
+            issue_x(nxt);
+            pending_x = 1;
+        }
+        if (has_next && !new_b3) build_kr((k + 1) & 1, (k + 1) & 1, kKrLo, kKrCnt);
         bool t_ready = false;
         auto read_t = [&]() {   // T from TMEM to Ts[row][j] (Yr is consumed once T and G3 are done)
             if (16 * cq < R) {
@@ -524,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                   make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
             }
         };
-        if (new_b3) {   // the A3 panel changes: drain the tensor core first
+        if (new_b3) {   // the A3 panel changes: T and G3 of this tile must be done first
             if (g23) {
                 if (!wait_phase(&mbar2, ph2)) fail();
                 ph2 ^= 1u;
@@ -539,29 +546,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
             build_a3(nxt.o3);
+            build_kr((k + 1) & 1, (k + 1) & 1, 0, kThreads);
         }
-        // ---- KR and the model product of the next tile
-        if (has_next) {
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            __syncthreads();
-            build_kr((k + 1) & 1, (k + 1) & 1);
-            publish_smem();
-            issue_gemm1((k + 1) & 1, (k + 1) & 1);
+        if (has_next) publish_smem();   // KR (and A3) of the next tile are in place
+        // ---- T of this tile
+        if (g23 && !t_ready) {
+            if (!wait_phase(&mbar2, ph2)) fail();
+            ph2 ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            read_t();
         }
-        // ---- T of this tile, then the G1 / G2 / gs reductions
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        // ---- thread 0 issues the next model product while warps 1 .. 15 reduce T into G1, G2, gs
+        if (has_next) issue_gemm1((k + 1) & 1, (k + 1) & 1);
         if (g23) {
-            if (!t_ready) {
-                if (!wait_phase(&mbar2, ph2)) fail();
-                ph2 ^= 1u;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                read_t();
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
             const float* A1 = stage + cb * 24 * kStageLd;
             const float* A2 = A1 + kB1 * kStageLd;
             const int per = R / 4;
-            for (int it = tid; it < (kB1 + kB2) * per; it += kThreads) {
+            for (int it = tid - kKrLo; it >= 0 && it < (kB1 + kB2) * per; it += kThreads - kKrLo) {
                 const int rr = it / per, j = (it - rr * per) * 4;
                 const float4 s4 = *reinterpret_cast<const float4*>(sv + j);
                 if (rr < kB1) {   // G1 row i1l (and gs): sum over the 16 i2 rows
