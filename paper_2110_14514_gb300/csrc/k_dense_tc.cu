@@ -94,13 +94,25 @@ __device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t phase) {
     return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// TMEM -> registers, 16 columns of this thread's lane (issue only).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// Wait for this thread's TMEM loads; the registers are operands so no use of them moves above the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    tmem_ld16_issue(taddr, r);
+    tmem_wait16(r);
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -433,11 +445,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* xs = Xs + row * kXld;
             const uint32_t dcol = tmem + (uint32_t)cb * 128 + lane_base;
             unsigned char* yb = reinterpret_cast<unsigned char*>(Yr);
-#pragma unroll 1
+            uint32_t mr[2][16];     // both 16-column halves in flight before one wait
+            tmem_ld16_issue(dcol + (uint32_t)(32 * cq), mr[0]);
+            tmem_ld16_issue(dcol + (uint32_t)(32 * cq + 16), mr[1]);
+            tmem_wait16(mr[0]);
+            tmem_wait16(mr[1]);
+#pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int c0 = 32 * cq + 16 * h;
                 float m[16], x[16], y[16];
-                tmem_ld16(dcol + (uint32_t)c0, m);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) m[q] = __uint_as_float(mr[h][q]);
                 if (xtma) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -564,14 +582,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* A1 = stage + cb * 24 * kStageLd;
             const float* A2 = A1 + kB1 * kStageLd;
             const int per = R / 4;
-            for (int it = tid - kKrLo; it >= 0 && it < (kB1 + kB2) * per; it += kThreads - kKrLo) {
+            for (int it = tid - kKrLo; it >= 0 && it < (2 * kB1 + kB2) * per; it += kThreads - kKrLo) {
                 const int rr = it / per, j = (it - rr * per) * 4;
                 const float4 s4 = *reinterpret_cast<const float4*>(sv + j);
-                if (rr < kB1) {   // G1 row i1l (and gs): sum over the 16 i2 rows
-                    const int i1l = rr;
+                if (rr < 2 * kB1) {   // G1 row i1l (and gs): half of the sum over the 16 i2 rows
+                    const int i1l = rr >> 1, h0 = (rr & 1) * (kB2 / 2);
                     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-                    for (int i2l = 0; i2l < kB2; ++i2l) {
+#pragma unroll
+                    for (int i2l = h0; i2l < h0 + kB2 / 2; ++i2l) {
                         const float4 w = *reinterpret_cast<const float4*>(A2 + i2l * kStageLd + j);
                         const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
                         g.x = fmaf(w.x, tv.x, g.x);
@@ -590,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         atomicAdd(reinterpret_cast<float4*>(a.G[0] + (cur.i1b + i1l) * R + j),
                                   make_float4(s4.x * g.x, s4.y * g.y, s4.z * g.z, s4.w * g.w));
                 } else if (wantG) {   // G2 row i2l: sum over the 8 i1 rows of (s A1) T
-                    const int i2l = rr - kB1;
+                    const int i2l = rr - 2 * kB1;
                     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int i1l = 0; i1l < kB1; ++i1l) {
