@@ -87,6 +87,10 @@ struct sgcp_ctx {
     std::vector<void*> lb_S, lb_Y;
     double* lb_dot = nullptr;
     int64_t graph_kernels[2] = {0, 0};
+    // tensor-core contexts: TMA tensor map of the current dense slice (device, 128 bytes)
+    bool tc = false;
+    void* xmap = nullptr;
+    bool xmap_ok = false;
 };
 
 namespace {
@@ -184,7 +188,9 @@ sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_i
     }
     const void* idx_d = X->idx;
     const void* vals_d = X->vals;
-    if (X->on_host) {
+    // the tensor-core kernel loads dense tiles by TMA, which needs a 16-byte aligned slice
+    const bool restage = !X->on_host && !sparse && c->tc && (reinterpret_cast<uintptr_t>(X->vals) & 15) != 0;
+    if (X->on_host || restage) {
         const size_t ib = sparse ? (size_t)nnz * c->ndim * sizeof(int32_t) : 0;
         const size_t vb = (size_t)nnz * (sparse ? sizeof(float) : c->esz);
         if (ib > c->stage_idx_bytes) {
@@ -203,8 +209,9 @@ sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_i
             if (st) return st;
             c->stage_vals_bytes = vb;
         }
-        if (ib) CK(cudaMemcpyAsync(c->stage_idx, X->idx, ib, cudaMemcpyHostToDevice, c->stream), "copy slice idx");
-        if (vb) CK(cudaMemcpyAsync(c->stage_vals, X->vals, vb, cudaMemcpyHostToDevice, c->stream), "copy slice vals");
+        const cudaMemcpyKind kind = X->on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        if (ib) CK(cudaMemcpyAsync(c->stage_idx, X->idx, ib, kind, c->stream), "copy slice idx");
+        if (vb) CK(cudaMemcpyAsync(c->stage_vals, X->vals, vb, kind, c->stream), "copy slice vals");
         idx_d = c->stage_idx;
         vals_d = c->stage_vals;
         force_ingest = true;
@@ -253,6 +260,18 @@ sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_i
     c->loaded_user_idx = X->idx;
     c->loaded_user_vals = X->vals;
     c->loaded_nnz = nnz;
+    return SGCP_OK;
+}
+
+// Tensor-core contexts: encode the TMA tensor map of the dense slice in c->cur and write it to
+// c->xmap on the context stream (the step graph and direct launches read it from there).  With
+// the slice staged to 16-byte alignment, whether it encodes depends only on I3 and the driver, so
+// it is the same for every slice of a context.
+sgcp_status prepare_xmap(sgcp_ctx* c) {
+    if (!c->tc) return SGCP_OK;
+    unsigned char map[128];
+    c->xmap_ok = encode_x_map(map, (const float*)c->cur.vals, c->dims[0], c->dims[1], c->dims[2]);
+    if (c->xmap_ok) CK(launch_write_map(c->xmap, map, c->stream, &c->launches), "tensor map");
     return SGCP_OK;
 }
 
@@ -318,6 +337,7 @@ DenseGradArgs<T> dense_args(sgcp_ctx* c, const SliceDesc* slice_dev, int want, c
     a.eps = (T)c->P.log_eps;
     a.y_scale = (const T*)y_scale;
     a.skip = skip;
+    a.xmap = (c->tc && c->xmap_ok) ? c->xmap : nullptr;
     return a;
 }
 
@@ -914,6 +934,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     c->ndim = P.ndim;
     c->R = P.rank;
     c->f64 = P.precision == SGCP_PREC_F64;
+    c->tc = P.precision == SGCP_PREC_BF16_MTTKRP || P.precision == SGCP_PREC_F16_MTTKRP;
     c->esz = c->f64 ? 8 : 4;
     if (std::isnan(P.lower_bound))
         c->lower = (P.loss == SGCP_LOSS_POISSON || P.loss == SGCP_LOSS_BERNOULLI_ODDS) ? 0.0 : -INFINITY;
@@ -973,7 +994,8 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         (st = dalloc_t(c, &c->err, sizeof(int))) || (st = dalloc_t(c, &c->slice_dev, sizeof(SliceDesc))) ||
         (st = dalloc_t(c, &c->counts, c->nrows * sizeof(int32_t))) ||
         (st = dalloc_t(c, &c->hot, c->nrows * sizeof(int32_t))) ||
-        (st = dalloc_t(c, &c->hot_rows, c->ndim * kMaxHot * sizeof(int32_t))))
+        (st = dalloc_t(c, &c->hot_rows, c->ndim * kMaxHot * sizeof(int32_t))) ||
+        (c->tc && (st = dalloc(c, &c->xmap, 128))))
         return bail(st);
     cudaStream_t s = c->stream;
     cudaError_t e = cudaSuccess;
@@ -1059,6 +1081,8 @@ sgcp_status sgcp_gradient(sgcp_ctx* c, const sgcp_slice* X, const void* s, const
         if ((want & SGCP_WANT_FACTORS) && !G_out[k]) return fail(c, SGCP_ERR_ARG, "gradient: G_out[%d] is NULL", k);
     }
     if (sgcp_status st = load_slice(c, X, opts->t, false)) return st;
+    if (!X->is_sparse)
+        if (sgcp_status st = prepare_xmap(c)) return st;
     if (!opts->accumulate) {
         if (want & SGCP_WANT_FACTORS)
             for (int k = 0; k < c->ndim; ++k)
@@ -1097,6 +1121,8 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
         return fail(c, SGCP_ERR_ARG, "step: sparse slices need p + q > 0 and p_obj + q_obj > 0");
     if (sgcp_status st = load_slice(c, X, t, false)) return st;
     CK(launch_write_desc(c->slice_dev, c->cur, c->stream, &c->launches), "slice descriptor");
+    if (!sparse)
+        if (sgcp_status st = prepare_xmap(c)) return st;
     const int gi = sparse ? 1 : 0;
     if (!c->graph[gi])
         if (sgcp_status st = build_graph(c, sparse)) return st;

@@ -65,6 +65,7 @@ struct DenseGradArgs {
     const int32_t* skip;
     int tstep_on;            // fuse the temporal ADAM step into the last block
     TemporalStep<T> tstep;
+    const void* xmap;        // tensor-core path: device CUtensorMap of the slice (nullptr = plain loads)
 };
 
 struct IngestArgs {
@@ -95,6 +96,12 @@ cudaError_t launch_dense_grad(const DenseGradArgs<T>& a, cudaStream_t st, int64_
 // bf16 selects BF16 MTTKRP operands, otherwise FP16.
 cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* err, cudaStream_t st,
                                  int64_t* launches);
+// Encode the TMA tensor map of a dense I1 x I2 x I3 float slice for the tensor-core kernel (boxes of
+// 32 i3 x 16 i2 x 8 i1, 128-byte swizzle) into a 128-byte host buffer; false when the slice does
+// not qualify (I3 % 4 != 0, a misaligned base) or the driver offers no encoder.
+bool encode_x_map(void* map128, const float* X, int64_t I1, int64_t I2, int64_t I3);
+// Copy a 128-byte tensor map into device memory (128-byte aligned) on a stream.
+cudaError_t launch_write_map(void* dst_dev, const void* map128, cudaStream_t st, int64_t* launches);
 
 // ---------------------------------------------------------------------------
 // Solver kernels (k_solver.cu)

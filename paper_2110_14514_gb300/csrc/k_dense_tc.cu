@@ -27,6 +27,8 @@
 // Every wait on an mbarrier is bounded; on timeout the kernel records
 // ERRB_TIMEOUT in the error word, stops issuing work, lets its own copies land
 // and frees its TMEM.
+#include <cstring>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -45,7 +47,7 @@ constexpr int kStageLd = 68;    // row stride (floats) of the staged factor rows
 constexpr int kXBase = kThreads - kRows;   // first of the threads that copy X rows
 constexpr int kKrLo = 32, kKrCnt = kXBase - 32;   // threads that build the next KR panel beside the MMA issue
 constexpr int kTmemCols = 512;  // D1 x 2: [0, 256), T: [256, 256 + R), G3: [320, 320 + R)
-constexpr int kXld = 132;       // row stride (floats) of the X tile in shared memory: 16-byte aligned, conflict-free
+constexpr int kXBox = 32;       // i3 columns per tensor-map box (128 bytes: one 128-byte swizzle row)
 constexpr long kWaitLimit = 1L << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -140,7 +142,8 @@ struct Op<false> {
 //   A316           [128 i3][R]   fp16   GEMM2 B in fp16 mode
 //   Yr             [128 rows][128 i3] op  GEMM2 A (K-major), GEMM3 A (MN-major);
 //                                       then Ts [128 rows][R + 4] f32 (T for the reductions)
-//   Xs             [128 rows][132] f32  X tile (cp.async.bulk, one row per thread)
+//   Xs             [4][128 rows][32] f32  X tile: four tensor-map boxes of 32 i3 columns, each row
+//                                       of 128 bytes with its 16-byte chunks XOR-swizzled by (row mod 8)
 //   stage          [2][24 rows][64] f32 A1 rows (8) and A2 rows (16) of a tile (cp.async)
 //   sv [64], gsacc [64] f32
 struct TcPlan {
@@ -164,7 +167,7 @@ __host__ __device__ inline TcPlan tc_plan(int R, bool bf16) {
     const int yb = kRows * kCols * 2, tb = kRows * (R + 4) * 4;
     o += (yb > tb ? yb : tb);
     o = (o + 1023) & ~1023;
-    p.Xs = o; o += kRows * kXld * 4;
+    p.Xs = o; o += kRows * kCols * 4;
     p.stage = o; o += 2 * 24 * kStageLd * 4;
     p.sv = o; o += 64 * 4;
     p.gsacc = o; o += 64 * 4;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool g23 = wantG || wantS;
     const float ysc = a.y_scale ? *a.y_scale : 1.0f;
     const float* X = reinterpret_cast<const float*>(a.slice ? a.slice->vals : a.inline_slice.vals);
-    const bool xtma = (I3 % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    const bool xtma = a.xmap != nullptr;     // X tiles by TMA from the slice's tensor map
     // this block's run of tiles
     const int tb = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
     const int te = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         abort_flag = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar1)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar2)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_x)), "r"(kRows));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_x)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     for (int j = tid; j < 64; j += kThreads) {
@@ -374,23 +377,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             commit(&mbar2);
         }
     };
-    // threads 0..127 bulk-copy their X row of a tile; mbar_x counts the 128 arrivals and the bytes
+    // one thread (kXBase) loads the X tile: four 3D tensor-map boxes of 32 i3 x 16 i2 x 8 i1 floats
+    // on mbar_x (64 KB of transactions; boxes reaching past the slice are zero-filled and still count)
+    if (xtma && tid == kXBase)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.xmap) : "memory");
     auto issue_x = [&](const TileIx& x) {
-        const int xr = tid - kXBase;     // the last 128 threads copy one X row each
-        if (xr >= 0 && xr < kRows) {
-            const int64_t ncol = (I3 - x.o3) < kCols ? (I3 - x.o3) : kCols;
-            const uint32_t rowbytes = (uint32_t)ncol * 4;
-            const int64_t i1 = x.i1b + xr / kB2, i2 = x.i2b + xr % kB2;
-            if (i1 < I1 && i2 < I2) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_x)),
-                             "r"(rowbytes) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(Xs + xr * kXld)), "l"(X + (i1 * I2 + i2) * I3 + x.o3), "r"(rowbytes),
-                             "r"(smem_u32(&mbar_x))
+        if (tid == kXBase) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar_x)),
+                         "r"((uint32_t)(kRows * kCols * 4)) : "memory");
+#pragma unroll
+            for (int b = 0; b < kCols / kXBox; ++b)
+                asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                             " [%0], [%1, {%2, %3, %4}], [%5];"
+                             ::"r"(smem_u32(Xs + b * kRows * kXBox)), "l"(a.xmap), "r"((int)(x.o3 + b * kXBox)),
+                             "r"((int)x.i2b), "r"((int)x.i1b), "r"(smem_u32(&mbar_x))
                              : "memory");
-            } else {
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mbar_x)) : "memory");
-            }
         }
     };
     auto fail = [&]() {
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool rv = i1 < I1 && i2 < I2;
             const bool interior = cur.i1b + kB1 <= I1 && cur.i2b + kB2 <= I2 && cur.o3 + kCols <= I3 && xtma;
             const float* xrow = X + (i1 * I2 + i2) * I3 + cur.o3;
-            const float* xs = Xs + row * kXld;
+            const int swz = row & 7;     // 128-byte swizzle of this row's 16-byte chunks
             const uint32_t dcol = tmem + (uint32_t)cb * 128 + lane_base;
             unsigned char* yb = reinterpret_cast<unsigned char*>(Yr);
             uint32_t mr[2][16];     // both 16-column halves in flight before one wait
@@ -457,9 +458,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int q = 0; q < 16; ++q) m[q] = __uint_as_float(mr[h][q]);
                 if (xtma) {
+                    const float* xb = Xs + (c0 / kXBox) * kRows * kXBox + row * kXBox;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 v = *reinterpret_cast<const float4*>(xs + c0 + 4 * q);
+                        const int chunk = ((c0 % kXBox) >> 2) + q;
+                        const float4 v = *reinterpret_cast<const float4*>(xb + ((chunk ^ swz) << 2));
                         x[4 * q] = v.x;
                         x[4 * q + 1] = v.y;
                         x[4 * q + 2] = v.z;
@@ -698,6 +701,59 @@ static cudaError_t run_tc_loss(const DenseGradArgs<float>& a, int t1n, int t2n, 
 }
 
 }  // namespace
+
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+__global__ void k_write_map(unsigned long long* dst, const CUtensorMap m) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&m);
+    if (threadIdx.x < sizeof(CUtensorMap) / 8) dst[threadIdx.x] = src[threadIdx.x];
+}
+}  // namespace
+
+bool encode_x_map(void* map128, const float* X, int64_t I1, int64_t I2, int64_t I3) {
+    if (I3 % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || I1 > 0x7fffffff || I2 > 0x7fffffff ||
+        I3 > 0x7fffffff)
+        return false;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)I3, (cuuint64_t)I2, (cuuint64_t)I1};
+    const cuuint64_t strides[2] = {(cuuint64_t)I3 * 4, (cuuint64_t)I2 * I3 * 4};   // bytes, dims 1 and 2
+    const cuuint32_t box[3] = {(cuuint32_t)kXBox, (cuuint32_t)kB2, (cuuint32_t)kB1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUtensorMap m;
+    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    memcpy(map128, &m, sizeof(m));
+    return true;
+}
+
+cudaError_t launch_write_map(void* dst_dev, const void* map128, cudaStream_t st, int64_t* launches) {
+    CUtensorMap m;
+    memcpy(&m, map128, sizeof(m));
+    k_write_map<<<1, 32, 0, st>>>(reinterpret_cast<unsigned long long*>(dst_dev), m);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dense_grad_tc(const DenseGradArgs<float>& a, bool bf16, int* err, cudaStream_t st,
                                  int64_t* launches) {
