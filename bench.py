@@ -43,13 +43,13 @@ N_SLICES = 4                # distinct slices cycled through (every step re-inge
 METRIC = "fused GCP gradient nnz/s"
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the dominant kernel from its committed ncu summary, or None when
+def recorded_traffic(summary="sparse_grad_factor_R32_zipf1e6.md"):
+    """DRAM bytes per launch of a dominant kernel from its committed ncu summary, or None when
     the kernel's source changed since that capture."""
     import hashlib
     import re
     try:
-        text = open(os.path.join(ROOT, "profiles", "sparse_grad_factor_R32_zipf1e6.md")).read()
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
         m = re.search(r"source=(\S+) source_sha256_16=([0-9a-f]+) dram_bytes_per_launch=(\d+)", text)
         src = open(os.path.join(ROOT, m.group(1)), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != m.group(2):
@@ -374,6 +374,21 @@ def run_native_dense(args, cfg, world, rank, local):
         tflops_peak = float(d["bf16_tflops"])
     except Exception:
         tflops_peak = 1900.0
+    if args.precision == "fp32":   # CUDA-core path: bound by FP32 FMA throughput
+        sm_clock = clk.get("sm_max_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = n_sm * 128 * 2 * sm_clock * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops_alg / kern_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": flops_alg / kern_s / 1e12 / fp32_peak, "traffic": None,
+                "peak_kind": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flop x {sm_clock:.0f} MHz",
+                "kernel_us": kern_s * 1e6, "hbm_gbs": bytes_alg / kern_s / 1e9}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_alg / kern_s / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": bytes_alg / kern_s / 1e9 / peak, "traffic": recorded_traffic("dense_grad_tc_bf16_R64_256cubed.md")
+                if args.precision == "bf16" else None, "peak_kind": peak_kind,
+                "kernel_us": kern_s * 1e6,
+                "tensor_tflops": flops_alg / kern_s / 1e12,
+                "tensor_frac_of_bf16_peak": flops_alg / kern_s / 1e12 / tflops_peak}
     return {
         "metric": "dense GCP gradient entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
@@ -385,10 +400,7 @@ def run_native_dense(args, cfg, world, rank, local):
                    "grads_per_step": grads_per_step, "solver": DENSE_SOLVER,
                    "l2": "flushed between steps (256 MB write)", "precision": args.precision},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": bytes_alg / kern_s / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": bytes_alg / kern_s / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel_us": kern_s * 1e6,
-                     "tensor_tflops": flops_alg / kern_s / 1e12, "tensor_frac_of_bf16_peak": flops_alg / kern_s / 1e12 / tflops_peak},
+        "roofline": roof,
         "clocks": clk,
     }
 
