@@ -213,7 +213,9 @@ sgcp_status sgcp_ingest(sgcp_ctx* ctx, const sgcp_slice* X);
  *   f_out    (device, 1 double) <- sum of weight * f(x, m)   if SGCP_WANT_LOSS
  * s (device, R) and A (device, ndim pointers, I_k x R) are the point of
  * evaluation.  History and regularisation terms are not included.  Outputs
- * not requested may be NULL.  Asynchronous on the context stream. */
+ * not requested may be NULL.  A[k] and G_out[k] must be 16-byte aligned (rows
+ * are moved with 16-byte vector accesses; any cudaMalloc'd or torch-allocated
+ * buffer is), else SGCP_ERR_ARG.  Asynchronous on the context stream. */
 sgcp_status sgcp_gradient(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, const void* const* A,
                           const sgcp_grad_opts* opts, void* const* G_out, void* gs_out, double* f_out);
 

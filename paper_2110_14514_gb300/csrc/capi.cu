@@ -91,6 +91,8 @@ struct sgcp_ctx {
     bool tc = false;
     void* xmap = nullptr;
     bool xmap_ok = false;
+    bool xmap_written = false;           // xmap holds xmap_last
+    unsigned char xmap_last[128] = {};
 };
 
 namespace {
@@ -266,12 +268,17 @@ sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_i
 // Tensor-core contexts: encode the TMA tensor map of the dense slice in c->cur and write it to
 // c->xmap on the context stream (the step graph and direct launches read it from there).  With
 // the slice staged to 16-byte alignment, whether it encodes depends only on I3 and the driver, so
-// it is the same for every slice of a context.
+// it is the same for every slice of a context.  The map encodes only the slice's address and
+// shape, so a map equal to the one already written is not written again.
 sgcp_status prepare_xmap(sgcp_ctx* c) {
     if (!c->tc) return SGCP_OK;
-    unsigned char map[128];
+    unsigned char map[128] = {};
     c->xmap_ok = encode_x_map(map, (const float*)c->cur.vals, c->dims[0], c->dims[1], c->dims[2]);
-    if (c->xmap_ok) CK(launch_write_map(c->xmap, map, c->stream, &c->launches), "tensor map");
+    if (!c->xmap_ok || (c->xmap_written && std::memcmp(map, c->xmap_last, sizeof(map)) == 0)) return SGCP_OK;
+    c->xmap_written = false;
+    CK(launch_write_map(c->xmap, map, c->stream, &c->launches), "tensor map");
+    std::memcpy(c->xmap_last, map, sizeof(map));
+    c->xmap_written = true;
     return SGCP_OK;
 }
 
@@ -1079,6 +1086,11 @@ sgcp_status sgcp_gradient(sgcp_ctx* c, const sgcp_slice* X, const void* s, const
     for (int k = 0; k < c->ndim; ++k) {
         if (!A[k]) return fail(c, SGCP_ERR_ARG, "gradient: A[%d] is NULL", k);
         if ((want & SGCP_WANT_FACTORS) && !G_out[k]) return fail(c, SGCP_ERR_ARG, "gradient: G_out[%d] is NULL", k);
+        // factor rows are read and gradient rows accumulated with 16-byte vector accesses
+        if ((reinterpret_cast<uintptr_t>(A[k]) & 15) != 0)
+            return fail(c, SGCP_ERR_ARG, "gradient: A[%d] is not 16-byte aligned", k);
+        if ((want & SGCP_WANT_FACTORS) && (reinterpret_cast<uintptr_t>(G_out[k]) & 15) != 0)
+            return fail(c, SGCP_ERR_ARG, "gradient: G_out[%d] is not 16-byte aligned", k);
     }
     if (sgcp_status st = load_slice(c, X, opts->t, false)) return st;
     if (!X->is_sparse)

@@ -141,7 +141,7 @@ struct Op<false> {
 //   A3hi, A3lo     [128 i3][R]   bf16   GEMM1 B (K-major); GEMM2 B (MN-major) in bf16 mode
 //   A316           [128 i3][R]   fp16   GEMM2 B in fp16 mode
 //   Yr             [128 rows][128 i3] op  GEMM2 A (K-major), GEMM3 A (MN-major);
-//                                       then Ts [128 rows][R + 4] f32 (T for the reductions)
+//                                       then [4][16][68] f32 G2 partials of the T reduction
 //   Xs             [4][128 rows][32] f32  X tile: four tensor-map boxes of 32 i3 columns, each row
 //                                       of 128 bytes with its 16-byte chunks XOR-swizzled by (row mod 8)
 //   stage          [2][24 rows][64] f32 A1 rows (8) and A2 rows (16) of a tile (cp.async)
@@ -164,8 +164,7 @@ __host__ __device__ inline TcPlan tc_plan(int R, bool bf16) {
     p.A3lo = o; o += a3;
     p.A316 = bf16 ? -1 : o; o += bf16 ? 0 : a3;
     p.Yr = o;
-    const int yb = kRows * kCols * 2, tb = kRows * (R + 4) * 4;
-    o += (yb > tb ? yb : tb);
+    o += kRows * kCols * 2;   // >= 4 * 16 * kStageLd * 4
     o = (o + 1023) & ~1023;
     p.Xs = o; o += kRows * kCols * 4;
     p.stage = o; o += 2 * 24 * kStageLd * 4;
@@ -211,12 +210,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __nv_bfloat16* A3lo = reinterpret_cast<__nv_bfloat16*>(sm + P.A3lo);
     __half* A316 = BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.A316);
     OT* Yr = reinterpret_cast<OT*>(sm + P.Yr);
-    float* Ts = reinterpret_cast<float*>(sm + P.Yr);
     float* Xs = reinterpret_cast<float*>(sm + P.Xs);
     float* stage = reinterpret_cast<float*>(sm + P.stage);   // [2][24][64]
     float* sv = reinterpret_cast<float*>(sm + P.sv);
     float* gsacc = reinterpret_cast<float*>(sm + P.gsacc);
-    const int ldT = R + 4;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
@@ -281,11 +278,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int rlo = i & 7, rest = i >> 3;
             const int j8 = (rest % nj) * 8, c = (rest / nj) * 8 + rlo;
             const bool cv = o3 + c < I3;
+            float a8[8];
+            {
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4* src = reinterpret_cast<const float4*>(a.A[2] + (cv ? (o3 + c) * R + j8 : 0));
+                const float4 p0 = cv ? __ldg(src) : z, p1 = cv ? __ldg(src + 1) : z;
+                a8[0] = p0.x, a8[1] = p0.y, a8[2] = p0.z, a8[3] = p0.w;
+                a8[4] = p1.x, a8[5] = p1.y, a8[6] = p1.z, a8[7] = p1.w;
+            }
             uint32_t hi[4], lo[4], h16[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float v0 = cv ? __ldg(a.A[2] + (o3 + c) * R + j8 + 2 * q) : 0.0f;
-                const float v1 = cv ? __ldg(a.A[2] + (o3 + c) * R + j8 + 2 * q + 1) : 0.0f;
+                const float v0 = a8[2 * q], v1 = a8[2 * q + 1];
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
                 const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - __low2float(h), v1 - __high2float(h));
                 const __half2 f = __floats2half2_rn(v0, v1);
@@ -402,24 +406,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
 
     float fsum = 0.0f;
+    float gs_acc = 0.0f;                              // gradient of s, column 16 cq + (lane & 15)
+    const float s_c = sv[16 * cq + (lane & 15)];
     uint32_t ph1 = 0, ph2 = 0, phx = 0;
     int pending_x = 0;
     bool g3_started = false;
     int b3_open = -1;            // i3 block whose G3 sits in TMEM
     TileIx cur{};
-    if (tb < te) {
+    if (tb < te) {   // the first X tile and factor rows are in flight while the A3 panel is built
         cur = decode(tb);
-        build_a3(cur.o3);
+        if (xtma) {
+            issue_x(cur);
+            pending_x = 1;
+        }
         stage_rows(cur, 0);
+        build_a3(cur.o3);
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         build_kr(0, 0, 0, kThreads);
         publish_smem();
         issue_gemm1(0, 0);
-        if (xtma) {
-            issue_x(cur);
-            pending_x = 1;
-        }
     }
     for (int t = tb, k = 0; t < te; ++t, ++k) {
         const int cb = k & 1;
@@ -530,16 +536,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (has_next && !new_b3) build_kr((k + 1) & 1, (k + 1) & 1, kKrLo, kKrCnt);
         bool t_ready = false;
-        auto read_t = [&]() {   // T from TMEM to Ts[row][j] (Yr is consumed once T and G3 are done)
-            if (16 * cq < R) {
-                float tv[16];
-                tmem_ld16(tT + lane_base + (uint32_t)(16 * cq), tv);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<float4*>(Ts + row * ldT + 16 * cq + 4 * q) =
-                        make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
-            }
-        };
         auto flush_g3 = [&](int b3) {   // G3 rows of an i3 block: TMEM -> global
             if (16 * cq < R) {
                 const int64_t i3 = (int64_t)b3 * kCols + row;
@@ -557,7 +553,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!wait_phase(&mbar2, ph2)) fail();
                 ph2 ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                read_t();
                 t_ready = true;
             }
             if (wantG && g3_started) {
@@ -570,64 +565,90 @@ __global__ void __launch_bounds__(kThreads, 1)
             build_kr((k + 1) & 1, (k + 1) & 1, 0, kThreads);
         }
         if (has_next) publish_smem();   // KR (and A3) of the next tile are in place
-        // ---- T of this tile
-        if (g23 && !t_ready) {
-            if (!wait_phase(&mbar2, ph2)) fail();
-            ph2 ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            read_t();
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        // ---- thread 0 issues the next model product while warps 1 .. 15 reduce T into G1, G2, gs
+        // ---- thread 0 queues the next model product behind T / G3 on the tensor pipe; every warp
+        // then reduces its 32 rows x 16 columns of T straight from TMEM (row = 16 i1l + i2l):
+        //   G1[i1l] += s * sum_i2l A2[i2l] * T      over the 16 lanes of a half-warp (shuffles)
+        //   gs      += sum_i1l A1[i1l] * (sum_i2l A2[i2l] * T)
+        //   G2[i2l] += sum_i1l s * A1[i1l] * T      over lane pairs, then the 4 lane quarters in Yr
         if (has_next) issue_gemm1((k + 1) & 1, (k + 1) & 1);
+        float* red = reinterpret_cast<float*>(Yr);   // [4 quarters][16 i2l][kStageLd] G2 partials
         if (g23) {
-            const float* A1 = stage + cb * 24 * kStageLd;
-            const float* A2 = A1 + kB1 * kStageLd;
-            const int per = R / 4;
-            for (int it = tid - kKrLo; it >= 0 && it < (2 * kB1 + kB2) * per; it += kThreads - kKrLo) {
-                const int rr = it / per, j = (it - rr * per) * 4;
-                const float4 s4 = *reinterpret_cast<const float4*>(sv + j);
-                if (rr < 2 * kB1) {   // G1 row i1l (and gs): half of the sum over the 16 i2 rows
-                    const int i1l = rr >> 1, h0 = (rr & 1) * (kB2 / 2);
-                    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!t_ready) {
+                if (!wait_phase(&mbar2, ph2)) fail();
+                ph2 ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+            }
+            if (16 * cq < R) {
+                const int i1l = row / kB2, i2l = row % kB2;
+                const float* A1 = stage + (cb * 24 + i1l) * kStageLd + 16 * cq;
+                const float* A2 = stage + (cb * 24 + kB1 + i2l) * kStageLd + 16 * cq;
+                float tv[16];
+                __syncwarp();   // lane 0 may come from the MMA issue: the TMEM load is warp-wide
+                tmem_ld16(tT + lane_base + (uint32_t)(16 * cq), tv);
+                float u[16], v[16];
 #pragma unroll
-                    for (int i2l = h0; i2l < h0 + kB2 / 2; ++i2l) {
-                        const float4 w = *reinterpret_cast<const float4*>(A2 + i2l * kStageLd + j);
-                        const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
-                        g.x = fmaf(w.x, tv.x, g.x);
-                        g.y = fmaf(w.y, tv.y, g.y);
-                        g.z = fmaf(w.z, tv.z, g.z);
-                        g.w = fmaf(w.w, tv.w, g.w);
-                    }
-                    if (wantS) {
-                        const float4 a1 = *reinterpret_cast<const float4*>(A1 + i1l * kStageLd + j);
-                        atomicAdd(gsacc + j, a1.x * g.x);
-                        atomicAdd(gsacc + j + 1, a1.y * g.y);
-                        atomicAdd(gsacc + j + 2, a1.z * g.z);
-                        atomicAdd(gsacc + j + 3, a1.w * g.w);
-                    }
-                    if (wantG && cur.i1b + i1l < I1)
-                        atomicAdd(reinterpret_cast<float4*>(a.G[0] + (cur.i1b + i1l) * R + j),
-                                  make_float4(s4.x * g.x, s4.y * g.y, s4.z * g.z, s4.w * g.w));
-                } else if (wantG) {   // G2 row i2l: sum over the 8 i1 rows of (s A1) T
-                    const int i2l = rr - 2 * kB1;
-                    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = 0; q < 4; ++q) {
+                    const float4 w2 = *reinterpret_cast<const float4*>(A2 + 4 * q);
+                    const float4 w1 = *reinterpret_cast<const float4*>(A1 + 4 * q);
+                    const float4 s4 = *reinterpret_cast<const float4*>(sv + 16 * cq + 4 * q);
+                    u[4 * q] = w2.x * tv[4 * q], u[4 * q + 1] = w2.y * tv[4 * q + 1];
+                    u[4 * q + 2] = w2.z * tv[4 * q + 2], u[4 * q + 3] = w2.w * tv[4 * q + 3];
+                    v[4 * q] = s4.x * w1.x * tv[4 * q], v[4 * q + 1] = s4.y * w1.y * tv[4 * q + 1];
+                    v[4 * q + 2] = s4.z * w1.z * tv[4 * q + 2], v[4 * q + 3] = s4.w * w1.w * tv[4 * q + 3];
+                }
+                // reduce-scatter of u over the half-warp: lane ends with column (lane & 15)
+                const bool b8 = lane & 8, b4 = lane & 4, b2 = lane & 2, b1 = lane & 1;
 #pragma unroll
-                    for (int i1l = 0; i1l < kB1; ++i1l) {
-                        const float4 w = *reinterpret_cast<const float4*>(A1 + i1l * kStageLd + j);
-                        const float4 tv = *reinterpret_cast<const float4*>(Ts + (i1l * kB2 + i2l) * ldT + j);
-                        g.x = fmaf(s4.x * w.x, tv.x, g.x);
-                        g.y = fmaf(s4.y * w.y, tv.y, g.y);
-                        g.z = fmaf(s4.z * w.z, tv.z, g.z);
-                        g.w = fmaf(s4.w * w.w, tv.w, g.w);
+                for (int i = 0; i < 8; ++i) {
+                    const float snd = b8 ? u[i] : u[i + 8];
+                    u[i] = (b8 ? u[i + 8] : u[i]) + __shfl_xor_sync(SGCP_FULL_MASK, snd, 8);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float snd = b4 ? u[i] : u[i + 4];
+                    u[i] = (b4 ? u[i + 4] : u[i]) + __shfl_xor_sync(SGCP_FULL_MASK, snd, 4);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float snd = b2 ? u[i] : u[i + 2];
+                    u[i] = (b2 ? u[i + 2] : u[i]) + __shfl_xor_sync(SGCP_FULL_MASK, snd, 2);
+                }
+                {
+                    const float snd = b1 ? u[0] : u[1];
+                    u[0] = (b1 ? u[1] : u[0]) + __shfl_xor_sync(SGCP_FULL_MASK, snd, 1);
+                }
+                const int c = lane & 15;
+                if (wantS) gs_acc = fmaf(A1[c], u[0], gs_acc);
+                if (wantG) {
+                    if (cur.i1b + i1l < I1) atomicAdd(a.G[0] + (cur.i1b + i1l) * R + 16 * cq + c, s_c * u[0]);
+                    // G2: lanes l and l ^ 16 hold the same i2l; keep 8 columns each, then stage them
+                    const bool b16 = lane & 16;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float snd = b16 ? v[i] : v[i + 8];
+                        v[i] = (b16 ? v[i + 8] : v[i]) + __shfl_xor_sync(SGCP_FULL_MASK, snd, 16);
                     }
-                    if (cur.i2b + i2l < I2) atomicAdd(reinterpret_cast<float4*>(a.G[1] + (cur.i2b + i2l) * R + j), g);
+                    float* dst = red + (quarter * kB2 + i2l) * kStageLd + 16 * cq + (b16 ? 8 : 0);
+                    *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4*>(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
                 }
             }
         }
-        __syncthreads();   // Ts (= Yr) and the stage buffer of this tile are free
-        if (abort_flag) break;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (g23 && wantG && tid < kB2 * 16) {   // G2 rows of the tile: the 4 quarters' partials
+            const int i2l = tid >> 4, c4 = (tid & 15) * 4;
+            if (c4 < R && cur.i2b + i2l < I2) {
+                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 w = *reinterpret_cast<const float4*>(red + (q * kB2 + i2l) * kStageLd + c4);
+                    g.x += w.x, g.y += w.y, g.z += w.z, g.w += w.w;
+                }
+                atomicAdd(reinterpret_cast<float4*>(a.G[1] + (cur.i2b + i2l) * R + c4), g);
+            }
+        }
+        // red (= Yr) is read before the next epilogue writes Y: the barrier at the loop top orders it
         cur = nxt;
     }
 
@@ -635,16 +656,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (pending_x) wait_phase(&mbar_x, phx);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (wantG && g3_started && !abort_flag) {
-        if (16 * cq < R) {
-            const int64_t i3 = (int64_t)b3_open * kCols + row;
-            float g[16];
-            tmem_ld16(tG3 + lane_base + (uint32_t)(16 * cq), g);
-            if (i3 < I3)
+    // G3 of the open i3 block: TMEM -> a padded staging copy in Xs (free now; 68-float rows keep
+    // the 16-byte stores conflict-free) -> one bulk reduce-add into G^(3) per row, so the blocks
+    // sharing an i3 block add whole rows in L2 instead of 16-byte atomics
+    if (wantS) {   // lanes l and l ^ 16 hold the same column
+        const float g = gs_acc + __shfl_xor_sync(SGCP_FULL_MASK, gs_acc, 16);
+        if (lane < 16 && 16 * cq < R && g != 0.0f) atomicAdd(gsacc + 16 * cq + lane, g);
+    }
+    const bool g3_flush = wantG && g3_started && !abort_flag;
+    if (g3_flush && 16 * cq < R) {
+        float g[16];
+        tmem_ld16(tG3 + lane_base + (uint32_t)(16 * cq), g);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    atomicAdd(reinterpret_cast<float4*>(a.G[2] + i3 * R + 16 * cq + 4 * q),
-                              make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4*>(Xs + row * kStageLd + 16 * cq + 4 * q) =
+                make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (g3_flush && tid < kRows) {
+        const int64_t i3 = (int64_t)b3_open * kCols + tid;
+        if (i3 < I3) {
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;"
+                         ::"l"(a.G[2] + i3 * R), "r"(smem_u32(Xs + tid * kStageLd)), "r"((uint32_t)(R * 4))
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // Xs is read before the block ends
         }
     }
     __syncthreads();

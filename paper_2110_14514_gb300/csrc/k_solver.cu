@@ -14,6 +14,8 @@
 //     = D (Gamma_k * S_H) + Abar ((Gamma_k - Gammabar_k) * S_H),   D = A - Abar,
 // and Gamma_k - Gammabar_k is summed from differences E_n = D^(n)'A^(n)
 // (telescoping over the Hadamard factors) so nothing cancels when A ~ Abar.
+#include <type_traits>
+
 #include "internal.h"
 #include "sgcp.h"
 
@@ -186,8 +188,8 @@ cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const doubl
 
 // ---------------------------------------------------------------------------
 // Factor row update: g = G + lambda a + d B_k + abar C_k; ADAM step (Alg. 2)
-// with the bias-corrected rate of iteration i; projection a <- max(a, l);
-// G <- 0 for the next gradient.  The last block advances i and beta^i.
+// with the bias-corrected rate of iteration i (written by k_epoch_begin);
+// projection a <- max(a, l); G <- 0 for the next gradient.
 // ---------------------------------------------------------------------------
 // Warp-per-row layout: LPR = min(R, 32) lanes per row (a template parameter so
 // the matrix-vector loops unroll), lane l holds columns l, l + 32, ... of its
@@ -287,9 +289,126 @@ static int solver_num_sms() {
     return n;
 }
 
+// FP32, R <= 32, history terms possible: a warp owns a chunk of kFuChunk rows of one mode and
+// keeps column j of B_k and C_k in lane j's registers, so the coefficients are read once per
+// chunk instead of once per row.  The chunk's d = a - abar and abar rows are staged in shared
+// memory and read back as 16-byte broadcasts; lane j then forms column j of every row.
+constexpr int kFuChunk = 16;
+
+__device__ __forceinline__ int fu_chunk_of(const FactorUpdateArgs<float>& a, int64_t c, int64_t& r0, int64_t& r1) {
+    for (int k = 0; k < a.ndim; ++k) {
+        const int64_t beg = a.row_off[k], end = k + 1 < a.ndim ? a.row_off[k + 1] : a.nrows;
+        const int64_t n = (end - beg + kFuChunk - 1) / kFuChunk;
+        if (c < n) {
+            r0 = beg + c * kFuChunk;
+            r1 = r0 + kFuChunk < end ? r0 + kFuChunk : end;
+            return k;
+        }
+        c -= n;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(256) k_factor_update_chunks(const FactorUpdateArgs<float> a, int64_t nchunks) {
+    if (a.skip && *a.skip) return;
+    __shared__ __align__(16) float sD[8][kFuChunk][32], sB[8][kFuChunk][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int R = a.R, j = lane;
+    const bool on = j < R;
+    const bool hist = a.B != nullptr && *a.hist_len > 0;
+    const float at = (float)*a.rate;
+    const float b1 = (float)a.beta1, b2 = (float)a.beta2, c1 = (float)(1.0 - a.beta1), c2 = (float)(1.0 - a.beta2);
+    const float lam = (float)a.lam, eps = (float)a.eps, lower = (float)a.lower;
+    const int64_t c = (int64_t)blockIdx.x * 8 + warp;
+    if (c >= nchunks) return;
+    int64_t r0 = 0, r1 = 0;
+    const int k = fu_chunk_of(a, c, r0, r1);
+    if (k < 0) return;
+    float Bj[32], Cj[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        const bool lo = hist && on && l < R;
+        Bj[l] = lo ? __ldg(a.B + ((int64_t)k * R + l) * R + j) : 0.0f;
+        Cj[l] = lo ? __ldg(a.C + ((int64_t)k * R + l) * R + j) : 0.0f;
+    }
+    float av[kFuChunk];
+#pragma unroll
+    for (int r = 0; r < kFuChunk; ++r) {
+        const int64_t row = r0 + r;
+        const bool act = on && row < r1;
+        const float x = act ? a.A[row * R + j] : 0.0f;
+        const float xb = act ? a.Abar[row * R + j] : 0.0f;
+        av[r] = x;
+        sD[warp][r][lane] = x - xb;     // zero outside the rank, so the broadcast loop may run to 32
+        sB[warp][r][lane] = xb;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kFuChunk; ++r) {
+        const int64_t row = r0 + r;
+        if (row >= r1) continue;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (hist) {
+#pragma unroll
+            for (int l4 = 0; l4 < 8; ++l4) {
+                if (4 * l4 < R) {
+                    const float4 d = *reinterpret_cast<const float4*>(&sD[warp][r][4 * l4]);
+                    const float4 b = *reinterpret_cast<const float4*>(&sB[warp][r][4 * l4]);
+                    acc[0] = fmaf(d.x, Bj[4 * l4], fmaf(b.x, Cj[4 * l4], acc[0]));
+                    acc[1] = fmaf(d.y, Bj[4 * l4 + 1], fmaf(b.y, Cj[4 * l4 + 1], acc[1]));
+                    acc[2] = fmaf(d.z, Bj[4 * l4 + 2], fmaf(b.z, Cj[4 * l4 + 2], acc[2]));
+                    acc[3] = fmaf(d.w, Bj[4 * l4 + 3], fmaf(b.w, Cj[4 * l4 + 3], acc[3]));
+                }
+            }
+        }
+        if (!on) continue;
+        const int64_t idx = row * R + j;
+        const float g = a.G[idx] + lam * av[r] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        if (a.grad_only) {
+            a.G[idx] = g;
+            continue;
+        }
+        const float u = b1 * a.u[idx] + c1 * g;
+        const float v = b2 * a.v[idx] + c2 * g * g;
+        float an = av[r] - at * u / (sqrtf(v) + eps);
+        if (an < lower) an = lower;
+        a.u[idx] = u;
+        a.v[idx] = v;
+        a.A[idx] = an;
+        a.G[idx] = 0.0f;
+    }
+}
+
+template <typename T>
+static bool factor_update_chunked(const FactorUpdateArgs<T>& a, cudaStream_t st, cudaError_t* err) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (a.R > 32 || a.B == nullptr) return false;
+        int64_t nchunks = 0;
+        for (int k = 0; k < a.ndim; ++k) {
+            const int64_t end = k + 1 < a.ndim ? a.row_off[k + 1] : a.nrows;
+            nchunks += (end - a.row_off[k] + kFuChunk - 1) / kFuChunk;
+        }
+        const int64_t blocks = (nchunks + 7) / 8;
+        if (blocks < 1 || blocks > 0x7fffffff) return false;
+        k_factor_update_chunks<<<(int)blocks, 256, 0, st>>>(a, nchunks);
+        *err = cudaGetLastError();
+        return true;
+    } else {
+        (void)a, (void)st, (void)err;
+        return false;
+    }
+}
+
 template <typename T>
 cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, int64_t* launches) {
     if (a.R > 128) return cudaErrorInvalidValue;
+    {
+        cudaError_t e = cudaSuccess;
+        if (factor_update_chunked(a, st, &e)) {
+            if (launches) *launches += 1;
+            return e;
+        }
+    }
     const int LPR = a.R < 32 ? a.R : 32;
     const int rows_per_block = 8 * (32 / LPR);
     // one row group per warp, every row in flight at once

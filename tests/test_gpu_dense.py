@@ -100,6 +100,28 @@ def test_dense_loss_only_and_partial_wants(sg):
     assert rel(gs, gso) < 1e-5
 
 
+def test_misaligned_factor_or_gradient_pointer_is_an_argument_error(sg):
+    """A[k] / G_out[k] 4 bytes off a 16-byte boundary: rejected on the host, nothing launched."""
+    X, A, s = case((20, 24, 28), 16, "gaussian", np.float32, seed=4)
+    p = sg.params(X.shape, 16, "gaussian")
+    with sg.Context(p, [dev(a) for a in A]) as ctx:
+        Ad = [dev(a) for a in A]
+        base = torch.zeros(A[1].size + 4, dtype=torch.float32, device="cuda")
+        off = base[1:1 + A[1].size].view(A[1].shape)
+        off.copy_(Ad[1])
+        with pytest.raises(sg.SgcpError) as ei:
+            ctx.gradient(dev(s), [Ad[0], off, Ad[2]], X=dev(X), want=sg.WANT_LOSS)
+        assert ei.value.status == sg.ERR_ARG
+        G = [torch.zeros_like(a) for a in Ad]
+        gbase = torch.zeros(G[2].numel() + 4, dtype=torch.float32, device="cuda")
+        G[2] = gbase[2:2 + G[2].numel()].view(G[2].shape)
+        with pytest.raises(sg.SgcpError) as ei:
+            ctx.gradient(dev(s), Ad, X=dev(X), want=sg.WANT_FACTORS, G=G)
+        assert ei.value.status == sg.ERR_ARG
+        ctx.gradient(dev(s), Ad, X=dev(X), want=sg.WANT_FACTORS)   # the context is still usable
+        ctx.check()
+
+
 def test_full_size_dense_poisson_3way(sg):
     cfg = S.workload("dense_poisson_3way")
     X, _ = S.dense_slice(cfg, 1)

@@ -64,6 +64,34 @@ def test_tensor_core_gradient_matches_oracle(sg, prec, loss, dims, R):
     assert abs(f - Fo) <= 1e-4 * abs(Fo), (f, Fo)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_blocks_spanning_i3_blocks_and_partial_wants(sg, prec):
+    """234 tiles of 8 x 16 x 128 over 152 SMs: one block runs two tiles of different i3 blocks
+    (the A3 panel is rebuilt and G3 flushed mid-run); each requested output alone and all three
+    together."""
+    rng = np.random.default_rng(17)
+    dims, R = (97, 82, 260), 32
+    A = [(rng.standard_normal((n, R)) / R ** (1 / 6)).astype(np.float32) for n in dims]
+    s = (0.5 + rng.random(R)).astype(np.float32)
+    X = rng.standard_normal(dims).astype(np.float32)
+    Go, gso, Fo = gcp.dense_gradient(X, s, A, "gaussian")
+    p = sg.params(dims, R, "gaussian", precision=sg.PREC_BF16_MTTKRP if prec == "bf16" else sg.PREC_F16_MTTKRP)
+    with sg.Context(p, [dev(a) for a in A]) as ctx:
+        Ad, sd, Xd = [dev(a) for a in A], dev(s), dev(X)
+        for want in (sg.WANT_FACTORS, sg.WANT_TEMPORAL, sg.WANT_LOSS, sg.WANT_FACTORS | sg.WANT_TEMPORAL | sg.WANT_LOSS):
+            G, gs, f = ctx.gradient(sd, Ad, X=Xd, want=want)
+            ctx.check()
+            if want & sg.WANT_FACTORS:
+                for k in range(3):
+                    assert rel(G[k].cpu().numpy(), Go[k]) < 2e-2, (want, k)
+            else:
+                assert G is None
+            if want & sg.WANT_TEMPORAL:
+                assert rel(gs.cpu().numpy(), gso) < 2e-2, want
+            if want & sg.WANT_LOSS:
+                assert abs(f.item() - Fo) <= 1e-4 * abs(Fo), (want, f.item(), Fo)
+
+
 def test_precision_report_dense_gaussian_256(sg):
     """256^3, R = 64, Gaussian loss with noise at 1% of the planted RMS: error of every result
     against the FP64 oracle for the FP32 CUDA-core path and the BF16 / FP16 tensor-core paths."""
