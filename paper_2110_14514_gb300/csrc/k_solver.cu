@@ -309,13 +309,14 @@ __device__ __forceinline__ int fu_chunk_of(const FactorUpdateArgs<float>& a, int
     return -1;
 }
 
-__global__ void __launch_bounds__(256) k_factor_update_chunks(const FactorUpdateArgs<float> a, int64_t nchunks) {
+__global__ void __launch_bounds__(256, 1) k_factor_update_chunks(const FactorUpdateArgs<float> a, int64_t nchunks) {
     if (a.skip && *a.skip) return;
     __shared__ __align__(16) float sD[8][kFuChunk][32], sB[8][kFuChunk][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = a.R, j = lane;
     const bool on = j < R;
     const bool hist = a.B != nullptr && *a.hist_len > 0;
+    const bool step = !a.grad_only;
     const float at = (float)*a.rate;
     const float b1 = (float)a.beta1, b2 = (float)a.beta2, c1 = (float)(1.0 - a.beta1), c2 = (float)(1.0 - a.beta2);
     const float lam = (float)a.lam, eps = (float)a.eps, lower = (float)a.lower;
@@ -324,6 +325,22 @@ __global__ void __launch_bounds__(256) k_factor_update_chunks(const FactorUpdate
     int64_t r0 = 0, r1 = 0;
     const int k = fu_chunk_of(a, c, r0, r1);
     if (k < 0) return;
+    // every load of the chunk is issued before the first store, so the rows' round trips overlap
+    float av[kFuChunk], gv[kFuChunk], uv[kFuChunk], vv[kFuChunk];
+#pragma unroll
+    for (int r = 0; r < kFuChunk; ++r) {
+        const int64_t row = r0 + r;
+        const bool act = on && row < r1;
+        const int64_t idx = act ? row * R + j : 0;
+        const float x = act ? a.A[idx] : 0.0f;
+        const float xb = act ? a.Abar[idx] : 0.0f;
+        gv[r] = act ? a.G[idx] : 0.0f;
+        uv[r] = act && step ? a.u[idx] : 0.0f;
+        vv[r] = act && step ? a.v[idx] : 0.0f;
+        av[r] = x;
+        sD[warp][r][lane] = x - xb;     // zero outside the rank, so the broadcast loop may run to 32
+        sB[warp][r][lane] = xb;
+    }
     float Bj[32], Cj[32];
 #pragma unroll
     for (int l = 0; l < 32; ++l) {
@@ -331,22 +348,10 @@ __global__ void __launch_bounds__(256) k_factor_update_chunks(const FactorUpdate
         Bj[l] = lo ? __ldg(a.B + ((int64_t)k * R + l) * R + j) : 0.0f;
         Cj[l] = lo ? __ldg(a.C + ((int64_t)k * R + l) * R + j) : 0.0f;
     }
-    float av[kFuChunk];
-#pragma unroll
-    for (int r = 0; r < kFuChunk; ++r) {
-        const int64_t row = r0 + r;
-        const bool act = on && row < r1;
-        const float x = act ? a.A[row * R + j] : 0.0f;
-        const float xb = act ? a.Abar[row * R + j] : 0.0f;
-        av[r] = x;
-        sD[warp][r][lane] = x - xb;     // zero outside the rank, so the broadcast loop may run to 32
-        sB[warp][r][lane] = xb;
-    }
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < kFuChunk; ++r) {
         const int64_t row = r0 + r;
-        if (row >= r1) continue;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         if (hist) {
 #pragma unroll
@@ -361,15 +366,15 @@ __global__ void __launch_bounds__(256) k_factor_update_chunks(const FactorUpdate
                 }
             }
         }
-        if (!on) continue;
+        if (!on || row >= r1) continue;
         const int64_t idx = row * R + j;
-        const float g = a.G[idx] + lam * av[r] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
-        if (a.grad_only) {
+        const float g = gv[r] + lam * av[r] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        if (!step) {
             a.G[idx] = g;
             continue;
         }
-        const float u = b1 * a.u[idx] + c1 * g;
-        const float v = b2 * a.v[idx] + c2 * g * g;
+        const float u = b1 * uv[r] + c1 * g;
+        const float v = b2 * vv[r] + c2 * g * g;
         float an = av[r] - at * u / (sqrtf(v) + eps);
         if (an < lower) an = lower;
         a.u[idx] = u;
