@@ -146,6 +146,14 @@ struct FactorUpdateArgs {
     const double* rate;       // bias-corrected learning rate of this iteration (see k_epoch_begin)
     const int32_t* skip;
     int grad_only;            // 1: store the full gradient g in G and leave A, u, v untouched
+    // Optional (FP32, R <= 32): Grams of the updated rows for the next iteration's history terms.
+    // gacc [2][ndim][R][R] (A'A, D'A; zero on entry, left zero), SH [R][R]; the last block writes
+    // Bn / Cn (may be B / C: every block has read them before the last block starts).
+    float* gacc;
+    const double* SH;
+    T* Bn;
+    T* Cn;
+    SolverState* tk;          // ticket that elects the last block
 };
 
 template <typename T>

@@ -289,98 +289,177 @@ static int solver_num_sms() {
     return n;
 }
 
-// FP32, R <= 32, history terms possible: a warp owns a chunk of kFuChunk rows of one mode and
-// keeps column j of B_k and C_k in lane j's registers, so the coefficients are read once per
-// chunk instead of once per row.  The chunk's d = a - abar and abar rows are staged in shared
-// memory and read back as 16-byte broadcasts; lane j then forms column j of every row.
-constexpr int kFuChunk = 16;
+// FP32, R <= 32, history terms possible.  A block owns up to kFuBlockRows rows of one mode and
+// stages B_k and C_k in shared memory; a warp updates 4 rows at a time with lane j on column j:
+// the rows' d = a - abar and abar are staged per warp and read as 16-byte broadcasts, B_k[l][j]
+// and C_k[l][j] as conflict-free words, so one coefficient load serves 4 rows.  Every load of
+// the 4 rows is issued before the first store.  With gacc set the block also keeps its updated
+// rows and their d in shared memory and sums the Grams A'A and D'A over them (thread = one l and
+// 4 columns); the block sums are added into gacc with 16-byte float atomics (GB300's FP64
+// atomics are far slower) and the last block turns them into the next iteration's B_k, C_k
+// (the coefficients k_hist_coeffs forms from k_gram's sums).
+constexpr int kFuBlockRows = 64;
+constexpr int kFuGroup = 4;        // rows a warp updates at once
+constexpr int kFuWarps = 8;
 
-__device__ __forceinline__ int fu_chunk_of(const FactorUpdateArgs<float>& a, int64_t c, int64_t& r0, int64_t& r1) {
-    for (int k = 0; k < a.ndim; ++k) {
-        const int64_t beg = a.row_off[k], end = k + 1 < a.ndim ? a.row_off[k + 1] : a.nrows;
-        const int64_t n = (end - beg + kFuChunk - 1) / kFuChunk;
-        if (c < n) {
-            r0 = beg + c * kFuChunk;
-            r1 = r0 + kFuChunk < end ? r0 + kFuChunk : end;
-            return k;
-        }
-        c -= n;
-    }
-    return -1;
+__host__ __device__ inline int64_t fu_blocks_of_mode(const FactorUpdateArgs<float>& a, int k, int64_t* beg,
+                                                     int64_t* end) {
+    *beg = a.row_off[k];
+    *end = k + 1 < a.ndim ? a.row_off[k + 1] : a.nrows;
+    return (*end - *beg + kFuBlockRows - 1) / kFuBlockRows;
 }
 
-__global__ void __launch_bounds__(256, 1) k_factor_update_chunks(const FactorUpdateArgs<float> a, int64_t nchunks) {
+__global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdateArgs<float> a) {
     if (a.skip && *a.skip) return;
-    __shared__ __align__(16) float sD[8][kFuChunk][32], sB[8][kFuChunk][32];
+    __shared__ __align__(16) float sBk[32][32], sCk[32][32];
+    __shared__ __align__(16) float sD[kFuWarps][kFuGroup][32], sAb[kFuWarps][kFuGroup][32];
+    extern __shared__ __align__(16) float fu_dyn[];   // with gacc: updated rows and their d
+    float(*sA)[32] = reinterpret_cast<float(*)[32]>(fu_dyn);
+    float(*sDn)[32] = reinterpret_cast<float(*)[32]>(fu_dyn + kFuBlockRows * 32);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = a.R, j = lane;
     const bool on = j < R;
     const bool hist = a.B != nullptr && *a.hist_len > 0;
     const bool step = !a.grad_only;
+    const bool gram = a.gacc != nullptr && step;
+    // this block's mode and rows
+    int k = -1;
+    int64_t b0 = 0, b1 = 0;
+    {
+        int64_t b = blockIdx.x;
+        for (int m = 0; m < a.ndim && k < 0; ++m) {
+            int64_t beg, end;
+            const int64_t nb = fu_blocks_of_mode(a, m, &beg, &end);
+            if (b < nb) {
+                k = m;
+                b0 = beg + b * kFuBlockRows;
+                b1 = b0 + kFuBlockRows < end ? b0 + kFuBlockRows : end;
+            } else {
+                b -= nb;
+            }
+        }
+    }
+    if (k < 0) return;   // the grid is sized from the same geometry
+    const int RR = R * R;
+    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+        const int l = i >> 5, m = i & 31;
+        const bool in = hist && l < R && m < R;
+        sBk[l][m] = in ? __ldg(a.B + (int64_t)k * RR + l * R + m) : 0.0f;
+        sCk[l][m] = in ? __ldg(a.C + (int64_t)k * RR + l * R + m) : 0.0f;
+    }
+    __syncthreads();
     const float at = (float)*a.rate;
-    const float b1 = (float)a.beta1, b2 = (float)a.beta2, c1 = (float)(1.0 - a.beta1), c2 = (float)(1.0 - a.beta2);
+    const float b1c = (float)a.beta1, b2c = (float)a.beta2, c1 = (float)(1.0 - a.beta1), c2 = (float)(1.0 - a.beta2);
     const float lam = (float)a.lam, eps = (float)a.eps, lower = (float)a.lower;
-    const int64_t c = (int64_t)blockIdx.x * 8 + warp;
-    if (c >= nchunks) return;
-    int64_t r0 = 0, r1 = 0;
-    const int k = fu_chunk_of(a, c, r0, r1);
-    if (k < 0) return;
-    // every load of the chunk is issued before the first store, so the rows' round trips overlap
-    float av[kFuChunk], gv[kFuChunk], uv[kFuChunk], vv[kFuChunk];
+    const int nrows = (int)(b1 - b0);
+#pragma unroll 1
+    for (int g0 = warp * kFuGroup; g0 < kFuBlockRows; g0 += kFuWarps * kFuGroup) {
+        float av[kFuGroup], gv[kFuGroup], uv[kFuGroup], vv[kFuGroup], xbv[kFuGroup];
 #pragma unroll
-    for (int r = 0; r < kFuChunk; ++r) {
-        const int64_t row = r0 + r;
-        const bool act = on && row < r1;
-        const int64_t idx = act ? row * R + j : 0;
-        const float x = act ? a.A[idx] : 0.0f;
-        const float xb = act ? a.Abar[idx] : 0.0f;
-        gv[r] = act ? a.G[idx] : 0.0f;
-        uv[r] = act && step ? a.u[idx] : 0.0f;
-        vv[r] = act && step ? a.v[idx] : 0.0f;
-        av[r] = x;
-        sD[warp][r][lane] = x - xb;     // zero outside the rank, so the broadcast loop may run to 32
-        sB[warp][r][lane] = xb;
-    }
-    float Bj[32], Cj[32];
+        for (int r = 0; r < kFuGroup; ++r) {
+            const bool act = on && g0 + r < nrows;
+            const int64_t idx = act ? (b0 + g0 + r) * R + j : 0;
+            av[r] = act ? a.A[idx] : 0.0f;
+            xbv[r] = act ? a.Abar[idx] : 0.0f;
+            gv[r] = act ? a.G[idx] : 0.0f;
+            uv[r] = act && step ? a.u[idx] : 0.0f;
+            vv[r] = act && step ? a.v[idx] : 0.0f;
+        }
 #pragma unroll
-    for (int l = 0; l < 32; ++l) {
-        const bool lo = hist && on && l < R;
-        Bj[l] = lo ? __ldg(a.B + ((int64_t)k * R + l) * R + j) : 0.0f;
-        Cj[l] = lo ? __ldg(a.C + ((int64_t)k * R + l) * R + j) : 0.0f;
-    }
-    __syncwarp();
+        for (int r = 0; r < kFuGroup; ++r) {
+            sD[warp][r][lane] = av[r] - xbv[r];   // zero outside the rank and the block's rows
+            sAb[warp][r][lane] = xbv[r];
+        }
+        __syncwarp();
+        float acc[kFuGroup];
 #pragma unroll
-    for (int r = 0; r < kFuChunk; ++r) {
-        const int64_t row = r0 + r;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < kFuGroup; ++r) acc[r] = 0.0f;
         if (hist) {
+#pragma unroll 2
+            for (int l4 = 0; l4 < R; l4 += 4) {
+                float bq[4], cq[4];
 #pragma unroll
-            for (int l4 = 0; l4 < 8; ++l4) {
-                if (4 * l4 < R) {
-                    const float4 d = *reinterpret_cast<const float4*>(&sD[warp][r][4 * l4]);
-                    const float4 b = *reinterpret_cast<const float4*>(&sB[warp][r][4 * l4]);
-                    acc[0] = fmaf(d.x, Bj[4 * l4], fmaf(b.x, Cj[4 * l4], acc[0]));
-                    acc[1] = fmaf(d.y, Bj[4 * l4 + 1], fmaf(b.y, Cj[4 * l4 + 1], acc[1]));
-                    acc[2] = fmaf(d.z, Bj[4 * l4 + 2], fmaf(b.z, Cj[4 * l4 + 2], acc[2]));
-                    acc[3] = fmaf(d.w, Bj[4 * l4 + 3], fmaf(b.w, Cj[4 * l4 + 3], acc[3]));
+                for (int q = 0; q < 4; ++q) {
+                    bq[q] = sBk[l4 + q][j];
+                    cq[q] = sCk[l4 + q][j];
+                }
+#pragma unroll
+                for (int r = 0; r < kFuGroup; ++r) {
+                    const float4 d = *reinterpret_cast<const float4*>(&sD[warp][r][l4]);
+                    const float4 x = *reinterpret_cast<const float4*>(&sAb[warp][r][l4]);
+                    acc[r] = fmaf(d.x, bq[0], fmaf(x.x, cq[0], acc[r]));
+                    acc[r] = fmaf(d.y, bq[1], fmaf(x.y, cq[1], acc[r]));
+                    acc[r] = fmaf(d.z, bq[2], fmaf(x.z, cq[2], acc[r]));
+                    acc[r] = fmaf(d.w, bq[3], fmaf(x.w, cq[3], acc[r]));
                 }
             }
         }
-        if (!on || row >= r1) continue;
-        const int64_t idx = row * R + j;
-        const float g = gv[r] + lam * av[r] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
-        if (!step) {
-            a.G[idx] = g;
-            continue;
+#pragma unroll
+        for (int r = 0; r < kFuGroup; ++r) {
+            const bool act = on && g0 + r < nrows;
+            float an = 0.0f;
+            if (act) {
+                const int64_t idx = (b0 + g0 + r) * R + j;
+                const float g = gv[r] + lam * av[r] + acc[r];
+                if (!step) {
+                    a.G[idx] = g;
+                } else {
+                    const float u = b1c * uv[r] + c1 * g;
+                    const float v = b2c * vv[r] + c2 * g * g;
+                    an = av[r] - at * u / (sqrtf(v) + eps);
+                    if (an < lower) an = lower;
+                    a.u[idx] = u;
+                    a.v[idx] = v;
+                    a.A[idx] = an;
+                    a.G[idx] = 0.0f;
+                }
+            }
+            if (gram) {
+                sA[g0 + r][lane] = an;
+                sDn[g0 + r][lane] = act ? an - xbv[r] : 0.0f;
+            }
         }
-        const float u = b1 * uv[r] + c1 * g;
-        const float v = b2 * vv[r] + c2 * g * g;
-        float an = av[r] - at * u / (sqrtf(v) + eps);
-        if (an < lower) an = lower;
-        a.u[idx] = u;
-        a.v[idx] = v;
-        a.A[idx] = an;
-        a.G[idx] = 0.0f;
+        __syncwarp();   // sD / sAb of this warp are reused by its next group
+    }
+    if (!gram) return;
+
+    // ---- Grams of the block's updated rows: thread = (l, 4 columns), rows in order
+    __syncthreads();
+    const int l = threadIdx.x >> 3, m4 = (threadIdx.x & 7) * 4;
+    if (l < R && m4 < R) {
+        float p[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+        for (int r = 0; r < nrows; ++r) {
+            const float al = sA[r][l], dl = sDn[r][l];
+            const float4 am = *reinterpret_cast<const float4*>(&sA[r][m4]);
+            p[0] = fmaf(al, am.x, p[0]), p[1] = fmaf(al, am.y, p[1]);
+            p[2] = fmaf(al, am.z, p[2]), p[3] = fmaf(al, am.w, p[3]);
+            e[0] = fmaf(dl, am.x, e[0]), e[1] = fmaf(dl, am.y, e[1]);
+            e[2] = fmaf(dl, am.z, e[2]), e[3] = fmaf(dl, am.w, e[3]);
+        }
+        float* P = a.gacc + (int64_t)k * RR + l * R + m4;
+        float* E = a.gacc + ((int64_t)a.ndim + k) * RR + l * R + m4;
+        atomicAdd(reinterpret_cast<float4*>(P), make_float4(p[0], p[1], p[2], p[3]));
+        atomicAdd(reinterpret_cast<float4*>(E), make_float4(e[0], e[1], e[2], e[3]));
+    }
+    if (last_block_ticket(a.tk)) {   // every block's sums are in: B_k, C_k of the updated factors
+        const bool hon = *a.hist_len > 0;
+        const float* P = a.gacc;
+        const float* E = a.gacc + (int64_t)a.ndim * RR;
+        const int idx[4] = {(int)threadIdx.x, (int)threadIdx.x + 256, (int)threadIdx.x + 512, (int)threadIdx.x + 768};
+        if (a.ndim == 3) hist_coeff_batch<3, 4>(RR, P, E, a.SH, idx, hon, a.Bn, a.Cn);   // RR <= 1024
+        else if (a.ndim == 2) hist_coeff_batch<2, 4>(RR, P, E, a.SH, idx, hon, a.Bn, a.Cn);
+        else {
+            const int i0[2] = {idx[0], idx[1]}, i1[2] = {idx[2], idx[3]};
+            hist_coeff_batch<4, 2>(RR, P, E, a.SH, i0, hon, a.Bn, a.Cn);
+            hist_coeff_batch<4, 2>(RR, P, E, a.SH, i1, hon, a.Bn, a.Cn);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * a.ndim * RR; i += blockDim.x) a.gacc[i] = 0.0f;
+        if (threadIdx.x == 0) {
+            a.tk->ticket = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -388,14 +467,15 @@ template <typename T>
 static bool factor_update_chunked(const FactorUpdateArgs<T>& a, cudaStream_t st, cudaError_t* err) {
     if constexpr (std::is_same<T, float>::value) {
         if (a.R > 32 || a.B == nullptr) return false;
-        int64_t nchunks = 0;
+        int64_t blocks = 0;
         for (int k = 0; k < a.ndim; ++k) {
-            const int64_t end = k + 1 < a.ndim ? a.row_off[k + 1] : a.nrows;
-            nchunks += (end - a.row_off[k] + kFuChunk - 1) / kFuChunk;
+            int64_t beg, end;
+            blocks += fu_blocks_of_mode(a, k, &beg, &end);
         }
-        const int64_t blocks = (nchunks + 7) / 8;
         if (blocks < 1 || blocks > 0x7fffffff) return false;
-        k_factor_update_chunks<<<(int)blocks, 256, 0, st>>>(a, nchunks);
+        const size_t smem = a.gacc ? 2 * kFuBlockRows * 32 * sizeof(float) : 0;
+        cudaFuncSetAttribute(k_factor_update_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_factor_update_rows<<<(int)blocks, 32 * kFuWarps, smem, st>>>(a);
         *err = cudaGetLastError();
         return true;
     } else {
