@@ -174,6 +174,17 @@ struct TemporalStep {
 
 // Last-block election: every block fences its global writes and takes a
 // ticket; the block that takes the last one sees all of them.
+// Two FP32 fused multiply-adds in one instruction (fma.rn.f32x2, Blackwell): each half is
+// rounded exactly as fmaf would round it.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rc, rd;\nmov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
+        "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 __device__ __forceinline__ bool last_block_ticket(SolverState* st) {
     __shared__ int last;
     __threadfence();

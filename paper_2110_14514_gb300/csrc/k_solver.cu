@@ -290,16 +290,16 @@ static int solver_num_sms() {
 }
 
 // FP32, R <= 32, history terms possible.  A block owns up to kFuBlockRows rows of one mode and
-// stages B_k and C_k in shared memory; a warp updates 4 rows at a time with lane j on column j:
+// stages B_k and C_k in shared memory; each warp updates 8 rows at once with lane j on column j:
 // the rows' d = a - abar and abar are staged per warp and read as 16-byte broadcasts, B_k[l][j]
-// and C_k[l][j] as conflict-free words, so one coefficient load serves 4 rows.  Every load of
-// the 4 rows is issued before the first store.  With gacc set the block also keeps its updated
+// and C_k[l][j] as conflict-free words, so one coefficient load serves 8 rows.  Every load of
+// the 8 rows is issued before the first store.  With gacc set the block also keeps its updated
 // rows and their d in shared memory and sums the Grams A'A and D'A over them (thread = one l and
 // 4 columns); the block sums are added into gacc with 16-byte float atomics (GB300's FP64
 // atomics are far slower) and the last block turns them into the next iteration's B_k, C_k
 // (the coefficients k_hist_coeffs forms from k_gram's sums).
 constexpr int kFuBlockRows = 64;
-constexpr int kFuGroup = 4;        // rows a warp updates at once
+constexpr int kFuGroup = kFuBlockRows / 8;   // rows a warp updates (all at once)
 constexpr int kFuWarps = 8;
 
 __host__ __device__ inline int64_t fu_blocks_of_mode(const FactorUpdateArgs<float>& a, int k, int64_t* beg,
@@ -310,19 +310,19 @@ __host__ __device__ inline int64_t fu_blocks_of_mode(const FactorUpdateArgs<floa
 }
 
 __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdateArgs<float> a) {
-    if (a.skip && *a.skip) return;
-    __shared__ __align__(16) float sBk[32][32], sCk[32][32];
+    __shared__ __align__(16) float2 sBk[16][32], sCk[16][32];   // [l / 2][j] = (X[l][j], X[l + 1][j])
     __shared__ __align__(16) float sD[kFuWarps][kFuGroup][32], sAb[kFuWarps][kFuGroup][32];
-    extern __shared__ __align__(16) float fu_dyn[];   // with gacc: updated rows and their d
-    float(*sA)[32] = reinterpret_cast<float(*)[32]>(fu_dyn);
-    float(*sDn)[32] = reinterpret_cast<float(*)[32]>(fu_dyn + kFuBlockRows * 32);
+    // dynamic: a, G, u, v of the warp's rows while B / C apply; with gacc the updated rows and d
+    extern __shared__ __align__(16) float fu_dyn[];
+    float(*sRow)[kFuWarps][kFuGroup][32] = reinterpret_cast<float(*)[kFuWarps][kFuGroup][32]>(fu_dyn);
+    float(*sA)[32] = reinterpret_cast<float(*)[32]>(fu_dyn + 4 * kFuBlockRows * 32);
+    float(*sDn)[32] = reinterpret_cast<float(*)[32]>(fu_dyn + 5 * kFuBlockRows * 32);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = a.R, j = lane;
     const bool on = j < R;
-    const bool hist = a.B != nullptr && *a.hist_len > 0;
     const bool step = !a.grad_only;
     const bool gram = a.gacc != nullptr && step;
-    // this block's mode and rows
+    // this block's mode and rows (no memory access)
     int k = -1;
     int64_t b0 = 0, b1 = 0;
     {
@@ -341,106 +341,176 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     }
     if (k < 0) return;   // the grid is sized from the same geometry
     const int RR = R * R;
-    for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-        const int l = i >> 5, m = i & 31;
-        const bool in = hist && l < R && m < R;
-        sBk[l][m] = in ? __ldg(a.B + (int64_t)k * RR + l * R + m) : 0.0f;
-        sCk[l][m] = in ? __ldg(a.C + (int64_t)k * RR + l * R + m) : 0.0f;
+    const int nrows = (int)(b1 - b0);
+    // The skip flag, the history length, the rate, the coefficients and the rows are all
+    // requested before any of them is used, so the block waits for one round trip, not four.
+    const int32_t skipv = a.skip ? *a.skip : 0;
+    const int32_t hlen = a.B != nullptr ? *a.hist_len : 0;
+    const double rate = *a.rate;
+    float bco[4], cco[4];   // B_k, C_k entries i = tid + 256 q of the padded 32 x 32 tiles
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.x + 256 * q, l = i >> 5, m = i & 31;
+        const bool in = a.B != nullptr && l < R && m < R;
+        bco[q] = in ? __ldg(a.B + (int64_t)k * RR + l * R + m) : 0.0f;
+        cco[q] = in ? __ldg(a.C + (int64_t)k * RR + l * R + m) : 0.0f;
     }
-    __syncthreads();
-    const float at = (float)*a.rate;
+    // the block's rows through 32-bit offsets from its first row
+    float* Ab = a.A + b0 * R;
+    const float* Abarb = a.Abar + b0 * R;
+    float* Gb = a.G + b0 * R;
+    float* ub = a.u + b0 * R;
+    float* vb = a.v + b0 * R;
+    const int g0 = warp * kFuGroup;   // this warp's rows of the block
+    float av[kFuGroup], gv[kFuGroup], uv[kFuGroup], vv[kFuGroup], xbv[kFuGroup];
+#pragma unroll
+    for (int r = 0; r < kFuGroup; ++r) {
+        const bool act = on && g0 + r < nrows;
+        const int o = act ? (g0 + r) * R + j : 0;
+        av[r] = act ? Ab[o] : 0.0f;
+        xbv[r] = act ? Abarb[o] : 0.0f;
+        gv[r] = act ? Gb[o] : 0.0f;
+        uv[r] = act && step ? ub[o] : 0.0f;
+        vv[r] = act && step ? vb[o] : 0.0f;
+    }
+    if (skipv) return;   // the solver has finished: nothing is written
+    const bool hist = hlen > 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.x + 256 * q, l = i >> 5, m = i & 31;
+        reinterpret_cast<float*>(&sBk[l >> 1][m])[l & 1] = hist ? bco[q] : 0.0f;
+        reinterpret_cast<float*>(&sCk[l >> 1][m])[l & 1] = hist ? cco[q] : 0.0f;
+    }
+    const float at = (float)rate;
     const float b1c = (float)a.beta1, b2c = (float)a.beta2, c1 = (float)(1.0 - a.beta1), c2 = (float)(1.0 - a.beta2);
     const float lam = (float)a.lam, eps = (float)a.eps, lower = (float)a.lower;
-    const int nrows = (int)(b1 - b0);
+#pragma unroll
+    for (int r = 0; r < kFuGroup; ++r) {
+        sD[warp][r][lane] = av[r] - xbv[r];   // zero outside the rank and the block's rows
+        sAb[warp][r][lane] = xbv[r];
+        sRow[0][warp][r][lane] = av[r];       // parked in shared memory: the matrix products
+        sRow[1][warp][r][lane] = gv[r];       // below then run without them in registers
+        sRow[2][warp][r][lane] = uv[r];
+        sRow[3][warp][r][lane] = vv[r];
+    }
+    __syncthreads();   // B_k, C_k and every warp's rows are staged
+    // (d B_k + abar C_k)[j] in two interleaved partial sums (even and odd l), packed FMAs
+    float2 acc[kFuGroup];
+#pragma unroll
+    for (int r = 0; r < kFuGroup; ++r) acc[r] = make_float2(0.f, 0.f);
+    if (hist) {
 #pragma unroll 1
-    for (int g0 = warp * kFuGroup; g0 < kFuBlockRows; g0 += kFuWarps * kFuGroup) {
-        float av[kFuGroup], gv[kFuGroup], uv[kFuGroup], vv[kFuGroup], xbv[kFuGroup];
+        for (int l4 = 0; l4 < R; l4 += 4) {
+            const float2 bp0 = sBk[l4 >> 1][j], bp1 = sBk[(l4 >> 1) + 1][j];
+            const float2 cp0 = sCk[l4 >> 1][j], cp1 = sCk[(l4 >> 1) + 1][j];
 #pragma unroll
-        for (int r = 0; r < kFuGroup; ++r) {
-            const bool act = on && g0 + r < nrows;
-            const int64_t idx = act ? (b0 + g0 + r) * R + j : 0;
-            av[r] = act ? a.A[idx] : 0.0f;
-            xbv[r] = act ? a.Abar[idx] : 0.0f;
-            gv[r] = act ? a.G[idx] : 0.0f;
-            uv[r] = act && step ? a.u[idx] : 0.0f;
-            vv[r] = act && step ? a.v[idx] : 0.0f;
-        }
-#pragma unroll
-        for (int r = 0; r < kFuGroup; ++r) {
-            sD[warp][r][lane] = av[r] - xbv[r];   // zero outside the rank and the block's rows
-            sAb[warp][r][lane] = xbv[r];
-        }
-        __syncwarp();
-        float acc[kFuGroup];
-#pragma unroll
-        for (int r = 0; r < kFuGroup; ++r) acc[r] = 0.0f;
-        if (hist) {
-#pragma unroll 2
-            for (int l4 = 0; l4 < R; l4 += 4) {
-                float bq[4], cq[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    bq[q] = sBk[l4 + q][j];
-                    cq[q] = sCk[l4 + q][j];
-                }
-#pragma unroll
-                for (int r = 0; r < kFuGroup; ++r) {
-                    const float4 d = *reinterpret_cast<const float4*>(&sD[warp][r][l4]);
-                    const float4 x = *reinterpret_cast<const float4*>(&sAb[warp][r][l4]);
-                    acc[r] = fmaf(d.x, bq[0], fmaf(x.x, cq[0], acc[r]));
-                    acc[r] = fmaf(d.y, bq[1], fmaf(x.y, cq[1], acc[r]));
-                    acc[r] = fmaf(d.z, bq[2], fmaf(x.z, cq[2], acc[r]));
-                    acc[r] = fmaf(d.w, bq[3], fmaf(x.w, cq[3], acc[r]));
-                }
+            for (int r = 0; r < kFuGroup; ++r) {
+                const float4 d = *reinterpret_cast<const float4*>(&sD[warp][r][l4]);
+                const float4 x = *reinterpret_cast<const float4*>(&sAb[warp][r][l4]);
+                acc[r] = fma2(make_float2(d.x, d.y), bp0, acc[r]);
+                acc[r] = fma2(make_float2(d.z, d.w), bp1, acc[r]);
+                acc[r] = fma2(make_float2(x.x, x.y), cp0, acc[r]);
+                acc[r] = fma2(make_float2(x.z, x.w), cp1, acc[r]);
             }
         }
+    }
 #pragma unroll
-        for (int r = 0; r < kFuGroup; ++r) {
-            const bool act = on && g0 + r < nrows;
-            float an = 0.0f;
-            if (act) {
-                const int64_t idx = (b0 + g0 + r) * R + j;
-                const float g = gv[r] + lam * av[r] + acc[r];
-                if (!step) {
-                    a.G[idx] = g;
-                } else {
-                    const float u = b1c * uv[r] + c1 * g;
-                    const float v = b2c * vv[r] + c2 * g * g;
-                    an = av[r] - at * u / (sqrtf(v) + eps);
-                    if (an < lower) an = lower;
-                    a.u[idx] = u;
-                    a.v[idx] = v;
-                    a.A[idx] = an;
-                    a.G[idx] = 0.0f;
-                }
-            }
-            if (gram) {
-                sA[g0 + r][lane] = an;
-                sDn[g0 + r][lane] = act ? an - xbv[r] : 0.0f;
+    for (int r = 0; r < kFuGroup; ++r) {
+        const bool act = on && g0 + r < nrows;
+        float an = 0.0f;
+        if (act) {
+            const int o = (g0 + r) * R + j;
+            const float x = sRow[0][warp][r][lane];
+            const float g = sRow[1][warp][r][lane] + lam * x + (acc[r].x + acc[r].y);
+            if (!step) {
+                Gb[o] = g;
+            } else {
+                const float u = b1c * sRow[2][warp][r][lane] + c1 * g;
+                const float v = b2c * sRow[3][warp][r][lane] + c2 * g * g;
+                an = x - at * u / (sqrtf(v) + eps);
+                if (an < lower) an = lower;
+                ub[o] = u;
+                vb[o] = v;
+                Ab[o] = an;
+                Gb[o] = 0.0f;
             }
         }
-        __syncwarp();   // sD / sAb of this warp are reused by its next group
+        if (gram) {
+            sA[g0 + r][lane] = an;
+            sDn[g0 + r][lane] = act ? an - sAb[warp][r][lane] : 0.0f;
+        }
     }
     if (!gram) return;
 
-    // ---- Grams of the block's updated rows: thread = (l, 4 columns), rows in order
+    // ---- Grams of the block's updated rows.  Thread = 4 x 4 tile (l4, m4) of A'A and of D'A over
+    // one half of the rows; pairs (x_l, x_l+1) * (a_m, a_m+1) give the diagonal entries of a 2 x 2
+    // block and (x_l, x_l+1) * (a_m+1, a_m) the off-diagonal ones, two packed FMAs each.
     __syncthreads();
-    const int l = threadIdx.x >> 3, m4 = (threadIdx.x & 7) * 4;
-    if (l < R && m4 < R) {
-        float p[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-        for (int r = 0; r < nrows; ++r) {
-            const float al = sA[r][l], dl = sDn[r][l];
+    const int tq = R >> 2, half = threadIdx.x >> 6, tile = threadIdx.x & 63;
+    const int l4 = (tile / 8) * 4, m4 = (tile % 8) * 4;
+    float2 pd[4], po[4], ed[4], eo[4];   // [2 x 2 block (lb, mb)]: diagonal, off-diagonal
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pd[q] = po[q] = ed[q] = eo[q] = make_float2(0.f, 0.f);
+    const bool tile_on = half < 2 && tile / 8 < tq && tile % 8 < tq;
+    if (tile_on) {
+        const int rb = half * (kFuBlockRows / 2), re = min(nrows, rb + kFuBlockRows / 2);
+#pragma unroll 2
+        for (int r = rb; r < re; ++r) {
+            const float4 al = *reinterpret_cast<const float4*>(&sA[r][l4]);
+            const float4 dl = *reinterpret_cast<const float4*>(&sDn[r][l4]);
             const float4 am = *reinterpret_cast<const float4*>(&sA[r][m4]);
-            p[0] = fmaf(al, am.x, p[0]), p[1] = fmaf(al, am.y, p[1]);
-            p[2] = fmaf(al, am.z, p[2]), p[3] = fmaf(al, am.w, p[3]);
-            e[0] = fmaf(dl, am.x, e[0]), e[1] = fmaf(dl, am.y, e[1]);
-            e[2] = fmaf(dl, am.z, e[2]), e[3] = fmaf(dl, am.w, e[3]);
+            const float2 al0 = make_float2(al.x, al.y), al1 = make_float2(al.z, al.w);
+            const float2 dl0 = make_float2(dl.x, dl.y), dl1 = make_float2(dl.z, dl.w);
+            const float2 am0 = make_float2(am.x, am.y), am1 = make_float2(am.z, am.w);
+            const float2 as0 = make_float2(am.y, am.x), as1 = make_float2(am.w, am.z);
+            pd[0] = fma2(al0, am0, pd[0]), po[0] = fma2(al0, as0, po[0]);
+            pd[1] = fma2(al0, am1, pd[1]), po[1] = fma2(al0, as1, po[1]);
+            pd[2] = fma2(al1, am0, pd[2]), po[2] = fma2(al1, as0, po[2]);
+            pd[3] = fma2(al1, am1, pd[3]), po[3] = fma2(al1, as1, po[3]);
+            ed[0] = fma2(dl0, am0, ed[0]), eo[0] = fma2(dl0, as0, eo[0]);
+            ed[1] = fma2(dl0, am1, ed[1]), eo[1] = fma2(dl0, as1, eo[1]);
+            ed[2] = fma2(dl1, am0, ed[2]), eo[2] = fma2(dl1, as0, eo[2]);
+            ed[3] = fma2(dl1, am1, ed[3]), eo[3] = fma2(dl1, as1, eo[3]);
         }
-        float* P = a.gacc + (int64_t)k * RR + l * R + m4;
-        float* E = a.gacc + ((int64_t)a.ndim + k) * RR + l * R + m4;
-        atomicAdd(reinterpret_cast<float4*>(P), make_float4(p[0], p[1], p[2], p[3]));
-        atomicAdd(reinterpret_cast<float4*>(E), make_float4(e[0], e[1], e[2], e[3]));
+    }
+    // the two halves meet in shared memory (sD / sAb are free), then one float4 atomic per row
+    float* hs = &sD[0][0][0];   // [64 tiles][32]: the second half's tile values
+    if (tile_on && half == 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            reinterpret_cast<float2*>(hs + tile * 32)[q] = pd[q];
+            reinterpret_cast<float2*>(hs + tile * 32)[4 + q] = po[q];
+            reinterpret_cast<float2*>(hs + tile * 32)[8 + q] = ed[q];
+            reinterpret_cast<float2*>(hs + tile * 32)[12 + q] = eo[q];
+        }
+    __syncthreads();
+    if (tile_on && half == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 a0 = reinterpret_cast<const float2*>(hs + tile * 32)[q];
+            const float2 a1 = reinterpret_cast<const float2*>(hs + tile * 32)[4 + q];
+            const float2 a2 = reinterpret_cast<const float2*>(hs + tile * 32)[8 + q];
+            const float2 a3 = reinterpret_cast<const float2*>(hs + tile * 32)[12 + q];
+            pd[q].x += a0.x, pd[q].y += a0.y, po[q].x += a1.x, po[q].y += a1.y;
+            ed[q].x += a2.x, ed[q].y += a2.y, eo[q].x += a3.x, eo[q].y += a3.y;
+        }
+        // block (lb, mb) = q: rows l4 + 2 lb + {0, 1}, columns m4 + 2 mb + {0, 1}
+        float P4[4][4], E4[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int lb = q >> 1, mb = q & 1;
+            P4[2 * lb][2 * mb] = pd[q].x, P4[2 * lb + 1][2 * mb + 1] = pd[q].y;
+            P4[2 * lb][2 * mb + 1] = po[q].x, P4[2 * lb + 1][2 * mb] = po[q].y;
+            E4[2 * lb][2 * mb] = ed[q].x, E4[2 * lb + 1][2 * mb + 1] = ed[q].y;
+            E4[2 * lb][2 * mb + 1] = eo[q].x, E4[2 * lb + 1][2 * mb] = eo[q].y;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            float* P = a.gacc + (int64_t)k * RR + (l4 + x) * R + m4;
+            float* E = a.gacc + ((int64_t)a.ndim + k) * RR + (l4 + x) * R + m4;
+            atomicAdd(reinterpret_cast<float4*>(P), make_float4(P4[x][0], P4[x][1], P4[x][2], P4[x][3]));
+            atomicAdd(reinterpret_cast<float4*>(E), make_float4(E4[x][0], E4[x][1], E4[x][2], E4[x][3]));
+        }
     }
     if (last_block_ticket(a.tk)) {   // every block's sums are in: B_k, C_k of the updated factors
         const bool hon = *a.hist_len > 0;
@@ -473,7 +543,7 @@ static bool factor_update_chunked(const FactorUpdateArgs<T>& a, cudaStream_t st,
             blocks += fu_blocks_of_mode(a, k, &beg, &end);
         }
         if (blocks < 1 || blocks > 0x7fffffff) return false;
-        const size_t smem = a.gacc ? 2 * kFuBlockRows * 32 * sizeof(float) : 0;
+        const size_t smem = (a.gacc ? 6 : 4) * kFuBlockRows * 32 * sizeof(float);
         cudaFuncSetAttribute(k_factor_update_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_factor_update_rows<<<(int)blocks, 32 * kFuWarps, smem, st>>>(a);
         *err = cudaGetLastError();
