@@ -354,30 +354,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
     };
+    // MMA issue: descriptors formed once per call and stepped by adds (a descriptor's address field
+    // counts 16-byte units), loops unrolled, so the issuing thread spends a few instructions per MMA
     auto issue_gemm1 = [&](int dbuf, int kbuf) {
         if (tid == 0) {
-            const uint32_t krh = smem_u32(KRh[kbuf]), krl = smem_u32(KRl), a3h = smem_u32(A3hi), a3l = smem_u32(A3lo);
-            const uint32_t Aop[3] = {krh, krh, krl}, Bop[3] = {a3h, a3l, a3h};
+            const uint64_t ahd = make_desc(smem_u32(KRh[kbuf]), 128, sboR), ald = make_desc(smem_u32(KRl), 128, sboR);
+            const uint64_t bh = make_desc(smem_u32(A3hi), 128, sboR), bl = make_desc(smem_u32(A3lo), 128, sboR);
             const uint32_t d = tmem + (uint32_t)dbuf * 128;
-            for (int sp = 0; sp < 3; ++sp)
-                for (int kk = 0; kk < R / 16; ++kk)
-                    mma(d, make_desc(Aop[sp] + kk * 256, 128, sboR), make_desc(Bop[sp] + kk * 256, 128, sboR), id_m,
-                        (sp > 0 || kk > 0) ? 1u : 0u);
+            const int nk = R >> 4;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                if (kk < nk) mma(d, ahd + 16 * kk, bh + 16 * kk, id_m, kk > 0 ? 1u : 0u);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                if (kk < nk) mma(d, ahd + 16 * kk, bl + 16 * kk, id_m, 1u);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                if (kk < nk) mma(d, ald + 16 * kk, bh + 16 * kk, id_m, 1u);
             commit(&mbar1);
         }
     };
     auto issue_gemm23 = [&](int kbuf, bool g3acc) {
         if (tid == 0) {
-            const uint32_t yr = smem_u32(Yr);
-            const uint32_t a3mt = smem_u32(BF16 ? (const void*)A3hi : (const void*)A316);
-            const uint32_t krmt = smem_u32(BF16 ? (const void*)KRh[kbuf] : (const void*)KR3[kbuf]);
-            for (int kk = 0; kk < kCols / 16; ++kk)    // K = i3
-                mma(tT, make_desc(yr + kk * 256, 128, 2048), make_desc(a3mt + kk * 2 * sboR, sboR, 128), id_2,
-                    kk > 0 ? 1u : 0u);
-            if (wantG)
-                for (int kk = 0; kk < kRows / 16; ++kk)   // K = rows
-                    mma(tG3, make_desc(yr + kk * 4096, 2048, 128), make_desc(krmt + kk * 2 * sboR, sboR, 128), id_3,
-                        (g3acc || kk > 0) ? 1u : 0u);
+            const uint64_t at = make_desc(smem_u32(Yr), 128, 2048);
+            const uint64_t bt = make_desc(smem_u32(BF16 ? (const void*)A3hi : (const void*)A316), sboR, 128);
+            const uint64_t ag = make_desc(smem_u32(Yr), 2048, 128);
+            const uint64_t bg = make_desc(smem_u32(BF16 ? (const void*)KRh[kbuf] : (const void*)KR3[kbuf]), sboR, 128);
+            const uint64_t stp = (uint64_t)(2 * sboR) >> 4;
+#pragma unroll
+            for (int kk = 0; kk < kCols / 16; ++kk)
+                mma(tT, at + 16 * kk, bt + stp * kk, id_2, kk > 0 ? 1u : 0u);
+            if (wantG) {
+#pragma unroll
+                for (int kk = 0; kk < kRows / 16; ++kk)
+                    mma(tG3, ag + 256 * kk, bg + stp * kk, id_3, (g3acc || kk > 0) ? 1u : 0u);
+            }
             commit(&mbar2);
         }
     };
