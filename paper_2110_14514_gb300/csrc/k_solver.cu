@@ -474,23 +474,23 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
         }
     }
     // the two halves meet in shared memory (sD / sAb are free), then one float4 atomic per row
-    float* hs = &sD[0][0][0];   // [64 tiles][32]: the second half's tile values
-    if (tile_on && half == 1)
+    float2* hs = reinterpret_cast<float2*>(&sD[0][0][0]);   // [16 values][64 tiles]: the second half's
+    if (tile_on && half == 1)                               // tiles, consecutive tiles in consecutive words
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            reinterpret_cast<float2*>(hs + tile * 32)[q] = pd[q];
-            reinterpret_cast<float2*>(hs + tile * 32)[4 + q] = po[q];
-            reinterpret_cast<float2*>(hs + tile * 32)[8 + q] = ed[q];
-            reinterpret_cast<float2*>(hs + tile * 32)[12 + q] = eo[q];
+            hs[q * 64 + tile] = pd[q];
+            hs[(4 + q) * 64 + tile] = po[q];
+            hs[(8 + q) * 64 + tile] = ed[q];
+            hs[(12 + q) * 64 + tile] = eo[q];
         }
     __syncthreads();
     if (tile_on && half == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float2 a0 = reinterpret_cast<const float2*>(hs + tile * 32)[q];
-            const float2 a1 = reinterpret_cast<const float2*>(hs + tile * 32)[4 + q];
-            const float2 a2 = reinterpret_cast<const float2*>(hs + tile * 32)[8 + q];
-            const float2 a3 = reinterpret_cast<const float2*>(hs + tile * 32)[12 + q];
+            const float2 a0 = hs[q * 64 + tile];
+            const float2 a1 = hs[(4 + q) * 64 + tile];
+            const float2 a2 = hs[(8 + q) * 64 + tile];
+            const float2 a3 = hs[(12 + q) * 64 + tile];
             pd[q].x += a0.x, pd[q].y += a0.y, po[q].x += a1.x, po[q].y += a1.y;
             ed[q].x += a2.x, ed[q].y += a2.y, eo[q].x += a3.x, eo[q].y += a3.y;
         }
