@@ -317,7 +317,9 @@ def run_native_dense(args, cfg, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = {"fp32": sg.PREC_F32, "bf16": sg.PREC_BF16_MTTKRP, "fp16": sg.PREC_F16_MTTKRP}[args.precision]
-    p = sg.params(cfg["dims"], cfg["rank"], cfg["loss"], precision=prec, seed=2000 + rank, **DENSE_SOLVER)
+    lsq_lbfgs = args.solver == "lsq_lbfgs"
+    extra = dict(temporal=sg.TEMPORAL_LSQ, optimizer=sg.OPT_LBFGS) if lsq_lbfgs else {}
+    p = sg.params(cfg["dims"], cfg["rank"], cfg["loss"], precision=prec, seed=2000 + rank, **DENSE_SOLVER, **extra)
     A0 = [torch.from_numpy(a).to(dev) for a in S.init_factors(cfg, stream=rank)]
     n_sl = 2
     host = [S.dense_slice(cfg, t + 1, stream=rank)[0] for t in range(n_sl)]
@@ -348,6 +350,8 @@ def run_native_dense(args, cfg, world, rank, local):
     launches = ctx.stats()["kernels_launched"] - k0
     total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     value = world * args.steps * grads_per_step * omega / total_s
+    if lsq_lbfgs:   # host-driven L-BFGS: gradient evaluations per step vary; report slice updates / s
+        value = world * args.steps / total_s
     # dominant kernel: one factor gradient over the slice, back to back behind a sleep kernel
     A, _, _ = ctx.factors()
     s0 = torch.full((cfg["rank"],), 1.0, device=dev)
@@ -390,19 +394,163 @@ def run_native_dense(args, cfg, world, rank, local):
                 "tensor_tflops": flops_alg / kern_s / 1e12,
                 "tensor_frac_of_bf16_peak": flops_alg / kern_s / 1e12 / tflops_peak}
     return {
-        "metric": "dense GCP gradient entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
+        "metric": "slice updates/s" if lsq_lbfgs else "dense GCP gradient entries/s", "value": value,
+        "unit": "slices/s" if lsq_lbfgs else "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16 MTTKRP / split-bf16 model, f32 accumulate",
                   "fp16": "f16 MTTKRP / split-bf16 model, f32 accumulate"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"dense_gaussian_3way: 256^3 slices, R=64, gaussian, noise 1% RMS",
-                   "grads_per_step": grads_per_step, "solver": DENSE_SOLVER,
+                   "grads_per_step": None if lsq_lbfgs else grads_per_step,
+                   "solver": "LSQ temporal solve + projected L-BFGS factor solve (defaults)" if lsq_lbfgs else DENSE_SOLVER,
                    "l2": "flushed between steps (256 MB write)", "precision": args.precision},
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,
     }
+
+
+# ----------------------------------------------------------------------------- autograd form
+def run_native_autograd(args, cfg, world, rank, local):
+    """100^3, R = 16 Poisson slices (the autograd configuration): one step is the GCP loss forward
+    and its hand-written backward through torch.autograd (GCPLoss; m recomputed in the backward
+    launch), set beside the same loss and gradients from one fused FP32 call, with both compared
+    to the FP64 oracle gradient of the first slice."""
+    import torch
+    import paper_2110_14514_gb300 as sg
+    from paper_2110_14514_gb300.autograd import gcp_loss
+    from oracle import gcp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    R = cfg["rank"]
+    p = sg.params(cfg["dims"], R, cfg["loss"], precision=sg.PREC_F32, seed=3000 + rank)
+    A0 = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev) for a in S.init_factors(cfg, stream=rank)]
+    n_sl = 2
+    host = [np.ascontiguousarray(S.dense_slice(cfg, t + 1, stream=rank)[0], np.float32) for t in range(n_sl)]
+    dsl = [torch.from_numpy(x).to(dev) for x in host]
+    pinned = [torch.from_numpy(x).pin_memory() for x in host]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = sg.Context(p, A0)
+    A = [a.clone().requires_grad_(True) for a in A0]
+    s = torch.full((R,), 0.5, dtype=torch.float32, device=dev, requires_grad=True)
+    omega = int(np.prod(cfg["dims"]))
+
+    def ag_step(X):
+        for t in A + [s]:
+            t.grad = None
+        loss = gcp_loss(ctx, s, A, X=X)
+        loss.backward()
+        return loss
+
+    def timed(fn, nsteps, off):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        torch.cuda.synchronize()
+        for k in range(nsteps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            fn((off + k) % n_sl)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    for w in range(args.warmup):
+        ag_step(dsl[w % n_sl])
+    torch.cuda.synchronize()
+    k0 = ctx.stats()["kernels_launched"]
+    clocks = Clocks(local)
+    clocks.start()
+    total_s = timed(lambda i: ag_step(dsl[i]), args.steps, args.warmup)
+    clk = clocks.stop()
+    launches = ctx.stats()["kernels_launched"] - k0
+    value = world * args.steps * omega / total_s
+    # the same loss and gradients from one fused call per step
+    sd, Ad = s.detach(), [a.detach() for a in A]
+    plain_s = timed(lambda i: ctx.gradient(sd, Ad, X=dsl[i]), args.steps, 0)
+    # end to end: the slice copied from pinned host memory each step, the loss read back
+    def e2e(i):
+        X = pinned[i].to(dev, non_blocking=True)
+        return ag_step(X).item()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(args.steps):
+        e2e(k % n_sl)
+    t1.record()
+    torch.cuda.synchronize()
+    e2e_s = t0.elapsed_time(t1) / 1e3
+    # accuracy at the current point against the FP64 oracle (first slice)
+    ag_step(dsl[0])
+    G_ag = [a.grad.double().cpu().numpy() for a in A]
+    gs_ag = s.grad.double().cpu().numpy()
+    Gp, gsp, _ = ctx.gradient(sd, Ad, X=dsl[0])
+    Go, gso, _ = gcp.dense_gradient(host[0].astype(np.float64), sd.double().cpu().numpy(),
+                                    [a.double().cpu().numpy() for a in Ad], cfg["loss"])
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    acc = {"autograd_vs_oracle": max([rel(G_ag[k], Go[k]) for k in range(3)] + [rel(gs_ag, gso)]),
+           "plain_vs_oracle": max([rel(Gp[k].double().cpu().numpy(), Go[k]) for k in range(3)] +
+                                  [rel(gsp.double().cpu().numpy(), gso)])}
+    # the kernels alone: the two launches of an autograd step (loss pass, then the factor and
+    # temporal gradients) back to back behind a sleep kernel, outputs preallocated (the 4 MB
+    # slice stays in L2 across these launches)
+    G = [torch.zeros_like(a) for a in Ad]
+    gs = torch.zeros(R, dtype=torch.float32, device=dev)
+    f = torch.zeros(1, dtype=torch.float64, device=dev)
+    nrep = 100
+    torch.cuda.synchronize()
+    with torch.cuda.stream(ctx.stream):
+        ctx.gradient(sd, Ad, X=dsl[0], want=sg.WANT_LOSS, f=f, accumulate=True)
+        torch.cuda._sleep(20_000_000)
+        k_e0, k_e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k_e0.record(ctx.stream)
+        for r in range(nrep):
+            ctx.gradient(sd, Ad, X=dsl[r % n_sl], want=sg.WANT_LOSS, f=f, accumulate=True)
+            ctx.gradient(sd, Ad, X=dsl[r % n_sl], want=sg.WANT_FACTORS | sg.WANT_TEMPORAL, G=G, gs=gs,
+                         accumulate=True)
+        k_e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    kern_s = k_e0.elapsed_time(k_e1) / 1e3 / nrep
+    ctx.close()
+    sm_clock = clk.get("sm_max_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_clock * 1e6 / 1e12
+    flops = 8 * R * omega           # forward model (2R) + backward model, T and G3 (6R) per entry
+    achieved = flops / kern_s / 1e12
+    out = {
+        "metric": "GCP loss forward + backward entries/s", "value": value, "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "dense_poisson_3way: 100^3 slices, R=16, poisson, autograd forward + backward",
+                   "bound_by": "host: torch.autograd and the two library calls per step take longer than the kernels",
+                   "l2": "flushed between steps (256 MB write)", "plain_fused_ms_per_step": 1e3 * plain_s / args.steps,
+                   "accuracy_rel_max": acc},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_kind": f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 flop x {sm_clock:.0f} MHz",
+                     "kernel_us": kern_s * 1e6,
+                     "note": "the loss and gradient launches of one step, back to back: 8R flops per entry"},
+        "e2e": {"value": world * args.steps * omega / e2e_s, "unit": "entries/s",
+                "h2d_bytes_per_step": 4 * omega, "d2h_bytes_per_step": 8},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        Xh = host[0].astype(np.float64)
+        Ah = [a.double().cpu().numpy() for a in A0]
+        sh = np.full(R, 0.5)
+        t0c = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0c < 10.0:
+            gcp.dense_gradient(Xh, sh, Ah, cfg["loss"])
+            n += 1
+        dt = time.perf_counter() - t0c
+        out["cpu_baseline"] = {"value": n * omega / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{n} FP64 oracle dense gradients (loss + all gradients) of one 100^3 slice"}
+    return out
 
 
 # ----------------------------------------------------------------------------- batched streams
@@ -552,8 +700,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "dense_gaussian_3way", "batched_streams"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "dense_gaussian_3way", "dense_poisson_3way", "batched_streams"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--solver", default="adam", choices=["adam", "lsq_lbfgs"],
+                    help="dense workload: ADAM solvers (Alg. 3 / 4) or the LSQ + L-BFGS options")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     cfg = S.workload(args.workload)
@@ -561,6 +712,8 @@ def main():
         out = run_reference(args, S.workload(WORKLOAD), world, rank)
     elif args.workload == "batched_streams":
         out = run_native_batched(args, cfg, world, rank, local)
+    elif args.workload == "dense_poisson_3way":
+        out = run_native_autograd(args, cfg, world, rank, local)
     elif args.workload != WORKLOAD:
         out = run_native_dense(args, cfg, world, rank, local)
     else:
