@@ -50,7 +50,7 @@ struct sgcp_ctx {
     int64_t gram_rpb = 256;
     cudaStream_t side = nullptr; // second capture stream: Gram work runs beside the gradient kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    float* gacc = nullptr;       // [2][ndim][R][R] Gram sums of the factor update (FP32, R <= 32, H > 0)
+    float* gacc = nullptr;       // 2 x [2][ndim][R][R] Gram sums of the factor updates (FP32, R <= 32, H > 0)
     void* Bc = nullptr;          // [ndim][R][R], element type T
     void* Cc = nullptr;
     double* lsq_work = nullptr;  // R*R + R
@@ -551,21 +551,30 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     fu.eps = P.adam_eps;
     fu.lower = c->lower;
     fu.skip = skip;
-    // With gacc the update also forms B_k, C_k of the factors it writes, so the Gram chain beside
-    // the gradient runs only for an epoch's first iteration (whose A may have been rolled back).
+    // With gacc each update also sums the Grams of the factors it writes (two alternating buffers)
+    // and the next update forms its B_k, C_k from them, so the Gram / history-coefficient chain
+    // beside the gradient runs only for an epoch's first iteration (whose A may have been rolled
+    // back).  Both buffers are zero at every epoch start: the update of iteration it accumulates
+    // into buffer it % 2 (except the epoch's last update, whose sums no update would read) and
+    // clears the buffer it read.
     const bool fused = hist_possible && c->gacc != nullptr;
+    const size_t gsz = 2 * (size_t)d * R * R;
     if (fused) {
-        fu.gacc = c->gacc;
         fu.SH = c->SH;
-        fu.Bn = (T*)c->Bc;
-        fu.Cn = (T*)c->Cc;
         fu.tk = sf;
+        CK(cudaMemsetAsync(c->gacc, 0, 2 * gsz * sizeof(float), c->stream), "clear Gram sums");
     }
     for (int e = 0; e < P.kappa_f; ++e) {
         CK(launch_epoch_begin(sf, P.tol_f, c->rates_f, P.tau_f, P.beta1, P.beta2, c->stream, &c->launches),
            "epoch begin");
         for (int it = 0; it < P.tau_f; ++it) {
             fu.rate = c->rates_f + it;
+            if (fused) {
+                float* prev = c->gacc + gsz * ((it + 1) & 1);   // written by the update of it - 1
+                fu.gprev = it > 0 ? prev : nullptr;
+                fu.gzero = it > 0 ? prev : nullptr;
+                fu.gacc = it + 1 < P.tau_f ? c->gacc + gsz * (it & 1) : nullptr;
+            }
             const bool chain = hist_possible && (!fused || it == 0);
             if (chain) CK(fork(), "fork");
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
@@ -1007,7 +1016,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         (st = dalloc(c, &c->gpart, (size_t)6 * c->ndim * c->gram_nblk * RR * c->esz)) ||
         (st = dalloc(c, &c->Bc, c->ndim * RR * c->esz)) || (st = dalloc(c, &c->Cc, c->ndim * RR * c->esz)) ||
         (c->esz == 4 && c->R <= 32 && P.H > 0 &&
-         (st = dalloc_t(c, &c->gacc, 2 * (size_t)c->ndim * RR * sizeof(float)))) ||
+         (st = dalloc_t(c, &c->gacc, 4 * (size_t)c->ndim * RR * sizeof(float)))) ||
         (st = dalloc_t(c, &c->lsq_work, (RR + c->R) * sizeof(double))) ||
         (st = dalloc_t(c, &c->st_w, sizeof(SolverState))) || (st = dalloc_t(c, &c->st_f, sizeof(SolverState))) ||
         (st = dalloc_t(c, &c->rates_w, (P.tau_w > 0 ? P.tau_w : 1) * sizeof(double))) ||
@@ -1041,7 +1050,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->st_w, &st0, sizeof(SolverState), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->st_f, &st0, sizeof(SolverState), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
-    if (e == cudaSuccess && c->gacc) e = cudaMemsetAsync(c->gacc, 0, 2 * (size_t)c->ndim * RR * sizeof(float), s);
+    if (e == cudaSuccess && c->gacc) e = cudaMemsetAsync(c->gacc, 0, 4 * (size_t)c->ndim * RR * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->Bc, 0, c->ndim * RR * c->esz, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->Cc, 0, c->ndim * RR * c->esz, s);
     std::vector<int64_t> hv(Hs, 0);

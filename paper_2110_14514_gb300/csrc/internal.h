@@ -146,14 +146,16 @@ struct FactorUpdateArgs {
     const double* rate;       // bias-corrected learning rate of this iteration (see k_epoch_begin)
     const int32_t* skip;
     int grad_only;            // 1: store the full gradient g in G and leave A, u, v untouched
-    // Optional (FP32, R <= 32): Grams of the updated rows for the next iteration's history terms.
-    // gacc [2][ndim][R][R] (A'A, D'A; zero on entry, left zero), SH [R][R]; the last block writes
-    // Bn / Cn (may be B / C: every block has read them before the last block starts).
+    // Optional (FP32, R <= 32), buffers of [2][ndim][R][R] floats (A'A, D'A):
+    //   gprev: Gram sums of the factors this update starts from (written by the previous update);
+    //          when set, B_k and C_k are formed from them and SH instead of read from B, C;
+    //   gacc:  zero on entry; receives the Grams of the rows this update writes;
+    //   gzero: cleared by the last block (ticket tk) once every block has read gprev.
+    const float* gprev;
     float* gacc;
+    float* gzero;
     const double* SH;
-    T* Bn;
-    T* Cn;
-    SolverState* tk;          // ticket that elects the last block
+    SolverState* tk;
 };
 
 template <typename T>

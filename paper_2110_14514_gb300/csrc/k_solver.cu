@@ -292,12 +292,12 @@ static int solver_num_sms() {
 // FP32, R <= 32, history terms possible.  A block owns up to kFuBlockRows rows of one mode and
 // stages B_k and C_k in shared memory; each warp updates 8 rows at once with lane j on column j:
 // the rows' d = a - abar and abar are staged per warp and read as 16-byte broadcasts, B_k[l][j]
-// and C_k[l][j] as conflict-free words, so one coefficient load serves 8 rows.  Every load of
-// the 8 rows is issued before the first store.  With gacc set the block also keeps its updated
-// rows and their d in shared memory and sums the Grams A'A and D'A over them (thread = one l and
-// 4 columns); the block sums are added into gacc with 16-byte float atomics (GB300's FP64
-// atomics are far slower) and the last block turns them into the next iteration's B_k, C_k
-// (the coefficients k_hist_coeffs forms from k_gram's sums).
+// and C_k[l][j] as conflict-free pairs, two-wide FMAs.  Every global request of the block is
+// issued before the first use.  With gacc set the block also keeps its updated rows and their d
+// in shared memory and sums its share of the Grams A'A and D'A (4 x 4 register tiles), added
+// into gacc with 16-byte float atomics (GB300's FP64 atomics are far slower); the next update
+// (gprev) forms B_k, C_k for its own mode from those sums at its start instead of reading them,
+// and its last block clears the buffer, so no kernel between two updates touches the Grams.
 constexpr int kFuBlockRows = 64;
 constexpr int kFuGroup = kFuBlockRows / 8;   // rows a warp updates (all at once)
 constexpr int kFuWarps = 8;
@@ -347,13 +347,24 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     const int32_t skipv = a.skip ? *a.skip : 0;
     const int32_t hlen = a.B != nullptr ? *a.hist_len : 0;
     const double rate = *a.rate;
-    float bco[4], cco[4];   // B_k, C_k entries i = tid + 256 q of the padded 32 x 32 tiles
+    // B_k, C_k entries i = tid + 256 q of the padded 32 x 32 tiles: read (an epoch's first update),
+    // or formed here from the previous update's Gram sums (P_n = A'A, E_n = D'A of every mode)
+    float bco[4], cco[4];
+    float gp[4][4], ge[4][4], gsh[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = threadIdx.x + 256 * q, l = i >> 5, m = i & 31;
         const bool in = a.B != nullptr && l < R && m < R;
-        bco[q] = in ? __ldg(a.B + (int64_t)k * RR + l * R + m) : 0.0f;
-        cco[q] = in ? __ldg(a.C + (int64_t)k * RR + l * R + m) : 0.0f;
+        const int e = l * R + m;
+        bco[q] = in && !a.gprev ? __ldg(a.B + (int64_t)k * RR + e) : 0.0f;
+        cco[q] = in && !a.gprev ? __ldg(a.C + (int64_t)k * RR + e) : 0.0f;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const bool ld = in && a.gprev && n < a.ndim;
+            gp[q][n] = ld ? __ldcg(a.gprev + (int64_t)n * RR + e) : 0.0f;
+            ge[q][n] = ld ? __ldcg(a.gprev + ((int64_t)a.ndim + n) * RR + e) : 0.0f;
+        }
+        gsh[q] = in && a.gprev ? (float)__ldcg(a.SH + e) : 0.0f;
     }
     // the block's rows through 32-bit offsets from its first row
     float* Ab = a.A + b0 * R;
@@ -375,6 +386,26 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     }
     if (skipv) return;   // the solver has finished: nothing is written
     const bool hist = hlen > 0;
+    if (a.gprev) {   // B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H, telescoped as in hist_coeff_elem
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float gam = 1.0f, dgam = 0.0f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (m == k || m >= a.ndim) continue;
+                gam *= gp[q][m];
+                float term = ge[q][m];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {
+                    if (n == k || n == m || n >= a.ndim) continue;
+                    term *= (n < m) ? (gp[q][n] - ge[q][n]) : gp[q][n];
+                }
+                dgam += term;
+            }
+            bco[q] = gam * gsh[q];
+            cco[q] = dgam * gsh[q];
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = threadIdx.x + 256 * q, l = i >> 5, m = i & 31;
@@ -440,92 +471,81 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
             sDn[g0 + r][lane] = act ? an - sAb[warp][r][lane] : 0.0f;
         }
     }
-    if (!gram) return;
+    if (gram) {
 
-    // ---- Grams of the block's updated rows.  Thread = 4 x 4 tile (l4, m4) of A'A and of D'A over
-    // one half of the rows; pairs (x_l, x_l+1) * (a_m, a_m+1) give the diagonal entries of a 2 x 2
-    // block and (x_l, x_l+1) * (a_m+1, a_m) the off-diagonal ones, two packed FMAs each.
-    __syncthreads();
-    const int tq = R >> 2, half = threadIdx.x >> 6, tile = threadIdx.x & 63;
-    const int l4 = (tile / 8) * 4, m4 = (tile % 8) * 4;
-    float2 pd[4], po[4], ed[4], eo[4];   // [2 x 2 block (lb, mb)]: diagonal, off-diagonal
-#pragma unroll
-    for (int q = 0; q < 4; ++q) pd[q] = po[q] = ed[q] = eo[q] = make_float2(0.f, 0.f);
-    const bool tile_on = half < 2 && tile / 8 < tq && tile % 8 < tq;
-    if (tile_on) {
-        const int rb = half * (kFuBlockRows / 2), re = min(nrows, rb + kFuBlockRows / 2);
-#pragma unroll 2
-        for (int r = rb; r < re; ++r) {
-            const float4 al = *reinterpret_cast<const float4*>(&sA[r][l4]);
-            const float4 dl = *reinterpret_cast<const float4*>(&sDn[r][l4]);
-            const float4 am = *reinterpret_cast<const float4*>(&sA[r][m4]);
-            const float2 al0 = make_float2(al.x, al.y), al1 = make_float2(al.z, al.w);
-            const float2 dl0 = make_float2(dl.x, dl.y), dl1 = make_float2(dl.z, dl.w);
-            const float2 am0 = make_float2(am.x, am.y), am1 = make_float2(am.z, am.w);
-            const float2 as0 = make_float2(am.y, am.x), as1 = make_float2(am.w, am.z);
-            pd[0] = fma2(al0, am0, pd[0]), po[0] = fma2(al0, as0, po[0]);
-            pd[1] = fma2(al0, am1, pd[1]), po[1] = fma2(al0, as1, po[1]);
-            pd[2] = fma2(al1, am0, pd[2]), po[2] = fma2(al1, as0, po[2]);
-            pd[3] = fma2(al1, am1, pd[3]), po[3] = fma2(al1, as1, po[3]);
-            ed[0] = fma2(dl0, am0, ed[0]), eo[0] = fma2(dl0, as0, eo[0]);
-            ed[1] = fma2(dl0, am1, ed[1]), eo[1] = fma2(dl0, as1, eo[1]);
-            ed[2] = fma2(dl1, am0, ed[2]), eo[2] = fma2(dl1, as0, eo[2]);
-            ed[3] = fma2(dl1, am1, ed[3]), eo[3] = fma2(dl1, as1, eo[3]);
-        }
-    }
-    // the two halves meet in shared memory (sD / sAb are free), then one float4 atomic per row
-    float2* hs = reinterpret_cast<float2*>(&sD[0][0][0]);   // [16 values][64 tiles]: the second half's
-    if (tile_on && half == 1)                               // tiles, consecutive tiles in consecutive words
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            hs[q * 64 + tile] = pd[q];
-            hs[(4 + q) * 64 + tile] = po[q];
-            hs[(8 + q) * 64 + tile] = ed[q];
-            hs[(12 + q) * 64 + tile] = eo[q];
-        }
-    __syncthreads();
-    if (tile_on && half == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 a0 = hs[q * 64 + tile];
-            const float2 a1 = hs[(4 + q) * 64 + tile];
-            const float2 a2 = hs[(8 + q) * 64 + tile];
-            const float2 a3 = hs[(12 + q) * 64 + tile];
-            pd[q].x += a0.x, pd[q].y += a0.y, po[q].x += a1.x, po[q].y += a1.y;
-            ed[q].x += a2.x, ed[q].y += a2.y, eo[q].x += a3.x, eo[q].y += a3.y;
-        }
-        // block (lb, mb) = q: rows l4 + 2 lb + {0, 1}, columns m4 + 2 mb + {0, 1}
-        float P4[4][4], E4[4][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int lb = q >> 1, mb = q & 1;
-            P4[2 * lb][2 * mb] = pd[q].x, P4[2 * lb + 1][2 * mb + 1] = pd[q].y;
-            P4[2 * lb][2 * mb + 1] = po[q].x, P4[2 * lb + 1][2 * mb] = po[q].y;
-            E4[2 * lb][2 * mb] = ed[q].x, E4[2 * lb + 1][2 * mb + 1] = ed[q].y;
-            E4[2 * lb][2 * mb + 1] = eo[q].x, E4[2 * lb + 1][2 * mb] = eo[q].y;
-        }
-#pragma unroll
-        for (int x = 0; x < 4; ++x) {
-            float* P = a.gacc + (int64_t)k * RR + (l4 + x) * R + m4;
-            float* E = a.gacc + ((int64_t)a.ndim + k) * RR + (l4 + x) * R + m4;
-            atomicAdd(reinterpret_cast<float4*>(P), make_float4(P4[x][0], P4[x][1], P4[x][2], P4[x][3]));
-            atomicAdd(reinterpret_cast<float4*>(E), make_float4(E4[x][0], E4[x][1], E4[x][2], E4[x][3]));
-        }
-    }
-    if (last_block_ticket(a.tk)) {   // every block's sums are in: B_k, C_k of the updated factors
-        const bool hon = *a.hist_len > 0;
-        const float* P = a.gacc;
-        const float* E = a.gacc + (int64_t)a.ndim * RR;
-        const int idx[4] = {(int)threadIdx.x, (int)threadIdx.x + 256, (int)threadIdx.x + 512, (int)threadIdx.x + 768};
-        if (a.ndim == 3) hist_coeff_batch<3, 4>(RR, P, E, a.SH, idx, hon, a.Bn, a.Cn);   // RR <= 1024
-        else if (a.ndim == 2) hist_coeff_batch<2, 4>(RR, P, E, a.SH, idx, hon, a.Bn, a.Cn);
-        else {
-            const int i0[2] = {idx[0], idx[1]}, i1[2] = {idx[2], idx[3]};
-            hist_coeff_batch<4, 2>(RR, P, E, a.SH, i0, hon, a.Bn, a.Cn);
-            hist_coeff_batch<4, 2>(RR, P, E, a.SH, i1, hon, a.Bn, a.Cn);
-        }
+        // ---- Grams of the block's updated rows.  Thread = 4 x 4 tile (l4, m4) of A'A and of D'A over
+        // one half of the rows; pairs (x_l, x_l+1) * (a_m, a_m+1) give the diagonal entries of a 2 x 2
+        // block and (x_l, x_l+1) * (a_m+1, a_m) the off-diagonal ones, two packed FMAs each.
         __syncthreads();
-        for (int i = threadIdx.x; i < 2 * a.ndim * RR; i += blockDim.x) a.gacc[i] = 0.0f;
+        const int tq = R >> 2, half = threadIdx.x >> 6, tile = threadIdx.x & 63;
+        const int l4 = (tile / 8) * 4, m4 = (tile % 8) * 4;
+        float2 pd[4], po[4], ed[4], eo[4];   // [2 x 2 block (lb, mb)]: diagonal, off-diagonal
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pd[q] = po[q] = ed[q] = eo[q] = make_float2(0.f, 0.f);
+        const bool tile_on = half < 2 && tile / 8 < tq && tile % 8 < tq;
+        if (tile_on) {
+            const int rb = half * (kFuBlockRows / 2), re = min(nrows, rb + kFuBlockRows / 2);
+#pragma unroll 2
+            for (int r = rb; r < re; ++r) {
+                const float4 al = *reinterpret_cast<const float4*>(&sA[r][l4]);
+                const float4 dl = *reinterpret_cast<const float4*>(&sDn[r][l4]);
+                const float4 am = *reinterpret_cast<const float4*>(&sA[r][m4]);
+                const float2 al0 = make_float2(al.x, al.y), al1 = make_float2(al.z, al.w);
+                const float2 dl0 = make_float2(dl.x, dl.y), dl1 = make_float2(dl.z, dl.w);
+                const float2 am0 = make_float2(am.x, am.y), am1 = make_float2(am.z, am.w);
+                const float2 as0 = make_float2(am.y, am.x), as1 = make_float2(am.w, am.z);
+                pd[0] = fma2(al0, am0, pd[0]), po[0] = fma2(al0, as0, po[0]);
+                pd[1] = fma2(al0, am1, pd[1]), po[1] = fma2(al0, as1, po[1]);
+                pd[2] = fma2(al1, am0, pd[2]), po[2] = fma2(al1, as0, po[2]);
+                pd[3] = fma2(al1, am1, pd[3]), po[3] = fma2(al1, as1, po[3]);
+                ed[0] = fma2(dl0, am0, ed[0]), eo[0] = fma2(dl0, as0, eo[0]);
+                ed[1] = fma2(dl0, am1, ed[1]), eo[1] = fma2(dl0, as1, eo[1]);
+                ed[2] = fma2(dl1, am0, ed[2]), eo[2] = fma2(dl1, as0, eo[2]);
+                ed[3] = fma2(dl1, am1, ed[3]), eo[3] = fma2(dl1, as1, eo[3]);
+            }
+        }
+        // the two halves meet in shared memory (sD / sAb are free), then one float4 atomic per row
+        float2* hs = reinterpret_cast<float2*>(&sD[0][0][0]);   // [16 values][64 tiles]: the second half's
+        if (tile_on && half == 1)                               // tiles, consecutive tiles in consecutive words
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                hs[q * 64 + tile] = pd[q];
+                hs[(4 + q) * 64 + tile] = po[q];
+                hs[(8 + q) * 64 + tile] = ed[q];
+                hs[(12 + q) * 64 + tile] = eo[q];
+            }
+        __syncthreads();
+        if (tile_on && half == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 a0 = hs[q * 64 + tile];
+                const float2 a1 = hs[(4 + q) * 64 + tile];
+                const float2 a2 = hs[(8 + q) * 64 + tile];
+                const float2 a3 = hs[(12 + q) * 64 + tile];
+                pd[q].x += a0.x, pd[q].y += a0.y, po[q].x += a1.x, po[q].y += a1.y;
+                ed[q].x += a2.x, ed[q].y += a2.y, eo[q].x += a3.x, eo[q].y += a3.y;
+            }
+            // block (lb, mb) = q: rows l4 + 2 lb + {0, 1}, columns m4 + 2 mb + {0, 1}
+            float P4[4][4], E4[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int lb = q >> 1, mb = q & 1;
+                P4[2 * lb][2 * mb] = pd[q].x, P4[2 * lb + 1][2 * mb + 1] = pd[q].y;
+                P4[2 * lb][2 * mb + 1] = po[q].x, P4[2 * lb + 1][2 * mb] = po[q].y;
+                E4[2 * lb][2 * mb] = ed[q].x, E4[2 * lb + 1][2 * mb + 1] = ed[q].y;
+                E4[2 * lb][2 * mb + 1] = eo[q].x, E4[2 * lb + 1][2 * mb] = eo[q].y;
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                float* P = a.gacc + (int64_t)k * RR + (l4 + x) * R + m4;
+                float* E = a.gacc + ((int64_t)a.ndim + k) * RR + (l4 + x) * R + m4;
+                atomicAdd(reinterpret_cast<float4*>(P), make_float4(P4[x][0], P4[x][1], P4[x][2], P4[x][3]));
+                atomicAdd(reinterpret_cast<float4*>(E), make_float4(E4[x][0], E4[x][1], E4[x][2], E4[x][3]));
+            }
+        }
+    }
+    if (a.gzero && last_block_ticket(a.tk)) {   // every block has read gprev: clear it for reuse
+        for (int i = threadIdx.x; i < 2 * a.ndim * RR; i += blockDim.x) a.gzero[i] = 0.0f;
         if (threadIdx.x == 0) {
             a.tk->ticket = 0u;
             __threadfence();

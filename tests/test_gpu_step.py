@@ -51,6 +51,7 @@ def run_stream(sg, p, A0, slices, okw, tol, check_own=False):
                 ctx.step(idx=dev(X["idx"]), vals=dev(X["val"]))
                 Xo = solver.Slice(dims=okw["dims"], idx=X["idx"], val=X["val"])
             st = ctx.stats()
+            ctx.last_stats = st
             assert st["error_bits"] == 0 and st["t"] == t
             dw = bits(st["accept_w"], st["epochs_w"]) if okw.get("temporal", "adam") == "adam" else []
             df = bits(st["accept_f"], st["epochs_f"])
@@ -130,6 +131,30 @@ def test_sparse_stream_matches_oracle(sg, loss):
     p = sg.params(dims, R, loss, **kw)
     okw = dict(dims=dims, rank=R, loss=loss, **kw)
     run_stream(sg, p, A0, slices, okw, tol=2e-4)
+
+
+@pytest.mark.parametrize("R,alpha_f", [(12, 0.01), (32, 0.01), (32, 3.0)])
+def test_sparse_fp32_history_factor_update_ranks_and_rollbacks(sg, R, alpha_f):
+    """FP32 factor solve with history at R = 12 and 32 on modes whose row counts are not multiples of
+    the update's 64-row blocks: the update forms the next iteration's history coefficients itself,
+    and with alpha_f = 3 epochs are rejected, so an epoch restarts from rolled-back factors (the Gram
+    chain runs again there)."""
+    dims = (300, 170, 90)
+    cfg = S.workload("sparse_binary_zipf")
+    rng = np.random.default_rng(R)
+    A0 = [(0.3 * rng.random((n, R)) + 0.05).astype(np.float32) for n in dims]
+    slices = []
+    for t in range(1, 4):
+        idx, val = S.sparse_slice(cfg, t, nnz=6000, dims=dims)
+        slices.append({"idx": idx, "val": val})
+    kw = dict(H=3, w=1.0, kappa_w=2, tau_w=5, alpha_w=0.05, kappa_f=3, tau_f=5, alpha_f=alpha_f,
+              p=900, q=900, p_obj=1500, q_obj=1500, seed=31)
+    p = sg.params(dims, R, "bernoulli_logit", **kw)
+    okw = dict(dims=dims, rank=R, loss="bernoulli_logit", **kw)
+    ctx = run_stream(sg, p, A0, slices, okw, tol=2e-4)
+    if alpha_f > 1.0:
+        st = ctx.last_stats
+        assert st["epochs_f"] > 0 and st["accept_f"] != (1 << st["epochs_f"]) - 1, "no epoch was rejected"
 
 
 def test_checkpoint_resume_continues_the_trajectory(sg):
