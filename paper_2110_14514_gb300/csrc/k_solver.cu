@@ -386,26 +386,9 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     }
     if (skipv) return;   // the solver has finished: nothing is written
     const bool hist = hlen > 0;
-    if (a.gprev) {   // B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H, telescoped as in hist_coeff_elem
+    if (a.gprev)   // B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H of this block's mode
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float gam = 1.0f, dgam = 0.0f;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                if (m == k || m >= a.ndim) continue;
-                gam *= gp[q][m];
-                float term = ge[q][m];
-#pragma unroll
-                for (int n = 0; n < 4; ++n) {
-                    if (n == k || n == m || n >= a.ndim) continue;
-                    term *= (n < m) ? (gp[q][n] - ge[q][n]) : gp[q][n];
-                }
-                dgam += term;
-            }
-            bco[q] = gam * gsh[q];
-            cco[q] = dgam * gsh[q];
-        }
-    }
+        for (int q = 0; q < 4; ++q) hist_coeff_k<float>(a.ndim, k, gp[q], ge[q], gsh[q], bco[q], cco[q]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = threadIdx.x + 256 * q, l = i >> 5, m = i & 31;

@@ -96,78 +96,45 @@ __device__ __forceinline__ void epoch_end_state(SolverState* st, bool passed, in
 
 // ---------------------------------------------------------------------------
 // History coefficients B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H
-// at entry i of the R x R matrices, from P_n = A'A and E_n = D'A (element type G).
+// at entry i of the R x R matrices, from P_n = A'A and E_n = D'A.
 // Gamma_k - Gammabar_k is telescoped: prod P - prod Q = sum_m (prod_{n<m} Q)
 // E_m (prod_{n>m} P), Q = P - E, so nothing cancels when A ~ Abar.
 // ---------------------------------------------------------------------------
-template <typename T, typename G = double>
-__device__ __forceinline__ void hist_coeff_elem(int ndim, int RR, const G* P, const G* E, const double* SH, int i,
-                                                bool on, T* B, T* C) {
+// B_k and C_k at one entry from that entry's P_n, E_n (n < ndim <= 4) and S_H.
+template <typename T>
+__device__ __forceinline__ void hist_coeff_k(int ndim, int k, const T (&p)[4], const T (&e)[4], T sh, T& b, T& c) {
+    T gam = T(1), dgam = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (m == k || m >= ndim) continue;
+        gam *= p[m];
+        T term = e[m];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            if (n == k || n == m || n >= ndim) continue;
+            term *= (n < m) ? (p[n] - e[n]) : p[n];
+        }
+        dgam += term;
+    }
+    b = gam * sh;
+    c = dgam * sh;
+}
+
+template <typename T>
+__device__ __forceinline__ void hist_coeff_elem(int ndim, int RR, const double* P, const double* E, const double* SH,
+                                                int i, bool on, T* B, T* C) {
     T p[4], e[4];
-    for (int n = 0; n < ndim; ++n) {
-        p[n] = on ? (T)__ldcg(P + n * RR + i) : T(0);
-        e[n] = on ? (T)__ldcg(E + n * RR + i) : T(0);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        p[n] = on && n < ndim ? (T)__ldcg(P + n * RR + i) : T(0);
+        e[n] = on && n < ndim ? (T)__ldcg(E + n * RR + i) : T(0);
     }
     const T sh = on ? (T)__ldcg(SH + i) : T(0);
     for (int k = 0; k < ndim; ++k) {
-        if (!on) {
-            B[k * RR + i] = T(0);
-            C[k * RR + i] = T(0);
-            continue;
-        }
-        T gam = T(1), dgam = T(0);
-        for (int m = 0; m < ndim; ++m) {
-            if (m == k) continue;
-            gam *= p[m];
-            T term = e[m];
-            for (int n = 0; n < ndim; ++n) {
-                if (n == k || n == m) continue;
-                term *= (n < m) ? (p[n] - e[n]) : p[n];
-            }
-            dgam += term;
-        }
-        B[k * RR + i] = gam * sh;
-        C[k * RR + i] = dgam * sh;
-    }
-}
-
-// The same coefficients for a compile-time order, every load issued before the arithmetic (one
-// thread may handle several entries: pass them as a batch so their loads overlap).
-template <int NDIM, int NQ, typename T, typename G>
-__device__ __forceinline__ void hist_coeff_batch(int RR, const G* P, const G* E, const double* SH, const int (&idx)[NQ],
-                                                 bool on, T* B, T* C) {
-    T p[NQ][NDIM], e[NQ][NDIM], sh[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const bool in = on && idx[q] < RR;
-#pragma unroll
-        for (int n = 0; n < NDIM; ++n) {
-            p[q][n] = in ? (T)__ldcg(P + n * RR + idx[q]) : T(0);
-            e[q][n] = in ? (T)__ldcg(E + n * RR + idx[q]) : T(0);
-        }
-        sh[q] = in ? (T)__ldcg(SH + idx[q]) : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        if (idx[q] >= RR) continue;
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-            T gam = T(1), dgam = T(0);
-#pragma unroll
-            for (int m = 0; m < NDIM; ++m) {
-                if (m == k) continue;
-                gam *= p[q][m];
-                T term = e[q][m];
-#pragma unroll
-                for (int n = 0; n < NDIM; ++n) {
-                    if (n == k || n == m) continue;
-                    term *= (n < m) ? (p[q][n] - e[q][n]) : p[q][n];
-                }
-                dgam += term;
-            }
-            B[k * RR + idx[q]] = gam * sh[q];
-            C[k * RR + idx[q]] = dgam * sh[q];
-        }
+        T b = T(0), c = T(0);
+        if (on) hist_coeff_k<T>(ndim, k, p, e, sh, b, c);
+        B[k * RR + i] = b;
+        C[k * RR + i] = c;
     }
 }
 
