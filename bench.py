@@ -123,6 +123,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x, device):
+    """The largest of every rank's x (the slowest rank's time); x itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_step_per_rank, total_s):
+    """Units processed by all ranks (weak scaling: each rank its own replica) per second of the
+    slowest rank's timed region."""
+    return world * steps * units_per_step_per_rank / total_s
+
+
 def make_slices(cfg, n):
     return [S.sparse_slice(cfg, t) for t in range(1, n + 1)]
 
@@ -217,13 +234,8 @@ def run_native(args, cfg, world, rank, local):
     st = ctx.stats()
     launches = st["kernels_launched"] - k0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
-    value = world * args.steps * samples_per_step / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
+    value = whole_job_rate(world, args.steps, samples_per_step, total_s)
 
     # dominant kernel: the fused sampled factor gradient, timed alone back to back on the context stream
     i, v = dslices[0]
