@@ -86,7 +86,8 @@ def loss_dfdm(loss, x, m, eps=1e-10):
     if loss == "bernoulli_odds":
         return 1.0 / (m + 1.0) - x / (m + eps)
     if loss == "bernoulli_logit":
-        return 1.0 / (1.0 + np.exp(-m)) - x
+        with np.errstate(over="ignore"):   # e^-m -> inf for m << 0: 1 / (1 + inf) = 0 is the limit
+            return 1.0 / (1.0 + np.exp(-m)) - x
     raise ValueError(loss)
 
 
