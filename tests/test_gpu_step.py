@@ -157,6 +157,25 @@ def test_sparse_fp32_history_factor_update_ranks_and_rollbacks(sg, R, alpha_f):
         assert st["epochs_f"] > 0 and st["accept_f"] != (1 << st["epochs_f"]) - 1, "no epoch was rejected"
 
 
+@pytest.mark.parametrize("dims,nnz,pq", [((60, 50), 600, 200), ((30, 20, 15, 12), 3000, 600)])
+def test_sparse_fp32_history_two_and_four_way(sg, dims, nnz, pq):
+    """The FP32 factor update with history on 2-way and 4-way slices (its blocks hold one mode each
+    and form B_k, C_k over the other d - 1 modes)."""
+    R = 8
+    cfg = S.workload("sparse_binary_zipf")
+    rng = np.random.default_rng(len(dims))
+    A0 = [(0.3 * rng.random((n, R)) + 0.05).astype(np.float32) for n in dims]
+    slices = []
+    for t in range(1, 4):
+        idx, val = S.sparse_slice(cfg, t, nnz=nnz, dims=dims)
+        slices.append({"idx": idx, "val": val})
+    kw = dict(H=2, w=1.0, kappa_w=2, tau_w=5, alpha_w=0.05, kappa_f=2, tau_f=5, alpha_f=0.01,
+              p=pq, q=pq, p_obj=pq, q_obj=pq, seed=17)
+    p = sg.params(dims, R, "bernoulli_logit", **kw)
+    okw = dict(dims=dims, rank=R, loss="bernoulli_logit", **kw)
+    run_stream(sg, p, A0, slices, okw, tol=2e-4)
+
+
 def test_checkpoint_resume_continues_the_trajectory(sg):
     cfg = S.workload("dense_gaussian_2way")
     A0 = S.init_factors(cfg)
