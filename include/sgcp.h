@@ -213,9 +213,10 @@ sgcp_status sgcp_ingest(sgcp_ctx* ctx, const sgcp_slice* X);
  *   f_out    (device, 1 double) <- sum of weight * f(x, m)   if SGCP_WANT_LOSS
  * s (device, R) and A (device, ndim pointers, I_k x R) are the point of
  * evaluation.  History and regularisation terms are not included.  Outputs
- * not requested may be NULL.  A[k] and G_out[k] must be 16-byte aligned (rows
- * are moved with 16-byte vector accesses; any cudaMalloc'd or torch-allocated
- * buffer is), else SGCP_ERR_ARG.  Asynchronous on the context stream. */
+ * not requested may be NULL.  s, A[k] and G_out[k] must be 16-byte aligned
+ * (they are read or accumulated with 16-byte vector accesses; any cudaMalloc'd
+ * or torch-allocated buffer is), else SGCP_ERR_ARG.  Asynchronous on the
+ * context stream. */
 sgcp_status sgcp_gradient(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, const void* const* A,
                           const sgcp_grad_opts* opts, void* const* G_out, void* gs_out, double* f_out);
 
@@ -240,7 +241,8 @@ sgcp_status sgcp_sample_coords(sgcp_ctx* ctx, const sgcp_slice* X, int32_t sampl
  * read; precision must not be SGCP_PREC_F64), the COO slice (device: idx
  * [nnz][ndim] int32, vals [nnz] float), s (device, R floats), A (host array
  * of ndim device pointers to I_k x R float matrices), opts, and the outputs
- * G_out / gs_out / f_out as in sgcp_gradient.  err_out (device int32 or
+ * G_out / gs_out / f_out as in sgcp_gradient (s, A[k], G_out[k] 16-byte
+ * aligned, else SGCP_ERR_ARG).  err_out (device int32 or
  * NULL) is set to 0 and then receives the device error bits of this call
  * (coordinate out of range or duplicate: 1 or 2; zero sampling exhausted: 4).
  * Work is queued on cuda_stream (NULL = legacy default stream).

@@ -1101,6 +1101,8 @@ sgcp_status sgcp_gradient(sgcp_ctx* c, const sgcp_slice* X, const void* s, const
                           const sgcp_grad_opts* opts, void* const* G_out, void* gs_out, double* f_out) {
     if (sgcp_status st = check_ready(c)) return st;
     if (!opts || !s || !A) return fail(c, SGCP_ERR_ARG, "gradient: NULL argument");
+    if ((reinterpret_cast<uintptr_t>(s) & 15) != 0)
+        return fail(c, SGCP_ERR_ARG, "gradient: s is not 16-byte aligned");   // read as 16-byte vectors
     const int want = opts->want;
     if (want & ~7) return fail(c, SGCP_ERR_ARG, "gradient: bad want bits");
     if ((want & SGCP_WANT_FACTORS) && !G_out) return fail(c, SGCP_ERR_ARG, "gradient: G_out is NULL");

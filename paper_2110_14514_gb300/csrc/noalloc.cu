@@ -81,6 +81,7 @@ extern "C" sgcp_status sgcp_gradient_sparse_noalloc(const sgcp_params* params, i
                                                     const sgcp_grad_opts* opts, float* const* G_out, float* gs_out,
                                                     double* f_out, int32_t* err_out, void* cuda_stream) {
     if (!params || !opts || !s || !A) return SGCP_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(s) & 15) != 0) return SGCP_ERR_ARG;   // read as 16-byte vectors
     const sgcp_params& P = *params;
     if (P.ndim < 2 || P.ndim > 4 || P.rank < 4 || P.rank > 128 || P.rank % 4 != 0) return SGCP_ERR_UNSUPPORTED;
     if (P.loss < 0 || P.loss > 3 || P.zero_attempt_cap < 1) return SGCP_ERR_ARG;
@@ -96,6 +97,9 @@ extern "C" sgcp_status sgcp_gradient_sparse_noalloc(const sgcp_params* params, i
         if (P.dims[k] < 1 || P.dims[k] > 0x7fffffff) return SGCP_ERR_ARG;
         if ((double)P.dims[k] * P.rank >= 2147483648.0) return SGCP_ERR_UNSUPPORTED;
         if (!A[k] || ((want & SGCP_WANT_FACTORS) && !G_out[k])) return SGCP_ERR_ARG;
+        if ((reinterpret_cast<uintptr_t>(A[k]) & 15) != 0 ||
+            ((want & SGCP_WANT_FACTORS) && (reinterpret_cast<uintptr_t>(G_out[k]) & 15) != 0))
+            return SGCP_ERR_ARG;
         omega *= (double)P.dims[k];
     }
     if (omega > 9.0e18) return SGCP_ERR_UNSUPPORTED;

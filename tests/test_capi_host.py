@@ -81,6 +81,23 @@ def test_argument_errors_are_synchronous_without_a_gpu(sg):
     assert sg.sgcp_params_default(None) == sg.ERR_ARG
 
 
+def test_noalloc_alignment_errors_are_synchronous_without_a_gpu(sg):
+    """s, A[k], G_out[k] off a 16-byte boundary are refused before any device work (the pointer
+    values below are never dereferenced)."""
+    p = sg.params((100, 80, 60), 8, "bernoulli_logit", p=64, q=64)
+    opts = sg.sgcp_grad_opts(want=sg.WANT_FACTORS)
+    A_ok = (ctypes.c_void_p * 3)(0x10000, 0x20000, 0x30000)
+    G_ok = (ctypes.c_void_p * 3)(0x40000, 0x50000, 0x60000)
+    A_bad = (ctypes.c_void_p * 3)(0x10000, 0x20004, 0x30000)
+    G_bad = (ctypes.c_void_p * 3)(0x40000, 0x50000, 0x60008)
+    def call(s, A, G):
+        return sg.sgcp_gradient_sparse_noalloc(ctypes.byref(p), 10, 0x70000, 0x80000, s, A, ctypes.byref(opts), G,
+                                               None, None, None, None)
+    assert call(0x90004, A_ok, G_ok) == sg.ERR_ARG
+    assert call(0x90000, A_bad, G_ok) == sg.ERR_ARG
+    assert call(0x90000, A_ok, G_bad) == sg.ERR_ARG
+
+
 def test_no_cpu_fallback_when_cuda_is_missing(sg):
     """Without a device the library refuses to create a context (it never computes on the host)."""
     import torch

@@ -101,7 +101,7 @@ def test_dense_loss_only_and_partial_wants(sg):
 
 
 def test_misaligned_factor_or_gradient_pointer_is_an_argument_error(sg):
-    """A[k] / G_out[k] 4 bytes off a 16-byte boundary: rejected on the host, nothing launched."""
+    """s, A[k], G_out[k] 4 bytes off a 16-byte boundary: rejected on the host, nothing launched."""
     X, A, s = case((20, 24, 28), 16, "gaussian", np.float32, seed=4)
     p = sg.params(X.shape, 16, "gaussian")
     with sg.Context(p, [dev(a) for a in A]) as ctx:
@@ -117,6 +117,12 @@ def test_misaligned_factor_or_gradient_pointer_is_an_argument_error(sg):
         G[2] = gbase[2:2 + G[2].numel()].view(G[2].shape)
         with pytest.raises(sg.SgcpError) as ei:
             ctx.gradient(dev(s), Ad, X=dev(X), want=sg.WANT_FACTORS, G=G)
+        assert ei.value.status == sg.ERR_ARG
+        sbase = torch.zeros(s.size + 1, dtype=torch.float32, device="cuda")
+        s_off = sbase[1:]
+        s_off.copy_(dev(s))
+        with pytest.raises(sg.SgcpError) as ei:
+            ctx.gradient(s_off, Ad, X=dev(X), want=sg.WANT_LOSS)
         assert ei.value.status == sg.ERR_ARG
         ctx.gradient(dev(s), Ad, X=dev(X), want=sg.WANT_FACTORS)   # the context is still usable
         ctx.check()
