@@ -282,6 +282,25 @@ def full_objective(X, A, s, Abar, s_hist, w_h, P):
     return F + gcp.regularization_objective(A, s, P.lam, 0.0)
 
 
+def lbfgs_direction(g, S, Yv):
+    """H g by the two-loop recursion (Nocedal & Wright Alg. 7.4) over the pairs (S[i], Yv[i]),
+    oldest first, with H_0 = gamma I, gamma = s'y / y'y of the newest pair (1 / ||g|| without
+    pairs)."""
+    qv = g.copy()
+    alphas = []
+    for sv, yv in reversed(list(zip(S, Yv))):
+        rho = 1.0 / (yv @ sv)
+        al = rho * (sv @ qv)
+        alphas.append((al, rho, sv, yv))
+        qv = qv - al * yv
+    gamma = (S[-1] @ Yv[-1]) / (Yv[-1] @ Yv[-1]) if S else 1.0 / max(np.linalg.norm(g), 1e-300)
+    r = gamma * qv
+    for al, rho, sv, yv in reversed(alphas):
+        be = rho * (yv @ r)
+        r = r + sv * (al - be)
+    return r
+
+
 def fac_lbfgs(X, A, s, Abar, s_hist, w_h, P, t):
     """Projected L-BFGS on the factor matrices of a dense slice (build-defined, not in the paper).
 
@@ -304,19 +323,7 @@ def fac_lbfgs(X, A, s, Abar, s_hist, w_h, P, t):
     F, g = fg(a)
     S, Yv = [], []
     for _ in range(P.lbfgs_iters):
-        qv = g.copy()
-        alphas = []
-        for sv, yv in reversed(list(zip(S, Yv))):
-            rho = 1.0 / (yv @ sv)
-            al = rho * (sv @ qv)
-            alphas.append((al, rho, sv, yv))
-            qv = qv - al * yv
-        gamma = (S[-1] @ Yv[-1]) / (Yv[-1] @ Yv[-1]) if S else 1.0 / max(np.linalg.norm(g), 1e-300)
-        r = gamma * qv
-        for al, rho, sv, yv in reversed(alphas):
-            be = rho * (yv @ r)
-            r = r + sv * (al - be)
-        pdir = -r
+        pdir = -lbfgs_direction(g, S, Yv)
         step = 1.0
         accepted = False
         for _ls in range(30):

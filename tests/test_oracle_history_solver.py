@@ -184,6 +184,30 @@ def test_teacher_forced_rejection_restores_the_factors():
         assert np.array_equal(a, b)
 
 
+def test_lbfgs_two_loop_equals_the_explicit_inverse_bfgs_update():
+    """The two-loop recursion returns H g for the matrix built by the inverse BFGS update
+    H <- (I - rho s y') H (I - rho y s') + rho s s' (Nocedal & Wright eq. 6.17), applied to the
+    pairs oldest first from H_0 = gamma I with gamma = s'y / y'y of the newest pair."""
+    rng = np.random.default_rng(8)
+    n, m = 9, 5
+    Q = rng.standard_normal((n, n))
+    B = Q @ Q.T + n * np.eye(n)                     # SPD curvature, so every s'y > 0
+    S = [rng.standard_normal(n) for _ in range(m)]
+    Yv = [B @ sv for sv in S]
+    g = rng.standard_normal(n)
+    r = solver.lbfgs_direction(g, S, Yv)
+    gamma = (S[-1] @ Yv[-1]) / (Yv[-1] @ Yv[-1])
+    H = gamma * np.eye(n)
+    for sv, yv in zip(S, Yv):
+        rho = 1.0 / (yv @ sv)
+        V = np.eye(n) - rho * np.outer(yv, sv)
+        H = V.T @ H @ V + rho * np.outer(sv, sv)
+    np.testing.assert_allclose(r, H @ g, rtol=1e-10, atol=1e-12)
+    # with no pairs the direction is the scaled gradient; the secant equation holds for the newest pair
+    np.testing.assert_allclose(solver.lbfgs_direction(g, [], []), g / np.linalg.norm(g), rtol=1e-14)
+    np.testing.assert_allclose(solver.lbfgs_direction(Yv[-1], S, Yv), S[-1], rtol=1e-9, atol=1e-12)
+
+
 def test_lbfgs_decreases_the_exact_objective():
     rng = np.random.default_rng(33)
     dims, R = (5, 4, 3), 2
