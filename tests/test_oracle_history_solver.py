@@ -144,6 +144,23 @@ def test_lsq_temporal_recovers_planted_weights():
     np.testing.assert_allclose(solver.lsq_temporal(Xs, A, P), s, rtol=1e-10)
 
 
+def test_lsq_temporal_with_ridge_minimises_the_penalised_residual():
+    """mu > 0: the solve returns the minimiser of ||x - Z s||^2 + (mu / 2) ||s||^2, checked against
+    a least-squares solve of the augmented system [Z; sqrt(mu / 2) I] s = [x; 0] with Z built from
+    explicit rank-one tensors."""
+    rng = np.random.default_rng(35)
+    dims, R, mu = (5, 4, 6), 3, 0.7
+    A = [rng.standard_normal((n, R)) for n in dims]
+    X = rng.standard_normal(dims)
+    P = solver.Params(dims=dims, rank=R, loss="gaussian", mu=mu)
+    s = solver.lsq_temporal(solver.Slice(dims=dims, X=X), A, P)
+    Z = np.stack([np.einsum("i,j,k->ijk", A[0][:, r], A[1][:, r], A[2][:, r]).ravel() for r in range(R)], axis=1)
+    Zaug = np.vstack([Z, np.sqrt(mu / 2) * np.eye(R)])
+    xaug = np.concatenate([X.ravel(), np.zeros(R)])
+    ref = np.linalg.lstsq(Zaug, xaug, rcond=None)[0]
+    np.testing.assert_allclose(s, ref, rtol=1e-10, atol=1e-12)
+
+
 def test_temporal_and_factor_solvers_decrease_the_objective():
     rng = np.random.default_rng(31)
     dims, R = (6, 5, 4), 2
