@@ -536,8 +536,10 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     }
 }
 
+// Launches k_factor_update_rows when it applies (FP32, R <= 32, history coefficients present);
+// false leaves the update to the warp-per-row kernel.
 template <typename T>
-static bool factor_update_chunked(const FactorUpdateArgs<T>& a, cudaStream_t st, cudaError_t* err) {
+static bool factor_update_rows(const FactorUpdateArgs<T>& a, cudaStream_t st, cudaError_t* err) {
     if constexpr (std::is_same<T, float>::value) {
         if (a.R > 32 || a.B == nullptr) return false;
         int64_t blocks = 0;
@@ -562,7 +564,7 @@ cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, 
     if (a.R > 128) return cudaErrorInvalidValue;
     {
         cudaError_t e = cudaSuccess;
-        if (factor_update_chunked(a, st, &e)) {
+        if (factor_update_rows(a, st, &e)) {
             if (launches) *launches += 1;
             return e;
         }
