@@ -39,24 +39,97 @@ import synthetic as S  # noqa: E402
 WORKLOAD = "sparse_binary_zipf"
 SOLVER = dict(H=10, w=1.0, theta=1.0, kappa_w=5, kappa_f=5, tau_w=100, tau_f=100, alpha_w=0.1, alpha_f=1e-3)
 BYTES_PER_SAMPLE = 784      # 12 B coords + 4 B value + 3 x 128 B row gathers + 3 x 128 B row scatters (R = 32)
+BYTES_PER_SAMPLE_TEMPORAL = 400   # 12 B coords + 4 B value + 3 x 128 B row gathers (no scatters)
 N_SLICES = 4                # distinct slices cycled through (every step re-ingests its slice)
 METRIC = "fused GCP gradient nnz/s"
+
+
+def recorded_counters(summary="sparse_grad_factor_R32_zipf1e6.md"):
+    """Counters of a dominant kernel from the machine-readable line of its committed ncu summary
+    (key=value pairs: dram_bytes_per_launch, and where captured lts_bytes_per_launch,
+    lts_throughput_pct), or {} when the kernel's source changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        line = re.search(r"machine-readable: (.*)", text).group(1)
+        kv = dict(re.findall(r"(\w+)=(\S+)", line))
+        src = open(os.path.join(ROOT, kv["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != kv["source_sha256_16"]:
+            return {}
+        return {k: float(v) if "." in v else int(v) for k, v in kv.items()
+                if k not in ("kernel", "source", "source_sha256_16")}
+    except Exception:
+        return {}
 
 
 def recorded_traffic(summary="sparse_grad_factor_R32_zipf1e6.md"):
     """DRAM bytes per launch of a dominant kernel from its committed ncu summary, or None when
     the kernel's source changed since that capture."""
-    import hashlib
-    import re
+    v = recorded_counters(summary).get("dram_bytes_per_launch")
+    return int(v) if v is not None else None
+
+
+def host_cores():
+    """Host cores this process may run on (the oracle baselines' worker count)."""
     try:
-        text = open(os.path.join(ROOT, "profiles", summary)).read()
-        m = re.search(r"source=(\S+) source_sha256_16=([0-9a-f]+) dram_bytes_per_launch=(\d+)", text)
-        src = open(os.path.join(ROOT, m.group(1)), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != m.group(2):
-            return None
-        return int(m.group(3))
+        return len(os.sched_getaffinity(0))
     except Exception:
-        return None
+        return os.cpu_count() or 1
+
+
+_ORACLE_SLICE = {}
+
+
+def _oracle_init(idx, val, A):
+    """Worker set-up: the slice and the factors, sent once per process."""
+    _ORACLE_SLICE.update(idx=idx, val=val, A=A)
+
+
+def _oracle_sparse_worker(job):
+    """FP64 oracle sampled gradients of the worker's slice for `budget` seconds (at least one),
+    each with its own draw index.  Returns (evaluations, seconds)."""
+    from oracle import gcp
+    dims, s, loss, p, q, draw0, budget, n_max = job
+    d = _ORACLE_SLICE
+    t0 = time.perf_counter()
+    n = 0
+    while n < n_max and (n == 0 or time.perf_counter() - t0 < budget):
+        gcp.sampled_gradient(d["idx"], d["val"], dims, s, d["A"], loss, p, q, 7, 1, draw0 + n)
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+class OraclePool:
+    """`workers` host processes running the oracle (spawned, so that no process is forked from one
+    that holds a CUDA context), each holding the same slice; workers = 1 runs in this process."""
+
+    def __init__(self, cfg, slice0, workers):
+        self.cfg, self.workers = cfg, workers
+        A = S.init_factors(cfg)
+        if workers == 1:
+            _oracle_init(slice0[0], slice0[1], A)
+            self.pool = None
+        else:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init,
+                                                     initargs=(slice0[0], slice0[1], A))
+
+    def rate(self, budget_s, n_max=10**9, draw0=0):
+        """Samples/s over all workers: each runs independent draws of the slice for budget_s (at
+        most n_max evaluations); all evaluations over the slowest worker's time."""
+        c = self.cfg
+        s = np.full(c["rank"], 0.5, np.float32)
+        jobs = [(c["dims"], s, c["loss"], c["p"], c["q"], draw0 + 100000 * w, budget_s, n_max)
+                for w in range(self.workers)]
+        res = [_oracle_sparse_worker(jobs[0])] if self.pool is None else self.pool.map(_oracle_sparse_worker, jobs)
+        n = sum(r[0] for r in res)
+        return n * (c["p"] + c["q"]) / max(r[1] for r in res), n
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
 
 
 def peaks():
@@ -146,33 +219,31 @@ def make_slices(cfg, n):
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
 def run_reference(args, cfg, world, rank):
+    """The FP64 oracle on the same metric: each step is a bounded sample of oracle sampled-gradient
+    evaluations of the same slice, one per host core (one process per core)."""
     if rank != 0:
         return None
-    from oracle import gcp
-    idx, val = S.sparse_slice(cfg, 1)
-    A = S.init_factors(cfg)
-    s = np.full(cfg["rank"], 0.5, np.float32)
-    per_step = 3          # oracle gradient evaluations per bounded step sample
-
-    def one_step(k):
-        for d in range(per_step):
-            gcp.sampled_gradient(idx, val, cfg["dims"], s, A, cfg["loss"], cfg["p"], cfg["q"], 7, 1, k * per_step + d)
-
-    for w in range(args.warmup):
-        one_step(w)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        one_step(args.warmup + k)
-    dt = time.perf_counter() - t0
-    samples = args.steps * per_step * (cfg["p"] + cfg["q"])
-    value = samples / dt
+    cores = host_cores()
+    pool = OraclePool(cfg, S.sparse_slice(cfg, 1), cores)
+    try:
+        for w in range(args.warmup):
+            pool.rate(0.0, n_max=1, draw0=w)
+        t0 = time.perf_counter()
+        n_all = 0
+        for k in range(args.steps):
+            n_all += pool.rate(0.0, n_max=1, draw0=1000 + k)[1]
+        t_all = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = n_all * (cfg["p"] + cfg["q"]) / t_all
+    sample = (f"{cores} FP64 numpy sampled-gradient evaluations per step (p + q = {cfg['p'] + cfg['q']} each; "
+              f"one per host core, one process per core), same slice")
     return {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": workload_name(cfg), "step": f"{per_step} oracle gradient evaluations (bounded sample)"},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} FP64 numpy sampled-gradient evaluations per step, same slice"},
+        "config": {"workload": workload_name(cfg), "step": sample},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -201,8 +272,12 @@ def run_native(args, cfg, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
     ctx = sg.Context(p, A0)
     stream = ctx.stream
-    grads_per_step = SOLVER["kappa_w"] * SOLVER["tau_w"] + SOLVER["kappa_f"] * SOLVER["tau_f"]
+    n_tmp = SOLVER["kappa_w"] * SOLVER["tau_w"]
+    n_fac = SOLVER["kappa_f"] * SOLVER["tau_f"]
+    n_obj = 2 + SOLVER["kappa_w"] + SOLVER["kappa_f"]
+    grads_per_step = n_tmp + n_fac
     samples_per_step = grads_per_step * (cfg["p"] + cfg["q"])
+    counters = recorded_counters()
 
     def barrier():
         torch.cuda.synchronize()
@@ -278,19 +353,31 @@ def run_native(args, cfg, world, rank, local):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(cfg), "step": "one OnlineGCP slice update (graph)",
-                       "grads_per_step": grads_per_step, "H": SOLVER["H"],
+                       "factor_grads_per_step": n_fac, "temporal_grads_per_step": n_tmp,
+                       "bytes_per_sample": {"factor_gradient": BYTES_PER_SAMPLE,
+                                            "temporal_gradient": BYTES_PER_SAMPLE_TEMPORAL},
+                       "objective_estimates_per_step": n_obj,
+                       "value_counts": "samples of the factor and temporal gradients (p + q each); the "
+                                       "objective estimates' samples are not counted",
+                       "H": SOLVER["H"],
                        "l2": "flushed between steps by a 256 MB write (outside the per-step events)",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "l2-latency (effective vs HBM)", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(), "peak_kind": peak_kind,
                          "traffic_note": "ncu dram read+write bytes per launch, cold caches (working set is L2-resident)",
+                         "lts_bytes_per_launch": counters.get("lts_bytes_per_launch"),
+                         "lts_throughput_pct": counters.get("lts_throughput_pct"),
+                         "note": "achieved = 784 B x (p + q) per launch / CUDA-event launch time: the effective "
+                                 "bandwidth of the algorithmic gathers and scatters, most of which L2 serves",
                          "kernel": "k_sparse_grad<3,32> (factor gradient, 2e5 samples)",
                          "kernel_us": kern_s * 1e6},
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk,
             "step_ms": {"min": min(step_ms), "max": max(step_ms)},
         }
+        if not args.no_dense_record:
+            out["dense_256_r64"] = dense_precision_record(dev)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(cfg, host[0])
     if world > 1:
@@ -300,24 +387,93 @@ def run_native(args, cfg, world, rank, local):
     return out
 
 
-def cpu_baseline(cfg, slice0, budget_s=15.0):
-    """The oracle as it stands: FP64 numpy sampled gradients of the same slice for ~15 s."""
-    from oracle import gcp
-    idx, val = slice0
-    A = S.init_factors(cfg)
-    s = np.full(cfg["rank"], 0.5, np.float32)
-    t0 = time.perf_counter()
-    n = 0
-    while time.perf_counter() - t0 < budget_s and n < 50:
-        gcp.sampled_gradient(idx, val, cfg["dims"], s, A, cfg["loss"], cfg["p"], cfg["q"], 7, 1, n)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": n * (cfg["p"] + cfg["q"]) / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 oracle sampled-gradient evaluations (p + q = {cfg['p'] + cfg['q']}) of one slice"}
+def cpu_baseline(cfg, slice0, budget_s=10.0):
+    """The oracle as it stands: FP64 numpy sampled gradients of the same slice, ~10 s on one core,
+    then ~10 s on every host core (one process per core, independent draws)."""
+    pool = OraclePool(cfg, slice0, 1)
+    one, n1 = pool.rate(budget_s)
+    cores = host_cores()
+    allc, na = one, n1
+    if cores > 1:
+        pool = OraclePool(cfg, slice0, cores)
+        try:
+            pool.rate(0.0, n_max=1)                      # worker start-up outside the timing
+            allc, na = pool.rate(budget_s, draw0=1)
+        finally:
+            pool.close()
+    pq = cfg["p"] + cfg["q"]
+    return {"value": allc, "unit": "samples/s", "cores": cores, "nproc": cores, "kind": "oracle",
+            "sample": f"{na} FP64 oracle sampled-gradient evaluations (p + q = {pq}) of one slice on {cores} cores "
+                      f"(one process per core, ~{budget_s:.0f} s each)",
+            "one_core": {"value": one, "unit": "samples/s", "cores": 1,
+                         "sample": f"{n1} evaluations on one core (~{budget_s:.0f} s)"}}
 
 
 # ----------------------------------------------------------------------------- dense workload (precision study)
 DENSE_SOLVER = dict(H=10, w=1.0, theta=1.0, kappa_w=20, kappa_f=5, tau_w=100, tau_f=100, alpha_w=10.0, alpha_f=1e-4)
+
+
+def dense_precision_record(dev, n_time=2):
+    """The second half of the metric on the 256^3, R = 64 Gaussian slices: per-slice update time
+    (sgcp_step with the Table 2 Gaussian-row solvers, kappa_w = 20, kappa_f = 5, tau = 100), the
+    dense factor-gradient kernel time, and the error of every gradient result (G1, G2, G3, g_s, F)
+    against the FP64 oracle at one point near the planted factors, for the plain FP32 path and the
+    BF16 / FP16 tensor-core MTTKRP paths."""
+    import torch
+    import paper_2110_14514_gb300 as sg
+    from oracle import gcp
+    cfg = S.workload("dense_gaussian_3way")
+    X, s_true = S.dense_slice(cfg, 1)
+    X2, _ = S.dense_slice(cfg, 2)
+    A_true = S.truth(cfg)
+    rng = np.random.default_rng(9)
+    A_pt = [(a + 0.05 * rng.standard_normal(a.shape)).astype(np.float32) for a in A_true]
+    s_pt = s_true.astype(np.float32)
+    Go, gso, Fo = gcp.dense_gradient(X, s_pt, A_pt, "gaussian")
+    Xd = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev) for x in (X, X2)]
+    A0 = [torch.from_numpy(a).to(dev) for a in S.init_factors(cfg)]
+    Apd = [torch.from_numpy(a).to(dev) for a in A_pt]
+    spd = torch.from_numpy(s_pt).to(dev)
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+    out = {"solver": DENSE_SOLVER, "point": "planted factors + 0.05 N(0,1), planted s_1"}
+    for name, prec in (("fp32", sg.PREC_F32), ("bf16", sg.PREC_BF16_MTTKRP), ("fp16", sg.PREC_F16_MTTKRP)):
+        p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=prec, seed=77, **DENSE_SOLVER)
+        with sg.Context(p, A0) as ctx:
+            G, gs, f = ctx.gradient(spd, Apd, X=Xd[0])
+            ctx.check()
+            errs = {f"G{k + 1}": rel(G[k].cpu().numpy(), Go[k]) for k in range(3)}
+            errs["gs"] = rel(gs.cpu().numpy(), gso)
+            errs["F"] = abs(f.item() - Fo) / abs(Fo)
+            ctx.step(X=Xd[0])                          # graph build and warm-up
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_time)]
+            with torch.cuda.stream(ctx.stream):
+                for k in range(n_time):
+                    ev[2 * k].record(ctx.stream)
+                    ctx.step(X=Xd[(k + 1) % 2])
+                    ev[2 * k + 1].record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n_time)) / n_time
+            Gk = [torch.zeros_like(a) for a in Apd]
+            nrep = 20
+            with torch.cuda.stream(ctx.stream):
+                ctx.gradient(spd, Apd, X=Xd[0], want=sg.WANT_FACTORS, G=Gk, accumulate=True)
+                torch.cuda._sleep(20_000_000)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                for r in range(nrep):
+                    ctx.gradient(spd, Apd, X=Xd[r % 2], want=sg.WANT_FACTORS, G=Gk, accumulate=True)
+                e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ctx.check()
+        out[f"{name}_ms_per_slice"] = ms
+        out[f"{name}_kernel_us"] = e0.elapsed_time(e1) * 1e3 / nrep
+        out.setdefault("err_vs_fp64", {})[name] = errs
+    out["bf16_speedup_vs_fp32_per_slice"] = out["fp32_ms_per_slice"] / out["bf16_ms_per_slice"]
+    return out
 
 
 def run_native_dense(args, cfg, world, rank, local):
@@ -712,6 +868,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense-record", action="store_true",
+                    help="sparse workload: skip the 256^3 R=64 per-precision slice-update record")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "dense_gaussian_3way", "dense_poisson_3way", "batched_streams"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])

@@ -245,14 +245,17 @@ sgcp_status sgcp_sample_coords(sgcp_ctx* ctx, const sgcp_slice* X, int32_t sampl
  * aligned, else SGCP_ERR_ARG).  err_out (device int32 or
  * NULL) is set to 0 and then receives the device error bits of this call
  * (coordinate out of range or duplicate: 1 or 2; zero sampling exhausted: 4).
+ * A sample that lands on an out-of-range COO entry is dropped before any
+ * factor or gradient row is touched, with or without err_out.
  * Work is queued on cuda_stream (NULL = legacy default stream).
  *
  * Its only scratch is a fixed 4 MiB device array (2^19 hash slots) inside
  * the library, which every GPU that loads the library holds until the
  * process exits.  Hence nnz is limited to 262144 (SGCP_ERR_UNSUPPORTED
  * beyond).  The first call on each device looks up that array's device
- * address (with the device current); make this first call before any CUDA
- * stream capture.  All calls share the array and each clears the part it
+ * address (with the device current) and keeps it for the life of the
+ * process; make this first call before any CUDA stream capture, and do not
+ * use the entry point on a device across a cudaDeviceReset.  All calls share the array and each clears the part it
  * uses, so calls whose GPU work overlaps (other streams or host threads)
  * race on it and must be serialised by the caller.  No hot-row shared-memory
  * tables are used, so the summation order differs from sgcp_gradient's

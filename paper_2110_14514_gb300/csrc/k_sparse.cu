@@ -84,8 +84,20 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
             philox4x32_10(ctr, a.key0, a.key1);
             e = bounded_u32(ctr[0], (uint32_t)sd.nnz);
         }
+        // The caller's coordinates are checked before any row is touched: an out-of-range
+        // entry latches ERRB_COORD and the sample is dropped (no gather, no scatter).
+        bool inb = true;
 #pragma unroll
-        for (int k = 0; k < D; ++k) ci[k] = __ldg(sd.idx + e * D + k);
+        for (int k = 0; k < D; ++k) {
+            ci[k] = __ldg(sd.idx + e * D + k);
+            inb = inb && ci[k] >= 0 && (int64_t)ci[k] < a.dims[k];
+        }
+        if (!inb) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) ci[k] = 0;
+            set_err(a.err, ERRB_COORD);
+            return;
+        }
         x = __ldg(vals + e);
         w = z.w_nz;
         ok = true;

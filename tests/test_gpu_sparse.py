@@ -32,6 +32,19 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
+def row_err(G, Go):
+    """Worst per-row error of a gradient matrix: max_i ||G_i - Go_i|| / max(||Go_i||, ||Go|| / sqrt(I)).
+    A Zipf head row dominates ||Go||, so the per-array Frobenius error alone would let a cold row be
+    wrong by 100 %; the floor ||Go|| / sqrt(I) (the RMS row norm) keeps rows that are zero or nearly
+    so from dividing by nothing."""
+    G = np.asarray(G, np.float64)
+    Go = np.asarray(Go, np.float64)
+    floor = np.linalg.norm(Go) / np.sqrt(Go.shape[0])
+    den = np.maximum(np.linalg.norm(Go, axis=1), floor)
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(np.linalg.norm(G - Go, axis=1) / den))
+
+
 def zipf_case(dims, nnz, R, seed=0, scale=0.5):
     cfg = S.workload("sparse_binary_zipf")
     idx, val = S.sparse_slice(cfg, 1 + seed, nnz=nnz, dims=dims)
@@ -86,6 +99,7 @@ def test_sampled_gradient_matches_oracle(sg, loss, R):
         Go, gso, Fo = gcp.sampled_gradient(idx, val, dims, s, A, loss, p, q, seed, t, draw)
         for k in range(3):
             assert rel(G[k].cpu().numpy(), Go[k]) < TOL_G, (k, rel(G[k].cpu().numpy(), Go[k]))
+            assert row_err(G[k].cpu().numpy(), Go[k]) < TOL_G, (k, row_err(G[k].cpu().numpy(), Go[k]))
         assert rel(gs.cpu().numpy(), gso) < TOL_G
         assert abs(f.item() - Fo) <= TOL_F * max(abs(Fo), 1.0)
         # temporal sample set, accumulate and y_scale
@@ -116,6 +130,7 @@ def test_two_and_four_way_slices(sg, dims):
     Go, gso, Fo = gcp.sampled_gradient(idx, val, dims, s, A, "bernoulli_logit", 700, 900, 9, 2, 1)
     for k in range(len(dims)):
         assert rel(G[k].cpu().numpy(), Go[k]) < TOL_G
+        assert row_err(G[k].cpu().numpy(), Go[k]) < TOL_G
     assert rel(gs.cpu().numpy(), gso) < TOL_G
     assert abs(f.item() - Fo) <= TOL_F * max(abs(Fo), 1.0)
 
@@ -178,6 +193,55 @@ def test_sampling_limit_and_bad_coordinates_are_reported(sg):
         assert e.value.status == sg.ERR_DATA
 
 
+def bad_coordinate_case(dims, R, pad, nnz=60, seed=8):
+    """A small COO slice whose entry 17 has i_1 = I_1 (one past the last row), and factor matrices
+    with `pad` extra rows past I_k so that even an unguarded row access would stay inside them."""
+    rng = np.random.default_rng(seed)
+    lin = rng.choice(int(np.prod(dims)), nnz, replace=False)
+    idx = np.stack(np.unravel_index(lin, dims), axis=1).astype(np.int32)
+    idx[17, 0] = dims[0]
+    val = np.ones(nnz, np.float32)
+    A = [(0.5 * rng.standard_normal((n + pad, R))).astype(np.float32) for n in dims]
+    s = (rng.random(R) + 0.5).astype(np.float32)
+    return idx, val, A, s
+
+
+def oracle_without_bad_samples(idx, val, dims, s, A, loss, p, q, seed, t, draw):
+    """The oracle's draw on the same slice with every sample that lands on an out-of-range entry
+    removed (the zero stratum is unaffected: the bad entry's linear key is >= prod I_k, so no zero
+    candidate can equal it)."""
+    A = [a[:n].astype(np.float64) for a, n in zip(A, dims)]
+    coords, x, w = gcp.stratified_samples(idx, val, dims, p, q, seed, t, draw, gcp.PURPOSE["grad_nz"],
+                                          gcp.PURPOSE["grad_z"])
+    keep = np.all(coords < np.asarray(dims)[None, :], axis=1)
+    assert (~keep).sum() > 0, "the draw never sampled the bad entry"
+    uc, yt = gcp.strat_grad_tensor(coords[keep], x[keep], w[keep], s, A, loss)
+    G = [gcp.sparse_mttkrp(uc, yt, s, A, k) for k in range(len(A))]
+    return G, gcp.sparse_temporal(uc, yt, A), gcp.sampled_loss(coords[keep], x[keep], w[keep], s, A, loss)
+
+
+def test_out_of_range_coordinates_are_never_dereferenced(sg):
+    """sgcp_gradient on a slice with a coordinate equal to I_1: the call reports SGCP_ERR_DATA, the
+    samples that hit the bad entry are dropped (the rest equals the oracle's draw without them), and
+    the gradient rows past I_k, which the kernel could only reach through the bad coordinate, keep
+    the value they had."""
+    dims, R, pad, p, q = (40, 30, 20), 8, 4, 4000, 100
+    idx, val, A, s = bad_coordinate_case(dims, R, pad)
+    with make_ctx(sg, dims, R, "bernoulli_logit", [a[:n] for a, n in zip(A, dims)], p=p, q=q, seed=3) as ctx:
+        G = [torch.full((n + pad, R), 7.0, device="cuda") for n in dims]
+        _, gs, f = ctx.gradient(dev(s), [dev(a) for a in A], idx=dev(idx), vals=dev(val), t=2, draw=1, G=G)
+        with pytest.raises(sg.SgcpError) as e:
+            ctx.check()
+        assert e.value.status == sg.ERR_DATA
+    Go, gso, Fo = oracle_without_bad_samples(idx, val, dims, s, A, "bernoulli_logit", p, q, 3, 2, 1)
+    for k, n in enumerate(dims):
+        Gk = G[k].cpu().numpy()
+        assert np.all(Gk[n:] == 7.0), k
+        assert rel(Gk[:n], Go[k]) < TOL_G, k
+    assert rel(gs.cpu().numpy(), gso) < TOL_G
+    assert abs(f.item() - Fo) <= TOL_F * max(abs(Fo), 1.0)
+
+
 def test_host_slice_matches_device_slice(sg):
     dims, R = (300, 200, 100), 32
     idx, val, A, s = zipf_case(dims, 5000, R, seed=3)
@@ -210,5 +274,7 @@ def test_full_size_sparse_binary_zipf_gradient(sg):
     Go, gso, Fo = gcp.sampled_gradient(idx, val, dims, s, A, cfg["loss"], cfg["p"], cfg["q"], 2024, 1, 0)
     for k in range(3):
         assert rel(G[k].cpu().numpy(), Go[k]) < TOL_G, (k, rel(G[k].cpu().numpy(), Go[k]))
+        # every row, cold rows included (the hot-row shared-memory flush and the direct scatters)
+        assert row_err(G[k].cpu().numpy(), Go[k]) < TOL_G, (k, row_err(G[k].cpu().numpy(), Go[k]))
     assert rel(gs.cpu().numpy(), gso) < TOL_G
     assert abs(f.item() - Fo) <= TOL_F * max(abs(Fo), 1.0)

@@ -201,6 +201,36 @@ def test_teacher_forced_rejection_restores_the_factors():
         assert np.array_equal(a, b)
 
 
+def test_temporal_solver_rejection_restores_s_F_and_the_iteration_count():
+    """Alg. 3 rejection branch (restore s, F <- F_old, i <- i - tau_w, decay alpha), pinned by two
+    invariants on a dense Gaussian slice (exact gradient, so the draw counter plays no part):
+    (1) two rejected epochs return the starting point s = 0 and the objective there, which for the
+        Gaussian loss is sum x^2 in closed form;
+    (2) a rejected epoch followed by an accepted one equals a single epoch run with the decayed
+        rate from scratch.  That holds only if the rejection restored s and the moments and also
+        rolled i back: with i left at tau_w the second epoch's bias correction would use
+        1 - beta^(tau_w + j + 1) instead of 1 - beta^(j + 1)."""
+    rng = np.random.default_rng(33)
+    dims, R = (5, 4, 3), 3
+    A = [rng.standard_normal((n, R)) for n in dims]
+    X = rng.standard_normal(dims)
+    Xs = solver.Slice(dims=dims, X=X)
+    kw = dict(dims=dims, rank=R, loss="gaussian", tau_w=7, alpha_w=0.05, alpha_decay=0.1)
+    P = solver.Params(kappa_w=2, **kw)
+    log = []
+    s, F = solver.wght_gcp_sgd(Xs, A, P, 1, decisions=iter([False, False]), log=log)
+    assert np.array_equal(s, np.zeros(R))
+    assert F == pytest.approx(float((X ** 2).sum()), rel=1e-14)
+    assert log[1]["F_old"] == log[0]["F_old"]          # the second epoch starts from the restored F
+    s2, F2 = solver.wght_gcp_sgd(Xs, A, P, 1, decisions=iter([False, True]))
+    P1 = solver.Params(kappa_w=1, **dict(kw, alpha_w=0.05 * 0.1))
+    s1, F1 = solver.wght_gcp_sgd(Xs, A, P1, 1, decisions=iter([True]))
+    assert np.allclose(s2, s1, rtol=1e-13, atol=0.0) and F2 == pytest.approx(F1, rel=1e-13)
+    # and the rolled-back counter matters: the un-decayed single epoch is a different point
+    s3, _ = solver.wght_gcp_sgd(Xs, A, solver.Params(kappa_w=1, **kw), 1, decisions=iter([True]))
+    assert not np.allclose(s3, s1)
+
+
 def test_lbfgs_two_loop_equals_the_explicit_inverse_bfgs_update():
     """The two-loop recursion returns H g for the matrix built by the inverse BFGS update
     H <- (I - rho s y') H (I - rho y s') + rho s s' (Nocedal & Wright eq. 6.17), applied to the
