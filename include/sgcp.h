@@ -162,6 +162,27 @@ typedef struct {
     int64_t kernels_launched;     /* kernels queued by this context so far (graph nodes included) */
 } sgcp_stats_t;
 
+/* Device-memory provider for the state a context or a batch owns (the variables of Alg. 1 and
+ * Table 1: factor matrices, Abar, ADAM moments and checkpoints, history window, Gram sums, the
+ * sparse-slice hash and hot-row tables, host-slice staging, L-BFGS work vectors).  With it a
+ * caller lets another memory manager -- for instance torch's caching allocator -- own that memory.
+ *   alloc(bytes, user)  returns `bytes` of device memory on the current device, aligned to at
+ *                       least 256 bytes, or NULL when it cannot (the library call then returns
+ *                       SGCP_ERR_OOM; memory that is not 256-byte aligned is handed back and the
+ *                       call returns SGCP_ERR_ARG);
+ *   free(ptr, user)     releases a pointer that alloc returned.
+ * Both are called on the host thread that calls the library: during sgcp_create /
+ * sgcp_batch_create, at the first use of a lazily sized buffer (the hash and staging buffers of a
+ * larger slice than before, the L-BFGS vectors, the batch's host-slice staging), and during
+ * destroy.  Before it frees a buffer that queued work may still use, the library synchronises its
+ * stream.  Every pointer obtained is freed by the time sgcp_destroy / sgcp_batch_destroy returns,
+ * and a create call that fails frees what it obtained before returning. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} sgcp_allocator;
+
 typedef struct sgcp_ctx sgcp_ctx;
 
 /* Version string of the library. */
@@ -183,13 +204,15 @@ sgcp_status sgcp_params_default(sgcp_params* p);
  *                time indices, each < the first slice's t) and hist_s (device,
  *                n_hist x R temporal weights) describe it (Table 1).
  *  t0            time index of the last warm-start slice; the first sgcp_step is t0 + 1.
- *  cuda_stream   cudaStream_t to queue work on (NULL = the legacy default stream).
+ *  allocator     host, copied: provider of every device buffer the context owns, or NULL for
+ *                cudaMalloc / cudaFree (see sgcp_allocator).
+ *  cuda_stream   cudaStream_t to queue work on (NULL = a stream the context creates).
  *  out           receives the context.
- * Errors: SGCP_ERR_ARG (bad parameters), SGCP_ERR_UNSUPPORTED (outside the
- * limits above), SGCP_ERR_OOM, SGCP_ERR_CUDA. */
+ * Errors: SGCP_ERR_ARG (bad parameters, an allocator without alloc or free),
+ * SGCP_ERR_UNSUPPORTED (outside the limits above), SGCP_ERR_OOM, SGCP_ERR_CUDA. */
 sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_factors,
                         int32_t n_hist, const int64_t* hist_t, const void* hist_s,
-                        int64_t t0, void* cuda_stream, sgcp_ctx** out);
+                        int64_t t0, const sgcp_allocator* allocator, void* cuda_stream, sgcp_ctx** out);
 
 /* Destroy a context and free its device state (synchronises its stream). */
 void sgcp_destroy(sgcp_ctx* ctx);
@@ -340,9 +363,10 @@ sgcp_status sgcp_batch_opts_default(sgcp_batch_opts* opts);
 /* params: host array of n_streams parameter sets.  init_factors: host array
  * of 3 * n_streams device pointers (stream s, mode k at [3 s + k]), each an
  * I_k x R float matrix copied into the batch.  opts may be NULL (defaults).
- * cuda_stream as in sgcp_create.  Streams start at t = 0 with empty history. */
+ * allocator and cuda_stream as in sgcp_create.  Streams start at t = 0 with empty history. */
 sgcp_status sgcp_batch_create(int32_t n_streams, const sgcp_params* params, const void* const* init_factors,
-                              const sgcp_batch_opts* opts, void* cuda_stream, sgcp_batch** out);
+                              const sgcp_batch_opts* opts, const sgcp_allocator* allocator, void* cuda_stream,
+                              sgcp_batch** out);
 void sgcp_batch_destroy(sgcp_batch* batch);
 const char* sgcp_batch_last_error(const sgcp_batch* batch);
 

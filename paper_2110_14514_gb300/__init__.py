@@ -70,6 +70,14 @@ class sgcp_batch_opts(ctypes.Structure):
                 ("n_table", c_int32), ("grid_blocks", c_int32), ("spin_limit", c_int64)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p)
+
+
+class sgcp_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
+
+
 _PTRS = POINTER(c_void_p)
 
 # (name, restype, argtypes) of every entry point declared in include/sgcp.h
@@ -77,8 +85,8 @@ SIGNATURES = [
     ("sgcp_version", c_char_p, []),
     ("sgcp_status_string", c_char_p, [c_int32]),
     ("sgcp_params_default", c_int32, [POINTER(sgcp_params)]),
-    ("sgcp_create", c_int32, [POINTER(sgcp_params), _PTRS, c_int32, POINTER(c_int64), c_void_p, c_int64, c_void_p,
-                              POINTER(c_void_p)]),
+    ("sgcp_create", c_int32, [POINTER(sgcp_params), _PTRS, c_int32, POINTER(c_int64), c_void_p, c_int64,
+                              POINTER(sgcp_allocator), c_void_p, POINTER(c_void_p)]),
     ("sgcp_destroy", None, [c_void_p]),
     ("sgcp_last_error", c_char_p, [c_void_p]),
     ("sgcp_ingest", c_int32, [c_void_p, POINTER(sgcp_slice)]),
@@ -98,8 +106,8 @@ SIGNATURES = [
                                                POINTER(sgcp_grad_opts), _PTRS, c_void_p, c_void_p, c_void_p,
                                                c_void_p]),
     ("sgcp_batch_opts_default", c_int32, [POINTER(sgcp_batch_opts)]),
-    ("sgcp_batch_create", c_int32, [c_int32, POINTER(sgcp_params), _PTRS, POINTER(sgcp_batch_opts), c_void_p,
-                                    POINTER(c_void_p)]),
+    ("sgcp_batch_create", c_int32, [c_int32, POINTER(sgcp_params), _PTRS, POINTER(sgcp_batch_opts),
+                                    POINTER(sgcp_allocator), c_void_p, POINTER(c_void_p)]),
     ("sgcp_batch_destroy", None, [c_void_p]),
     ("sgcp_batch_last_error", c_char_p, [c_void_p]),
     ("sgcp_batch_step", c_int32, [c_void_p, _PTRS, c_int32]),
@@ -197,10 +205,54 @@ def make_slice(X=None, idx=None, vals=None):
     return sl, keep
 
 
-class Context:
-    """One streaming-GCP context (sgcp_create ... sgcp_destroy) on the current CUDA device."""
+class Allocator:
+    """A device-memory provider for the library (sgcp_allocator) built from two Python callables:
+    alloc(nbytes) -> device address (int) or 0 / None when it cannot, and free(address).  The
+    callables must stay valid while a context or batch created with this object exists (the
+    object keeps them alive; keep the object)."""
 
-    def __init__(self, p, init_factors, hist_t=(), hist_s=None, t0=0, stream=None):
+    def __init__(self, alloc, free):
+        def _alloc(nbytes, user):
+            try:
+                return alloc(int(nbytes)) or None
+            except Exception:
+                return None
+
+        def _free(ptr, user):
+            try:
+                free(int(ptr))
+            except Exception:
+                pass
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        self.c = sgcp_allocator(self._alloc_cb, self._free_cb, None)
+
+
+def torch_allocator(stream):
+    """torch's caching allocator as the provider of a context's or batch's device memory; blocks
+    are allocated for `stream` (the stream the library queues its work on)."""
+    import torch
+
+    def alloc(nbytes):
+        return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+
+    return Allocator(alloc, torch.cuda.caching_allocator_delete)
+
+
+def _alloc_arg(allocator, stream):
+    if allocator is None:
+        return None, None
+    if allocator == "torch":
+        allocator = torch_allocator(stream)
+    return allocator, ctypes.byref(allocator.c)
+
+
+class Context:
+    """One streaming-GCP context (sgcp_create ... sgcp_destroy) on the current CUDA device.
+    allocator: None (the library calls cudaMalloc), "torch" (torch's caching allocator owns the
+    context's device memory) or an Allocator."""
+
+    def __init__(self, p, init_factors, hist_t=(), hist_s=None, t0=0, stream=None, allocator=None):
         import torch
         self.p = p
         self.ndim = p.ndim
@@ -216,8 +268,9 @@ class Context:
         self._enter()
         ht = (c_int64 * max(len(hist_t), 1))(*[int(h) for h in hist_t])
         out = c_void_p()
+        self.allocator, aref = _alloc_arg(allocator, self.stream)
         st = lib.sgcp_create(ctypes.byref(p), _ptr_array(init_factors), len(hist_t), ht,
-                             _ptr(hist_s), int(t0), c_void_p(self.stream.cuda_stream), ctypes.byref(out))
+                             _ptr(hist_s), int(t0), aref, c_void_p(self.stream.cuda_stream), ctypes.byref(out))
         _check(st)
         self.h = out
         self._keep = None
@@ -233,6 +286,7 @@ class Context:
         if getattr(self, "h", None):
             lib.sgcp_destroy(self.h)
             self.h = None
+        self._keep = None           # destroy waited for the stream: the last inputs may go
 
     def __del__(self):
         try:
@@ -348,7 +402,7 @@ class Batch:
     persistent kernel per time step runs every stream's Alg. 1 loop body."""
 
     def __init__(self, plist, init_factors, autotune=False, tune_reps=3, table=None, grid_blocks=0,
-                 spin_limit=0, stream=None):
+                 spin_limit=0, stream=None, allocator=None):
         import torch
         self._torch = torch
         self.n = len(plist)
@@ -380,7 +434,8 @@ class Batch:
             opts.n_table = len(table)
         self.stream.wait_stream(torch.cuda.current_stream())
         out = c_void_p()
-        _check(lib.sgcp_batch_create(self.n, arr, _ptr_array(flat), ctypes.byref(opts),
+        self.allocator, aref = _alloc_arg(allocator, self.stream)
+        _check(lib.sgcp_batch_create(self.n, arr, _ptr_array(flat), ctypes.byref(opts), aref,
                                      c_void_p(self.stream.cuda_stream), ctypes.byref(out)))
         self.h = out
         self._keep = None
@@ -390,6 +445,7 @@ class Batch:
         if getattr(self, "h", None):
             lib.sgcp_batch_destroy(self.h)
             self.h = None
+        self._keep = None
 
     def __del__(self):
         try:

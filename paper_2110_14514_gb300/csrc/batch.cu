@@ -44,6 +44,8 @@ struct sgcp_batch {
     std::string last_error;
     sgcp_status sticky = SGCP_OK;
     int64_t launches = 0;
+    sgcp_allocator ualloc{};               // caller's device-memory provider (used when custom_alloc)
+    bool custom_alloc = false;
 };
 
 namespace {
@@ -59,6 +61,42 @@ sgcp_status bcuda(sgcp_batch* b, cudaError_t e, const char* what) {
         b->sticky = SGCP_ERR_CUDA;
     }
     return e == cudaErrorMemoryAllocation ? SGCP_ERR_OOM : SGCP_ERR_CUDA;
+}
+
+// Device allocation of batch state: through the caller's allocator when one was given at
+// sgcp_batch_create (NULL on failure or misalignment), else cudaMalloc.
+template <typename P>
+bool balloc(sgcp_batch* b, P** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b->custom_alloc) {
+        void* q = b->ualloc.alloc(bytes, b->ualloc.user);
+        if (q && (reinterpret_cast<uintptr_t>(q) & 255) != 0) {
+            b->ualloc.free(q, b->ualloc.user);
+            q = nullptr;
+        }
+        *p = (P*)q;
+        return q != nullptr;
+    }
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    *p = (P*)q;
+    return true;
+}
+
+// Release a pointer from balloc; a caller's allocator may hand the memory out again at once, so
+// the batch stream's queued work is waited for first (cudaFree waits by itself).
+void bfree(sgcp_batch* b, void* p) {
+    if (!p) return;
+    if (b->custom_alloc) {
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        b->ualloc.free(p, b->ualloc.user);
+    } else {
+        cudaFree(p);
+    }
 }
 
 #define BCK(call, what)                                      \
@@ -225,17 +263,16 @@ sgcp_status autotune(sgcp_batch* b, int reps) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     sgcp_status st = SGCP_OK;
     auto cleanup = [&]() {
-        if (xones) cudaFree(xones);
-        if (gscratch) cudaFree(gscratch);
-        if (dtune) cudaFree(dtune);
-        if (dEt) cudaFree(dEt);
+        bfree(b, xones);
+        bfree(b, gscratch);
+        bfree(b, dtune);
+        bfree(b, dEt);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-    if (cudaMalloc(&xones, std::max<int64_t>(maxX, kBatchMaxR) * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&gscratch, maxN * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&dtune, sizeof(BatchStream)) != cudaSuccess ||
-        cudaMalloc(&dEt, sizeof(BatchStepEntry)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+    if (!balloc(b, &xones, std::max<int64_t>(maxX, kBatchMaxR) * sizeof(float)) ||
+        !balloc(b, &gscratch, maxN * sizeof(float)) || !balloc(b, &dtune, sizeof(BatchStream)) ||
+        !balloc(b, &dEt, sizeof(BatchStepEntry)) || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
@@ -327,9 +364,11 @@ sgcp_status sgcp_batch_opts_default(sgcp_batch_opts* o) {
 }
 
 sgcp_status sgcp_batch_create(int32_t n_streams, const sgcp_params* params, const void* const* init_factors,
-                              const sgcp_batch_opts* opts, void* cuda_stream, sgcp_batch** out) {
+                              const sgcp_batch_opts* opts, const sgcp_allocator* allocator, void* cuda_stream,
+                              sgcp_batch** out) {
     if (!out) return SGCP_ERR_ARG;
     *out = nullptr;
+    if (allocator && (!allocator->alloc || !allocator->free)) return SGCP_ERR_ARG;
     if (n_streams < 1 || n_streams > 65536 || !params || !init_factors) return SGCP_ERR_ARG;
     sgcp_batch_opts o;
     sgcp_batch_opts_default(&o);
@@ -353,6 +392,10 @@ sgcp_status sgcp_batch_create(int32_t n_streams, const sgcp_params* params, cons
     if (!b) return SGCP_ERR_OOM;
     b->nS = n_streams;
     b->device = dev;
+    if (allocator) {
+        b->ualloc = *allocator;
+        b->custom_alloc = true;
+    }
     b->P.assign(params, params + n_streams);
     if (o.spin_limit > 0) b->spin_limit = o.spin_limit;
     for (int i = 0; i < o.n_table; ++i) b->table.push_back(o.table[i]);
@@ -425,20 +468,13 @@ sgcp_status sgcp_batch_create(int32_t n_streams, const sgcp_params* params, cons
     Carver sizer{nullptr};
     for (int s = 0; s < n_streams; ++s) carve_stream(sizer, b->hS[s], params[s].H, b->hS[s].R);
     const size_t arena_bytes = sizer.off + 256;
-    if (cudaMalloc(&b->arena, arena_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return bail(bfail(b, SGCP_ERR_OOM, "batch state allocation failed"));
-    }
+    if (!balloc(b, &b->arena, arena_bytes)) return bail(bfail(b, SGCP_ERR_OOM, "batch state allocation failed"));
     Carver cv{(char*)b->arena};
     for (int s = 0; s < n_streams; ++s) carve_stream(cv, b->hS[s], params[s].H, b->hS[s].R);
-    if (cudaMalloc(&b->dS, n_streams * sizeof(BatchStream)) != cudaSuccess ||
-        cudaMalloc(&b->dE, n_streams * sizeof(BatchStepEntry)) != cudaSuccess ||
-        cudaMalloc(&b->ctl, n_streams * sizeof(BatchCtl)) != cudaSuccess ||
-        cudaMalloc(&b->dorder, n_streams * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&b->finished, sizeof(int)) != cudaSuccess || cudaMalloc(&b->err, sizeof(int)) != cudaSuccess) {
-        cudaGetLastError();
+    if (!balloc(b, &b->dS, n_streams * sizeof(BatchStream)) || !balloc(b, &b->dE, n_streams * sizeof(BatchStepEntry)) ||
+        !balloc(b, &b->ctl, n_streams * sizeof(BatchCtl)) || !balloc(b, &b->dorder, n_streams * sizeof(int32_t)) ||
+        !balloc(b, &b->finished, sizeof(int)) || !balloc(b, &b->err, sizeof(int)))
         return bail(bfail(b, SGCP_ERR_OOM, "batch control allocation failed"));
-    }
     cudaStream_t st = b->stream;
     cudaError_t e = cudaMemsetAsync(b->arena, 0, arena_bytes, st);
     SolverState st0{};
@@ -496,8 +532,7 @@ void sgcp_batch_destroy(sgcp_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     void* ptrs[] = {b->arena, b->dS, b->dE, b->ctl, b->dorder, b->finished, b->err, b->xstage};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) bfree(b, p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -517,7 +552,7 @@ sgcp_status sgcp_batch_step(sgcp_batch* b, const void* const* X, int32_t x_on_ho
             const BatchStream& S = b->hS[s];
             tot += ((int64_t)S.dims[0] * S.dims[1] * S.dims[2] + 63) / 64 * 64;
         }
-        BCK(cudaMalloc(&b->xstage, tot * sizeof(float)), "slice staging");
+        if (!balloc(b, &b->xstage, tot * sizeof(float))) return bfail(b, SGCP_ERR_OOM, "slice staging allocation failed");
     }
     for (int s = 0; s < b->nS; ++s) {
         const BatchStream& S = b->hS[s];

@@ -31,6 +31,8 @@ struct sgcp_ctx {
     sgcp_status sticky = SGCP_OK;
     int64_t launches = 0;
     std::vector<void*> allocs;
+    sgcp_allocator ualloc{};     // caller's device-memory provider (used when custom_alloc)
+    bool custom_alloc = false;
 
     // factor-solver state (N elements each, element type T)
     void *A = nullptr, *Abar = nullptr, *G = nullptr, *u = nullptr, *v = nullptr, *u_o = nullptr, *v_o = nullptr,
@@ -124,8 +126,25 @@ sgcp_status cuda_fail(sgcp_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
+// Device allocation of context state: through the caller's allocator when one was given at
+// sgcp_create, else cudaMalloc.  Every pointer is recorded so that sgcp_destroy releases it.
 sgcp_status dalloc(sgcp_ctx* c, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
+    if (c->custom_alloc) {
+        *p = c->ualloc.alloc(bytes, c->ualloc.user);
+        if (!*p) {
+            c->last_error = "allocator returned NULL";
+            return SGCP_ERR_OOM;
+        }
+        if ((reinterpret_cast<uintptr_t>(*p) & 255) != 0) {
+            c->ualloc.free(*p, c->ualloc.user);
+            *p = nullptr;
+            c->last_error = "allocator returned memory that is not 256-byte aligned";
+            return SGCP_ERR_ARG;
+        }
+        c->allocs.push_back(*p);
+        return SGCP_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -135,6 +154,17 @@ sgcp_status dalloc(sgcp_ctx* c, void** p, size_t bytes) {
     }
     c->allocs.push_back(*p);
     return SGCP_OK;
+}
+
+// Release one pointer obtained from dalloc.  cudaFree waits for the device; a caller's allocator
+// may hand the memory out again at once, so the context's queued work is waited for first.
+void release(sgcp_ctx* c, void* p) {
+    if (c->custom_alloc) {
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        c->ualloc.free(p, c->ualloc.user);
+    } else {
+        cudaFree(p);
+    }
 }
 
 template <typename P>
@@ -152,7 +182,7 @@ void dfree(sgcp_ctx* c, void* p) {
             c->allocs.erase(c->allocs.begin() + (long)i);
             break;
         }
-    cudaFree(p);
+    release(c, p);
 }
 
 int64_t omega_of(const sgcp_ctx* c) {
@@ -921,8 +951,10 @@ sgcp_status sgcp_params_default(sgcp_params* p) {
 }
 
 sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_factors, int32_t n_hist,
-                        const int64_t* hist_t, const void* hist_s, int64_t t0, void* cuda_stream, sgcp_ctx** out) {
+                        const int64_t* hist_t, const void* hist_s, int64_t t0, const sgcp_allocator* allocator,
+                        void* cuda_stream, sgcp_ctx** out) {
     if (!params || !init_factors || !out) return SGCP_ERR_ARG;
+    if (allocator && (!allocator->alloc || !allocator->free)) return SGCP_ERR_ARG;
     *out = nullptr;
     const sgcp_params& P = *params;
     if (P.ndim < 2 || P.ndim > 4) return SGCP_ERR_UNSUPPORTED;
@@ -959,6 +991,10 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     sgcp_ctx* c = new (std::nothrow) sgcp_ctx();
     if (!c) return SGCP_ERR_OOM;
     c->P = P;
+    if (allocator) {
+        c->ualloc = *allocator;
+        c->custom_alloc = true;
+    }
     c->ndim = P.ndim;
     c->R = P.rank;
     c->f64 = P.precision == SGCP_PREC_F64;
@@ -1081,7 +1117,7 @@ void sgcp_destroy(sgcp_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 2; ++i)
         if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
-    for (void* p : c->allocs) cudaFree(p);
+    for (void* p : c->allocs) c->custom_alloc ? c->ualloc.free(p, c->ualloc.user) : (void)cudaFree(p);
     c->allocs.clear();
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->side) cudaStreamDestroy(c->side);

@@ -70,13 +70,18 @@ def test_argument_errors_are_synchronous_without_a_gpu(sg):
     out = ctypes.c_void_p()
     arr = (ctypes.c_void_p * 3)()
     bad = sg.params((10, 20, 30), 6)           # rank not a multiple of 4
-    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_UNSUPPORTED
+    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, None, ctypes.byref(out)) == sg.ERR_UNSUPPORTED
     bad = sg.params((10, 20, 30, 4, 5)[:4], 8, precision=sg.PREC_BF16_MTTKRP)
     bad.ndim = 5
-    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_UNSUPPORTED
+    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, None, ctypes.byref(out)) == sg.ERR_UNSUPPORTED
     bad = sg.params((10, 20, 30), 8, "poisson", temporal=sg.TEMPORAL_LSQ)
-    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, ctypes.byref(out)) in (sg.ERR_ARG, sg.ERR_CUDA)
-    assert sg.sgcp_create(None, arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_ARG
+    assert sg.sgcp_create(ctypes.byref(bad), arr, 0, None, None, 0, None, None, ctypes.byref(out)) in (sg.ERR_ARG, sg.ERR_CUDA)
+    assert sg.sgcp_create(None, arr, 0, None, None, 0, None, None, ctypes.byref(out)) == sg.ERR_ARG
+    half = sg.sgcp_allocator()                 # an allocator without a free callback
+    half.alloc = sg.ALLOC_FN(lambda n, u: None)
+    good = sg.params((10, 20, 30), 8)
+    assert sg.sgcp_create(ctypes.byref(good), arr, 0, None, None, 0, ctypes.byref(half), None,
+                          ctypes.byref(out)) == sg.ERR_ARG
     assert sg.sgcp_status_string(sg.ERR_SAMPLING_LIMIT) == b"SGCP_ERR_SAMPLING_LIMIT"
     assert sg.sgcp_params_default(None) == sg.ERR_ARG
 
@@ -106,7 +111,7 @@ def test_no_cpu_fallback_when_cuda_is_missing(sg):
     out = ctypes.c_void_p()
     arr = (ctypes.c_void_p * 3)()
     p = sg.params((10, 20, 30), 8)
-    assert sg.sgcp_create(ctypes.byref(p), arr, 0, None, None, 0, None, ctypes.byref(out)) == sg.ERR_CUDA
+    assert sg.sgcp_create(ctypes.byref(p), arr, 0, None, None, 0, None, None, ctypes.byref(out)) == sg.ERR_CUDA
 
 
 def test_batch_argument_errors_are_synchronous_without_a_gpu(sg):
@@ -115,7 +120,7 @@ def test_batch_argument_errors_are_synchronous_without_a_gpu(sg):
     arr = (ctypes.c_void_p * 6)(*([1] * 6))   # non-NULL placeholders: never dereferenced on these paths
     def create(plist, opts=None):
         pa = (sg.sgcp_params * len(plist))(*plist)
-        return sg.sgcp_batch_create(len(plist), pa, arr, ctypes.byref(opts) if opts else None, None,
+        return sg.sgcp_batch_create(len(plist), pa, arr, ctypes.byref(opts) if opts else None, None, None,
                                     ctypes.byref(out))
     good = sg.params((40, 50, 60), 16)
     assert create([good, sg.params((40, 50), 16)]) == sg.ERR_UNSUPPORTED           # 2-way slice
@@ -130,5 +135,10 @@ def test_batch_argument_errors_are_synchronous_without_a_gpu(sg):
     bad_entry[0].b1log, bad_entry[0].n1, bad_entry[0].n2 = 1, 1, 1             # tile row split out of range
     opts.table, opts.n_table = bad_entry, 1
     assert create([good], opts) == sg.ERR_ARG
-    assert sg.sgcp_batch_create(0, None, arr, None, None, ctypes.byref(out)) == sg.ERR_ARG
+    assert sg.sgcp_batch_create(0, None, arr, None, None, None, ctypes.byref(out)) == sg.ERR_ARG
     assert sg.sgcp_batch_check(None) == sg.ERR_ARG
+    # an allocator needs both callbacks (checked before any device work)
+    half = sg.sgcp_allocator()
+    half.alloc = sg.ALLOC_FN(lambda n, u: None)
+    pa = (sg.sgcp_params * 1)(good)
+    assert sg.sgcp_batch_create(1, pa, arr, None, ctypes.byref(half), None, ctypes.byref(out)) == sg.ERR_ARG
