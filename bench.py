@@ -515,6 +515,7 @@ def run_native_dense(args, cfg, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ctx.check()
+    st_last = ctx.stats()
     launches = ctx.stats()["kernels_launched"] - k0
     total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     value = world * args.steps * grads_per_step * omega / total_s
@@ -572,6 +573,8 @@ def run_native_dense(args, cfg, world, rank, local):
         "config": {"workload": f"dense_gaussian_3way: 256^3 slices, R=64, gaussian, noise 1% RMS",
                    "grads_per_step": None if lsq_lbfgs else grads_per_step,
                    "solver": "LSQ temporal solve + projected L-BFGS factor solve (defaults)" if lsq_lbfgs else DENSE_SOLVER,
+                   "lbfgs_last_slice": {"iterations": st_last["epochs_f"], "evaluations": st_last["evals_f"]}
+                   if lsq_lbfgs else None,
                    "l2": "flushed between steps (256 MB write)", "precision": args.precision},
         "gpu_launches": int(launches),
         "roofline": roof,

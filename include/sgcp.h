@@ -160,6 +160,9 @@ typedef struct {
     int32_t hist_len;             /* current history window size */
     int32_t error_bits;           /* device error word (0 = none) */
     int64_t kernels_launched;     /* kernels queued by this context so far (graph nodes included) */
+    int32_t evals_f;              /* L-BFGS factor solver: objective evaluations of the last slice
+                                     (the first point plus every line-search trial); ADAM: 0 */
+    int32_t pad;
 } sgcp_stats_t;
 
 /* Device-memory provider for the state a context or a batch owns (the variables of Alg. 1 and

@@ -57,7 +57,7 @@ class sgcp_stats_t(ctypes.Structure):
     _fields_ = [("t", c_int64), ("iter", c_int64), ("F_w", c_double), ("F_f", c_double),
                 ("epochs_w", c_int32), ("epochs_f", c_int32), ("accept_w", c_uint32), ("accept_f", c_uint32),
                 ("alpha_w", c_double), ("alpha_f", c_double), ("hist_len", c_int32), ("error_bits", c_int32),
-                ("kernels_launched", c_int64)]
+                ("kernels_launched", c_int64), ("evals_f", c_int32), ("pad", c_int32)]
 
 
 class sgcp_tune_entry(ctypes.Structure):

@@ -85,10 +85,12 @@ struct sgcp_ctx {
 
     int64_t t = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [dense, sparse]
-    // L-BFGS work vectors (allocated at the first L-BFGS step)
-    void *lb_x = nullptr, *lb_g = nullptr, *lb_p = nullptr, *lb_d = nullptr;
-    std::vector<void*> lb_S, lb_Y;
-    double* lb_dot = nullptr;
+    // L-BFGS solver (optimizer SGCP_OPT_LBFGS): iterate, gradient, direction, m + 1 pair slots,
+    // their device pointer tables and the device-resident iteration state
+    void *lb_x = nullptr, *lb_g = nullptr, *lb_p = nullptr;
+    void** lb_tab = nullptr;       // [2][kLbfgsSlots]: S slots, then Y slots
+    LbfgsState* lb_state = nullptr;
+    cudaStream_t lb_stream = nullptr;   // captures the bodies of the line-search WHILE nodes
     int64_t graph_kernels[2] = {0, 0};
     // tensor-core contexts: TMA tensor map of the current dense slice (device, 128 bytes)
     bool tc = false;
@@ -448,6 +450,9 @@ sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_de
 // enqueued on c->stream; captured into a graph by build_graph.
 // ---------------------------------------------------------------------------
 template <typename T>
+sgcp_status enqueue_lbfgs(sgcp_ctx* c);
+
+template <typename T>
 sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     const int R = c->R, d = c->ndim;
     const sgcp_params& P = c->P;
@@ -533,7 +538,13 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
         }
     }
 
-    if (!with_factor) return SGCP_OK;   // the L-BFGS factor solve runs after the graph
+    if (!with_factor) return SGCP_OK;
+    if (P.optimizer == SGCP_OPT_LBFGS) {
+        // ---------------- factor matrices: projected L-BFGS (dense slices) ----------------
+        if (sgcp_status st = enqueue_lbfgs<T>(c)) return st;
+        CK(cudaMemcpyAsync(c->Abar, c->A, (size_t)c->N * esz, cudaMemcpyDeviceToDevice, c->stream), "Abar <- A");
+        return SGCP_OK;
+    }
     // ---------------- factor matrices (Alg. 4) ----------------
     SolverState* sf = c->st_f;
     const int32_t* skip = &sf->done;
@@ -620,7 +631,7 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
                 g2.sel_v[1] = SEL_A;
                 g2.skip = skip;
                 CK(launch_gram<T>(g2, c->nrows, c->side, &c->launches), "gram2");
-                CK(launch_hist_coeffs<T>(d, R, c->grams, c->SH, c->hist_len_dev, (T*)c->Bc, (T*)c->Cc, skip,
+                CK(launch_hist_coeffs<T>(d, R, c->grams, 1, c->SH, c->hist_len_dev, (T*)c->Bc, (T*)c->Cc, skip,
                                          c->side, &c->launches),
                    "hist coeffs");
                 CK(join(), "join");
@@ -641,34 +652,18 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
 // Projected L-BFGS on the factor matrices of a dense slice (the paper's
 // conclusions ask for solvers other than SGD; this one follows Nocedal &
 // Wright, "Numerical Optimization", Alg. 7.4, with a backtracking Armijo line
-// search on the projected point).  The host drives the iteration; every
-// evaluation runs in the library's kernels: the dense loss + gradient, the
-// telescoped history objective, the history / lambda gradient terms.
+// search on the projected point), enqueued into the step graph: every
+// evaluation (the dense loss + gradient, the telescoped history objective, the
+// history / lambda gradient terms) and every scalar of the recursion stay on
+// the device.  Each of the lbfgs_iters iterations is a direction kernel, the
+// first line-search trial (trial point, evaluation, Armijo test), a WHILE
+// conditional node whose body is one further trial and which runs only while
+// the Armijo test rejects, and an update kernel.
 // ---------------------------------------------------------------------------
 template <typename T>
-sgcp_status lbfgs_factor(sgcp_ctx* c) {
-    const int d = c->ndim, R = c->R, m = c->P.lbfgs_mem;
-    const int64_t N = c->N;
-    const size_t nb = (size_t)N * sizeof(T);
-    cudaStream_t st = c->stream;
-    if (!c->lb_x) {
-        void** one[] = {&c->lb_x, &c->lb_g, &c->lb_p, &c->lb_d};
-        for (void** q : one)
-            if (sgcp_status e = dalloc(c, q, nb)) return e;
-        c->lb_S.assign(m + 1, nullptr);   // m live pairs + one candidate slot
-        c->lb_Y.assign(m + 1, nullptr);
-        for (int i = 0; i <= m; ++i) {
-            if (sgcp_status e = dalloc(c, &c->lb_S[i], nb)) return e;
-            if (sgcp_status e = dalloc(c, &c->lb_Y[i], nb)) return e;
-        }
-        if (sgcp_status e = dalloc_t(c, &c->lb_dot, 4 * sizeof(double))) return e;
-    }
-    T* x = (T*)c->lb_x;
-    T* g = (T*)c->lb_g;
-    T* pd = (T*)c->lb_p;
-    T* dv = (T*)c->lb_d;
-    T* A = (T*)c->A;
-    T* G = (T*)c->G;
+sgcp_status enqueue_lbfgs(sgcp_ctx* c) {
+    const int d = c->ndim, R = c->R;
+    const size_t nb = (size_t)c->N * sizeof(T);
     const void* Aptr[4];
     void* Gptr[4];
     for (int k = 0; k < d; ++k) {
@@ -682,7 +677,7 @@ sgcp_status lbfgs_factor(sgcp_ctx* c) {
         ga.dims[k] = c->dims[k];
         ga.row_off[k] = c->row_off[k];
     }
-    ga.A = A;
+    ga.A = (const T*)c->A;
     ga.Abar = (const T*)c->Abar;
     ga.part = (T*)c->gpart;
     ga.nblk = c->gram_nblk;
@@ -693,9 +688,9 @@ sgcp_status lbfgs_factor(sgcp_ctx* c) {
     fu.R = R;
     fu.nrows = c->nrows;
     for (int k = 0; k < 4; ++k) fu.row_off[k] = c->row_off[k];
-    fu.A = A;
+    fu.A = (T*)c->A;
     fu.Abar = (const T*)c->Abar;
-    fu.G = G;
+    fu.G = (T*)c->G;
     fu.u = (T*)c->u;
     fu.v = (T*)c->v;
     fu.B = c->P.H > 0 ? (const T*)c->Bc : nullptr;
@@ -707,16 +702,17 @@ sgcp_status lbfgs_factor(sgcp_ctx* c) {
     fu.eps = c->P.adam_eps;
     fu.lower = c->lower;
     fu.rate = c->rates_f;
-    fu.skip = nullptr;
     fu.grad_only = 1;
     SolverState* sf = c->st_f;
-    // F(A) into *F and the full gradient into G
-    auto eval = [&](double* F) -> sgcp_status {
-        CK(cudaMemsetAsync(c->G, 0, nb, st), "clear G");
-        CK(cudaMemsetAsync(&sf->F_new, 0, sizeof(double), st), "clear F");
+    // F(A) into sf->F_new and the full gradient of eq. gcp_stream_objective into G, on c->stream;
+    // every kernel skips while *skip (the solve has stopped)
+    const int32_t* skip = nullptr;
+    auto eval = [&]() -> sgcp_status {
+        CK(cudaMemsetAsync(c->G, 0, nb, c->stream), "clear G");
+        CK(cudaMemsetAsync(&sf->F_new, 0, sizeof(double), c->stream), "clear F");
         sgcp_status e2 = enqueue_gradient(c, false, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, 0,
                                           SGCP_WANT_FACTORS | SGCP_WANT_LOSS, c->s, Aptr, Gptr, nullptr, &sf->F_new,
-                                          c->P.loss, nullptr, nullptr);
+                                          c->P.loss, nullptr, skip);
         if (e2) return e2;
         GramArgs<T> g6 = ga;
         g6.npairs = 6;
@@ -726,121 +722,84 @@ sgcp_status lbfgs_factor(sgcp_ctx* c) {
             g6.sel_u[i] = su[i];
             g6.sel_v[i] = sv[i];
         }
-        CK(launch_gram<T>(g6, c->nrows, st, &c->launches), "gram6");
-        CK(launch_obj_finish_f(sf, d, R, c->grams, c->SH, c->hist_len_dev, c->P.lambda, 0, c->err, nullptr, st,
+        g6.skip = skip;
+        CK(launch_gram<T>(g6, c->nrows, c->stream, &c->launches), "gram6");
+        CK(launch_obj_finish_f(sf, d, R, c->grams, c->SH, c->hist_len_dev, c->P.lambda, 0, c->err, skip, c->stream,
                                &c->launches),
            "objective");
-        if (c->P.H > 0) {
-            GramArgs<T> g2 = ga;
-            g2.npairs = 2;
-            g2.sel_u[0] = SEL_A;
-            g2.sel_v[0] = SEL_A;
-            g2.sel_u[1] = SEL_D;
-            g2.sel_v[1] = SEL_A;
-            CK(launch_gram<T>(g2, c->nrows, st, &c->launches), "gram2");
-            CK(launch_hist_coeffs<T>(d, R, c->grams, c->SH, c->hist_len_dev, (T*)c->Bc, (T*)c->Cc, nullptr, st,
+        // history coefficients from the same Grams: A'A is pair 0 and D'A pair 4 of the six
+        if (c->P.H > 0)
+            CK(launch_hist_coeffs<T>(d, R, c->grams, 4, c->SH, c->hist_len_dev, (T*)c->Bc, (T*)c->Cc, skip, c->stream,
                                      &c->launches),
                "hist coeffs");
-        }
-        CK(launch_factor_update<T>(fu, st, &c->launches), "gradient terms");
-        CK(cudaMemcpyAsync(F, &sf->F_new, sizeof(double), cudaMemcpyDeviceToHost, st), "read F");
-        CK(cudaStreamSynchronize(st), "sync");
+        fu.skip = skip;
+        CK(launch_factor_update<T>(fu, c->stream, &c->launches), "gradient terms");
         return SGCP_OK;
     };
-    auto dot = [&](const T* a, const T* b, double* out) -> sgcp_status {
-        CK(launch_dot<T>(a, b, N, c->lb_dot, st, &c->launches), "dot");
-        CK(cudaMemcpyAsync(out, c->lb_dot, sizeof(double), cudaMemcpyDeviceToHost, st), "read dot");
-        CK(cudaStreamSynchronize(st), "sync");
-        return SGCP_OK;
-    };
-    double F = 0.0;
-    CK(cudaMemcpyAsync(x, A, nb, cudaMemcpyDeviceToDevice, st), "copy x");
-    if (sgcp_status e = eval(&F)) return e;
-    CK(cudaMemcpyAsync(g, G, nb, cudaMemcpyDeviceToDevice, st), "copy g");
-    std::vector<int> order;          // ring slots, oldest first
-    std::vector<double> rho(m + 1, 0.0), alpha(m + 1, 0.0);
-    int iters = 0;
+    LbfgsArgs<T> la{};
+    la.ls = c->lb_state;
+    la.sf = sf;
+    la.A = (T*)c->A;
+    la.G = (const T*)c->G;
+    la.x = (T*)c->lb_x;
+    la.g = (T*)c->lb_g;
+    la.pd = (T*)c->lb_p;
+    la.S = (T* const*)c->lb_tab;
+    la.Y = (T* const*)(c->lb_tab + kLbfgsSlots);
+    la.n = c->N;
+    la.m = c->P.lbfgs_mem;
+    la.lower = c->lower;
+
+    if (sgcp_status e = eval()) return e;
+    CK(launch_lbfgs_begin<T>(la, c->stream, &c->launches), "lbfgs begin");
     for (int it = 0; it < c->P.lbfgs_iters; ++it) {
-        // two-loop recursion: pd <- H g
-        CK(cudaMemcpyAsync(pd, g, nb, cudaMemcpyDeviceToDevice, st), "q <- g");
-        for (int q = (int)order.size() - 1; q >= 0; --q) {
-            const int sl = order[q];
-            double sq;
-            if (sgcp_status e = dot((const T*)c->lb_S[sl], pd, &sq)) return e;
-            alpha[sl] = rho[sl] * sq;
-            CK(launch_axpby<T>(pd, (const T*)c->lb_Y[sl], -alpha[sl], 1.0, N, st, &c->launches), "axpy");
-        }
-        double gamma;
-        if (!order.empty()) {
-            const int sl = order.back();
-            double sy, yy;
-            if (sgcp_status e = dot((const T*)c->lb_S[sl], (const T*)c->lb_Y[sl], &sy)) return e;
-            if (sgcp_status e = dot((const T*)c->lb_Y[sl], (const T*)c->lb_Y[sl], &yy)) return e;
-            gamma = sy / yy;
-        } else {
-            double gg;
-            if (sgcp_status e = dot(g, g, &gg)) return e;
-            gamma = 1.0 / std::max(std::sqrt(gg), 1e-300);
-        }
-        CK(launch_axpby<T>(pd, pd, gamma, 0.0, N, st, &c->launches), "scale");
-        for (size_t q = 0; q < order.size(); ++q) {
-            const int sl = order[q];
-            double yr;
-            if (sgcp_status e = dot((const T*)c->lb_Y[sl], pd, &yr)) return e;
-            const double beta = rho[sl] * yr;
-            CK(launch_axpby<T>(pd, (const T*)c->lb_S[sl], alpha[sl] - beta, 1.0, N, st, &c->launches), "axpy");
-        }
-        // direction -pd; backtracking on the projected point
-        double step = 1.0, Fn = 0.0;
-        bool accepted = false;
-        for (int ls = 0; ls < 30; ++ls) {
-            CK(launch_project_step<T>(A, x, pd, -step, c->lower, N, st, &c->launches), "trial point");
-            if (sgcp_status e = eval(&Fn)) return e;
-            CK(cudaMemcpyAsync(dv, A, nb, cudaMemcpyDeviceToDevice, st), "d <- a");
-            CK(launch_axpby<T>(dv, x, -1.0, 1.0, N, st, &c->launches), "d <- a - x");
-            double gd;
-            if (sgcp_status e = dot(g, dv, &gd)) return e;
-            if (Fn <= F + 1e-4 * gd) {
-                accepted = true;
-                break;
-            }
-            step *= 0.5;
-        }
-        if (!accepted) {
-            CK(cudaMemcpyAsync(A, x, nb, cudaMemcpyDeviceToDevice, st), "restore");
-            break;
-        }
-        // new pair s = a_new - x (in dv), y = g_new - g
-        int sl = 0;   // a slot not holding a live pair
-        while (std::find(order.begin(), order.end(), sl) != order.end()) ++sl;
-        T* S_ = (T*)c->lb_S[sl];
-        T* Y_ = (T*)c->lb_Y[sl];
-        CK(cudaMemcpyAsync(S_, dv, nb, cudaMemcpyDeviceToDevice, st), "s");
-        CK(cudaMemcpyAsync(Y_, G, nb, cudaMemcpyDeviceToDevice, st), "y");
-        CK(launch_axpby<T>(Y_, g, -1.0, 1.0, N, st, &c->launches), "y <- g_new - g");
-        double sy, ss, yy;
-        if (sgcp_status e = dot(S_, Y_, &sy)) return e;
-        if (sgcp_status e = dot(S_, S_, &ss)) return e;
-        if (sgcp_status e = dot(Y_, Y_, &yy)) return e;
-        if (sy > 1e-12 * std::sqrt(ss) * std::sqrt(yy)) {
-            if ((int)order.size() == m) order.erase(order.begin());
-            order.push_back(sl);
-            rho[sl] = 1.0 / sy;
-        }
-        CK(cudaMemcpyAsync(x, A, nb, cudaMemcpyDeviceToDevice, st), "x <- a");
-        CK(cudaMemcpyAsync(g, G, nb, cudaMemcpyDeviceToDevice, st), "g <- g_new");
-        F = Fn;
-        ++iters;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
+        if (cs != cudaStreamCaptureStatusActive) return fail(c, SGCP_ERR_CUDA, "lbfgs: step graph not capturing");
+        // 0 at every graph launch; an Armijo test that rejects its trial raises it
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0u, cudaGraphCondAssignDefault), "conditional handle");
+        CK(launch_lbfgs_direction<T>(la, c->stream, &c->launches), "lbfgs direction");
+        // the first trial (step 1) in line: every kernel of it skips once the solve has stopped
+        skip = &c->lb_state->done;
+        CK(launch_lbfgs_trial<T>(la, c->stream, &c->launches), "lbfgs trial");
+        if (sgcp_status e = eval()) return e;
+        skip = nullptr;
+        CK(launch_lbfgs_armijo<T>(la, h, c->stream, &c->launches), "lbfgs armijo");
+        // further trials (step 1/2, 1/4, ...) only when it was rejected: a WHILE node whose body is
+        // one trial, captured on the side stream
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &nd), "capture info");
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np), "line-search node");
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+           "capture dependencies");
+        cudaStream_t main = c->stream;
+        CK(cudaStreamBeginCaptureToGraph(c->lb_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed),
+           "begin body capture");
+        c->stream = c->lb_stream;
+        sgcp_status e = SGCP_OK;
+        cudaError_t ce = launch_lbfgs_trial<T>(la, c->stream, &c->launches);
+        if (ce == cudaSuccess) e = eval();
+        if (ce == cudaSuccess && e == SGCP_OK) ce = launch_lbfgs_armijo<T>(la, h, c->stream, &c->launches);
+        c->stream = main;
+        cudaGraph_t out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->lb_stream, &out);
+        if (e) return e;
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "line-search body");
+        if (ee != cudaSuccess) return cuda_fail(c, ee, "end body capture");
+        CK(launch_lbfgs_update<T>(la, c->stream, &c->launches), "lbfgs update");
     }
-    // report the final objective and iteration count like an epoch summary
-    SolverState hs{};
-    CK(cudaMemcpy(&hs, sf, sizeof(hs), cudaMemcpyDeviceToHost), "read state");
-    hs.F_cur = F;
-    hs.epoch = iters;
-    hs.accept = 0u;
-    hs.done = 0;
-    CK(cudaMemcpy(sf, &hs, sizeof(hs), cudaMemcpyHostToDevice), "write state");
-    CK(cudaMemsetAsync(c->G, 0, nb, st), "clear G");
+    CK(launch_lbfgs_finish(c->lb_state, sf, c->stream, &c->launches), "lbfgs finish");
+    CK(cudaMemsetAsync(c->G, 0, nb, c->stream), "clear G");
     return SGCP_OK;
 }
 
@@ -849,8 +808,7 @@ sgcp_status build_graph(sgcp_ctx* c, bool sparse) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "begin capture");
     const int64_t before = c->launches;
-    const bool adam = c->P.optimizer == SGCP_OPT_ADAM;
-    sgcp_status st = c->f64 ? enqueue_step<double>(c, sparse, adam) : enqueue_step<float>(c, sparse, adam);
+    sgcp_status st = c->f64 ? enqueue_step<double>(c, sparse, true) : enqueue_step<float>(c, sparse, true);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     c->launches = before;
     if (st != SGCP_OK) {
@@ -1063,6 +1021,19 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         (st = dalloc_t(c, &c->hot_rows, c->ndim * kMaxHot * sizeof(int32_t))) ||
         (c->tc && (st = dalloc(c, &c->xmap, 128))))
         return bail(st);
+    if (P.optimizer == SGCP_OPT_LBFGS) {
+        // L-BFGS work vectors, m + 1 pair slots and their pointer table, the iteration state
+        void* tab[2 * kLbfgsSlots] = {};
+        for (int i = 0; i <= P.lbfgs_mem; ++i)
+            if ((st = dalloc(c, &tab[i], nb)) || (st = dalloc(c, &tab[kLbfgsSlots + i], nb))) return bail(st);
+        if ((st = dalloc(c, &c->lb_x, nb)) || (st = dalloc(c, &c->lb_g, nb)) || (st = dalloc(c, &c->lb_p, nb)) ||
+            (st = dalloc_t(c, &c->lb_tab, sizeof(tab))) || (st = dalloc_t(c, &c->lb_state, sizeof(LbfgsState))))
+            return bail(st);
+        if (cudaStreamCreateWithFlags(&c->lb_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(SGCP_ERR_CUDA);
+        if (cudaMemcpyAsync(c->lb_tab, tab, sizeof(tab), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)   // tab dies with this scope
+            return bail(SGCP_ERR_CUDA);
+    }
     cudaStream_t s = c->stream;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < c->ndim && e == cudaSuccess; ++k) {
@@ -1121,6 +1092,7 @@ void sgcp_destroy(sgcp_ctx* c) {
     c->allocs.clear();
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->lb_stream) cudaStreamDestroy(c->lb_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
@@ -1193,6 +1165,8 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
     const bool sparse = X->is_sparse != 0;
     if (sparse && (c->P.p + c->P.q == 0 || c->P.p_obj + c->P.q_obj == 0) && c->P.temporal != SGCP_TEMPORAL_LSQ)
         return fail(c, SGCP_ERR_ARG, "step: sparse slices need p + q > 0 and p_obj + q_obj > 0");
+    if (sparse && c->P.optimizer == SGCP_OPT_LBFGS)
+        return fail(c, SGCP_ERR_UNSUPPORTED, "step: the L-BFGS factor solver needs dense slices");
     if (sgcp_status st = load_slice(c, X, t, false)) return st;
     CK(launch_write_desc(c->slice_dev, c->cur, c->stream, &c->launches), "slice descriptor");
     if (!sparse)
@@ -1202,12 +1176,6 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
         if (sgcp_status st = build_graph(c, sparse)) return st;
     CK(cudaGraphLaunch(c->graph[gi], c->stream), "graph launch");
     c->launches += c->graph_kernels[gi];
-    if (c->P.optimizer == SGCP_OPT_LBFGS) {
-        if (sparse) return fail(c, SGCP_ERR_UNSUPPORTED, "step: the L-BFGS factor solver needs dense slices");
-        sgcp_status st = c->f64 ? lbfgs_factor<double>(c) : lbfgs_factor<float>(c);
-        if (st) return st;
-        CK(cudaMemcpyAsync(c->Abar, c->A, (size_t)c->N * c->esz, cudaMemcpyDeviceToDevice, c->stream), "Abar <- A");
-    }
     // reservoir update of the history window (Alg. 1), decided on the host from t alone
     if (c->P.H > 0) {
         int slot = -1;
@@ -1304,6 +1272,7 @@ sgcp_status sgcp_stats(sgcp_ctx* c, sgcp_stats_t* out) {
     out->hist_len = (int32_t)c->hist_t.size();
     out->error_bits = bits;
     out->kernels_launched = c->launches;
+    out->evals_f = c->P.optimizer == SGCP_OPT_LBFGS ? f.evals : 0;
     return st;
 }
 

@@ -147,7 +147,7 @@ struct SolverState {
     int32_t done;      // set once the estimate is <= tol (Alg. 3/4 loop test)
     uint32_t accept;   // bit e = epoch e accepted
     uint32_t ticket;   // last-block counter (epoch end, fused temporal step)
-    int32_t pad;
+    int32_t evals;     // objective evaluations of the last L-BFGS factor solve (0 for ADAM)
     double b1pow;      // beta1^i, i = iterations accepted before the current epoch
     double b2pow;      // beta2^i
 };

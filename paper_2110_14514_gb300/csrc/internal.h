@@ -160,10 +160,12 @@ struct FactorUpdateArgs {
 
 template <typename T>
 cudaError_t launch_gram(const GramArgs<T>& a, int64_t nrows, cudaStream_t st, int64_t* launches);
-// B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H from grams [P_n = A'A, E_n = D'A].
+// B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H from grams [pair][ndim][R][R]: P_n = A'A at
+// pair 0, E_n = D'A at pair e_pair.
 template <typename T>
-cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
-                               T* B, T* C, const int32_t* skip, cudaStream_t st, int64_t* launches);
+cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, int e_pair, const double* SH,
+                               const int32_t* hist_len, T* B, T* C, const int32_t* skip, cudaStream_t st,
+                               int64_t* launches);
 template <typename T>
 cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, int64_t* launches);
 
@@ -211,17 +213,63 @@ template <typename T>
 cudaError_t launch_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_len, int slot, int64_t t, int len,
                                const T* s, cudaStream_t stream, int64_t* launches);
 
-// Vector kernels of the L-BFGS factor solver (vectors of n elements of T).
+// ---------------------------------------------------------------------------
+// Projected L-BFGS factor solver, driven on the device (k_solver.cu).  The
+// iteration's scalars live in LbfgsState; one slice's solve is captured in the
+// step graph with the line search as a WHILE conditional node whose body the
+// Armijo test ends (no host round trip).
+// ---------------------------------------------------------------------------
+constexpr int kLbfgsSlots = 65;   // lbfgs_mem <= 64 live pairs plus one candidate slot
+
+struct LbfgsState {
+    double F;        // objective at the current iterate x
+    double step;     // trial step of the current line search
+    double gamma;    // s'y / y'y of the newest stored pair (initial Hessian scaling)
+    int32_t npairs;  // stored pairs (order[0..npairs), oldest first)
+    int32_t trial;   // trials made in the current line search
+    int32_t done;    // set when a line search found no acceptable step: later iterations do nothing
+    int32_t accepted;
+    int32_t iters;   // accepted iterations of this solve
+    int32_t evals;   // objective evaluations of this solve
+    int32_t order[kLbfgsSlots];
+    double rho[kLbfgsSlots];
+};
+
 template <typename T>
-cudaError_t launch_dot(const T* a, const T* b, int64_t n, double* out, cudaStream_t stream, int64_t* launches);
-// y = alpha_host * x + beta * y  (alpha from the host)
+struct LbfgsArgs {
+    LbfgsState* ls;
+    SolverState* sf;    // F_new holds the objective of the last evaluation
+    T* A;               // the context's factors (the evaluation point)
+    const T* G;         // full gradient at A (written by the evaluation)
+    T* x;               // current iterate
+    T* g;               // gradient at x
+    T* pd;              // search direction H g
+    T* const* S;        // device table of kLbfgsSlots pair vectors s
+    T* const* Y;        // device table of kLbfgsSlots pair vectors y
+    int64_t n;          // sum I_k * R
+    int m;              // memory (live pairs kept)
+    double lower;       // projection bound l
+};
+
+// After the first evaluation: x <- A, g <- G, F <- F(A), empty memory.
 template <typename T>
-cudaError_t launch_axpby(T* y, const T* x, double alpha, double beta, int64_t n, cudaStream_t stream,
-                         int64_t* launches);
-// out = max(x + step * p, lower)
+cudaError_t launch_lbfgs_begin(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches);
+// pd <- H g (two-loop recursion); step <- 1 for the line search.  Nothing once the solve stopped.
 template <typename T>
-cudaError_t launch_project_step(T* out, const T* x, const T* p, double step, double lower, int64_t n,
-                                cudaStream_t stream, int64_t* launches);
+cudaError_t launch_lbfgs_direction(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches);
+// Trial point A <- max(x - step pd, l).
+template <typename T>
+cudaError_t launch_lbfgs_trial(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches);
+// Armijo test of the evaluated trial point: on rejection halves the step and sets the line
+// search's WHILE handle to 1 (another trial, at most 30), else to 0.
+template <typename T>
+cudaError_t launch_lbfgs_armijo(const LbfgsArgs<T>& a, cudaGraphConditionalHandle h, cudaStream_t st,
+                                int64_t* launches);
+// After the line search: store the pair, move to the trial point; or restore x and stop.
+template <typename T>
+cudaError_t launch_lbfgs_update(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches);
+// Report the solve like an epoch summary: F_cur <- F, epoch <- iterations.
+cudaError_t launch_lbfgs_finish(LbfgsState* ls, SolverState* sf, cudaStream_t st, int64_t* launches);
 
 // Small helpers.
 template <typename T>

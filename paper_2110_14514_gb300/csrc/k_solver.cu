@@ -16,8 +16,12 @@
 // (telescoping over the Hadamard factors) so nothing cancels when A ~ Abar.
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "sgcp.h"
+
+namespace cg = cooperative_groups;
 
 namespace sgcp {
 
@@ -166,22 +170,23 @@ cudaError_t launch_gram(const GramArgs<T>& a, int64_t, cudaStream_t st, int64_t*
 
 // ---------------------------------------------------------------------------
 // B_k = Gamma_k * S_H and C_k = (Gamma_k - Gammabar_k) * S_H  (float outputs)
-// grams = [P (ndim x R x R) | E (ndim x R x R)], P_n = A'A, E_n = D'A.
+// grams = [pairs][ndim][R][R]: P_n = A'A at pair 0, E_n = D'A at pair e_pair.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
-                              T* B, T* C, const int32_t* skip) {
+__global__ void k_hist_coeffs(int ndim, int R, const double* grams, int e_pair, const double* SH,
+                              const int32_t* hist_len, T* B, T* C, const int32_t* skip) {
     if (skip && *skip) return;
     const int RR = R * R;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= RR) return;
-    hist_coeff_elem<T>(ndim, RR, grams, grams + (int64_t)ndim * RR, SH, i, *hist_len > 0, B, C);
+    hist_coeff_elem<T>(ndim, RR, grams, grams + (int64_t)e_pair * ndim * RR, SH, i, *hist_len > 0, B, C);
 }
 
 template <typename T>
-cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
-                               T* B, T* C, const int32_t* skip, cudaStream_t st, int64_t* launches) {
-    k_hist_coeffs<T><<<(R * R + 127) / 128, 128, 0, st>>>(ndim, R, grams, SH, hist_len, B, C, skip);
+cudaError_t launch_hist_coeffs(int ndim, int R, const double* grams, int e_pair, const double* SH,
+                               const int32_t* hist_len, T* B, T* C, const int32_t* skip, cudaStream_t st,
+                               int64_t* launches) {
+    k_hist_coeffs<T><<<(R * R + 127) / 128, 128, 0, st>>>(ndim, R, grams, e_pair, SH, hist_len, B, C, skip);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -686,7 +691,7 @@ cudaError_t launch_obj_finish_w(SolverState* st, const T* s, int R, double mu, i
     return cudaGetLastError();
 }
 
-__global__ void k_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
+__global__ void __launch_bounds__(1024) k_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
                                const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip) {
     if (skip && *skip) return;
     obj_finish_f_block(st, ndim, R, grams, SH, *hist_len > 0, lam, set_cur, err);
@@ -695,7 +700,7 @@ __global__ void k_obj_finish_f(SolverState* st, int ndim, int R, const double* g
 cudaError_t launch_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
                                 const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip,
                                 cudaStream_t stream, int64_t* launches) {
-    k_obj_finish_f<<<1, 256, 0, stream>>>(st, ndim, R, grams, SH, hist_len, lam, set_cur, err, skip);
+    k_obj_finish_f<<<1, 1024, 0, stream>>>(st, ndim, R, grams, SH, hist_len, lam, set_cur, err, skip);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -809,69 +814,325 @@ cudaError_t launch_hist_update(int R, T* s_hist, int64_t* h_dev, int32_t* hist_l
 }
 
 // ---------------------------------------------------------------------------
-// L-BFGS vector kernels
+// Projected L-BFGS on the device (Nocedal & Wright, "Numerical Optimization",
+// Alg. 7.4 two-loop recursion; backtracking Armijo line search on the
+// projected point).  The vectors are the concatenated factor matrices
+// (n = sum I_k R elements, L2-resident for the dense workloads).  The
+// recursion, the Armijo test and the pair update each run as one cluster of
+// kLbCluster CTAs (one per SM): a pass over the vectors is spread over the
+// cluster's threads, and every dot product is reduced per CTA and then across
+// the cluster through distributed shared memory, in a fixed order, so that
+// every CTA holds the same value and no scalar leaves the device.  One CTA
+// alone was limited to ~15 GB/s by its outstanding loads (~40 us per pass at
+// n = 49152).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_dot(const T* a, const T* b, int64_t n, double* out) {
-    __shared__ double red[32];
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)a[i] * (double)b[i];
+constexpr int kLbThreads = 1024;
+constexpr int kLbCluster = 8;
+constexpr int kLbUnroll = 8;
+
+// Sum of v over the whole cluster, returned to every thread of every CTA (same value, same
+// order everywhere).  red: 32 doubles, part: 1 double, both in shared memory.
+__device__ double lb_cluster_sum(double v, double* red, double* part) {
+    cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(SGCP_FULL_MASK, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(SGCP_FULL_MASK, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-        atomicAdd(out, t);
+        *part = t;
+    }
+    cl.sync();
+    double tot = 0.0;
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) tot += *cl.map_shared_rank(part, r);
+    cl.sync();   // every CTA has read every part before any part is written again
+    return tot;
+}
+
+// First element and stride of this thread in a cluster-wide pass.
+__device__ __forceinline__ int64_t lb_first() {
+    return (int64_t)cg::this_cluster().block_rank() * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ int64_t lb_stride() { return (int64_t)kLbCluster * blockDim.x; }
+__device__ __forceinline__ bool lb_leader() { return cg::this_cluster().block_rank() == 0 && threadIdx.x == 0; }
+
+// pd <- c x + pd (x == nullptr: pd <- c pd), returning w'pd of the updated pd.  A thread's
+// kLbUnroll elements are loaded before the first store (the pointers do not alias).  Products
+// are summed per thread in T (double runs at ~1/64 of the float rate on GB300) and across
+// threads in double.
+template <typename T>
+__device__ double lb_axpy_dot(int64_t n, double* red, double* part, T c, const T* __restrict__ x,
+                              T* __restrict__ pd, const T* __restrict__ w) {
+    T acc = T(0);
+    const int64_t S = lb_stride();
+    for (int64_t base = lb_first(); base < n; base += kLbUnroll * S) {
+        T xv[kLbUnroll], pv[kLbUnroll], wv[kLbUnroll];
+#pragma unroll
+        for (int u = 0; u < kLbUnroll; ++u) {
+            const int64_t i = base + u * S;
+            const bool in = i < n;
+            xv[u] = (in && x) ? x[i] : T(0);
+            pv[u] = in ? pd[i] : T(0);
+            wv[u] = in ? w[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kLbUnroll; ++u) {
+            const int64_t i = base + u * S;
+            const T v = x ? c * xv[u] + pv[u] : c * pv[u];
+            if (i < n) pd[i] = v;
+            acc += wv[u] * v;
+        }
+    }
+    return lb_cluster_sum((double)acc, red, part);
+}
+
+// pd <- g, returning w'g.
+template <typename T>
+__device__ double lb_copy_dot(int64_t n, double* red, double* part, const T* __restrict__ g, T* __restrict__ pd,
+                              const T* __restrict__ w) {
+    T acc = T(0);
+    const int64_t S = lb_stride();
+    for (int64_t base = lb_first(); base < n; base += kLbUnroll * S) {
+        T gv[kLbUnroll], wv[kLbUnroll];
+#pragma unroll
+        for (int u = 0; u < kLbUnroll; ++u) {
+            const int64_t i = base + u * S;
+            gv[u] = i < n ? g[i] : T(0);
+            wv[u] = i < n ? w[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kLbUnroll; ++u) {
+            const int64_t i = base + u * S;
+            if (i < n) pd[i] = gv[u];
+            acc += wv[u] * gv[u];
+        }
+    }
+    return lb_cluster_sum((double)acc, red, part);
+}
+
+template <typename T>
+__global__ void __cluster_dims__(kLbCluster, 1, 1) __launch_bounds__(kLbThreads) k_lbfgs_begin(const LbfgsArgs<T> a) {
+    for (int64_t i = lb_first(); i < a.n; i += lb_stride()) {
+        a.x[i] = a.A[i];
+        a.g[i] = a.G[i];
+    }
+    if (lb_leader()) {
+        LbfgsState* ls = a.ls;
+        ls->F = a.sf->F_new;
+        ls->npairs = 0;
+        ls->done = 0;
+        ls->iters = 0;
+        ls->evals = 1;
+        ls->accepted = 0;
+        ls->trial = 0;
+        ls->gamma = 1.0;
     }
 }
 
 template <typename T>
-cudaError_t launch_dot(const T* a, const T* b, int64_t n, double* out, cudaStream_t stream, int64_t* launches) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), stream);
-    if (e != cudaSuccess) return e;
-    int64_t want = (n + 255) / 256;
-    const int64_t cap = 2LL * solver_num_sms();
-    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_dot<T><<<blocks, 256, 0, stream>>>(a, b, n, out);
+cudaError_t launch_lbfgs_begin(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches) {
+    k_lbfgs_begin<T><<<kLbCluster, kLbThreads, 0, st>>>(a);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// pd <- H g by the two-loop recursion over the stored pairs, newest first then oldest first,
+// with H_0 = gamma I (gamma = s'y / y'y of the newest pair, 1 / ||g|| without pairs).  Each
+// update of pd shares its pass with the dot product that the next step needs.
+template <typename T>
+__global__ void __cluster_dims__(kLbCluster, 1, 1) __launch_bounds__(kLbThreads)
+    k_lbfgs_direction(const LbfgsArgs<T> a) {
+    __shared__ double red[32];
+    __shared__ double part;
+    __shared__ double alpha[kLbfgsSlots];   // the same values in every CTA
+    const LbfgsState* ls = a.ls;
+    if (ls->done) return;
+    const int np = ls->npairs;
+    T* pd = a.pd;
+    const T* g = a.g;
+    // first loop, newest pair first: q <- q - alpha_k y_k with alpha_k = rho_k s_k'q
+    double dot = lb_copy_dot<T>(a.n, red, &part, g, pd, np > 0 ? a.S[ls->order[np - 1]] : g);
+    for (int q = np - 1; q >= 0; --q) {
+        const int sl = ls->order[q];
+        const double al = ls->rho[sl] * dot;
+        if (threadIdx.x == 0) alpha[sl] = al;
+        const T* y = a.Y[sl];
+        const T* sn = q > 0 ? a.S[ls->order[q - 1]] : y;   // (the last step's dot is not used)
+        dot = lb_axpy_dot<T>(a.n, red, &part, (T)(-al), y, pd, sn);
+    }
+    // r = gamma q (gamma = 1 / ||g|| without pairs: dot = g'g then); the same pass forms
+    // y_oldest' r for the second loop
+    const double gamma = np > 0 ? ls->gamma : 1.0 / fmax(sqrt(dot), 1e-300);
+    dot = lb_axpy_dot<T>(a.n, red, &part, (T)gamma, nullptr, pd, np > 0 ? a.Y[ls->order[0]] : g);
+    // (alpha[] was written before the cluster barriers of the passes above)
+    // second loop, oldest pair first: r <- r + (alpha_k - rho_k y_k'r) s_k
+    for (int q = 0; q < np; ++q) {
+        const int sl = ls->order[q];
+        const T* sv = a.S[sl];
+        dot = lb_axpy_dot<T>(a.n, red, &part, (T)(alpha[sl] - ls->rho[sl] * dot), sv, pd,
+                             q + 1 < np ? a.Y[ls->order[q + 1]] : sv);
+    }
+    if (lb_leader()) {
+        LbfgsState* lw = a.ls;
+        lw->step = 1.0;
+        lw->trial = 0;
+        lw->accepted = 0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_lbfgs_direction(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches) {
+    k_lbfgs_direction<T><<<kLbCluster, kLbThreads, 0, st>>>(a);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
 
 template <typename T>
-__global__ void k_axpby(T* y, const T* x, double alpha, double beta, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
-}
-
-template <typename T>
-cudaError_t launch_axpby(T* y, const T* x, double alpha, double beta, int64_t n, cudaStream_t stream,
-                         int64_t* launches) {
-    int64_t want = (n + 255) / 256;
-    const int64_t cap = 4LL * solver_num_sms();
-    const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_axpby<T><<<blocks, 256, 0, stream>>>(y, x, alpha, beta, n);
-    if (launches) *launches += 1;
-    return cudaGetLastError();
-}
-
-template <typename T>
-__global__ void k_project_step(T* out, const T* x, const T* p, double step, double lower, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)x[i] + step * (double)p[i];
-        out[i] = (T)(v < lower ? lower : v);
+__global__ void k_lbfgs_trial(const LbfgsArgs<T> a) {
+    if (a.ls->done) return;
+    const T step = (T)a.ls->step;    // a power of two: exact in either type
+    const T lower = (T)a.lower;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T v = a.x[i] - step * a.pd[i];
+        a.A[i] = v < lower ? lower : v;
     }
 }
 
 template <typename T>
-cudaError_t launch_project_step(T* out, const T* x, const T* p, double step, double lower, int64_t n,
-                                cudaStream_t stream, int64_t* launches) {
-    int64_t want = (n + 255) / 256;
+cudaError_t launch_lbfgs_trial(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches) {
+    int64_t want = (a.n + 255) / 256;
     const int64_t cap = 4LL * solver_num_sms();
     const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    k_project_step<T><<<blocks, 256, 0, stream>>>(out, x, p, step, lower, n);
+    k_lbfgs_trial<T><<<blocks, 256, 0, st>>>(a);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// Armijo condition on the projected trial point: F(a+) <= F(x) + 1e-4 g'(a+ - x).  A rejected
+// trial halves the step and sets the handle of the line search's WHILE node to 1 (another trial)
+// while fewer than 30 trials were made; an accepted or last trial sets it to 0.
+template <typename T>
+__global__ void __cluster_dims__(kLbCluster, 1, 1) __launch_bounds__(kLbThreads)
+    k_lbfgs_armijo(const LbfgsArgs<T> a, cudaGraphConditionalHandle h) {
+    __shared__ double red[32];
+    __shared__ double part;
+    if (a.ls->done) return;   // the solve has stopped: the handle keeps its launch value 0
+    T acc = T(0);
+    const int64_t S = lb_stride();
+    for (int64_t base = lb_first(); base < a.n; base += kLbUnroll * S) {
+        T gv[kLbUnroll], dv[kLbUnroll];
+#pragma unroll
+        for (int u = 0; u < kLbUnroll; ++u) {
+            const int64_t i = base + u * S;
+            const bool in = i < a.n;
+            gv[u] = in ? a.g[i] : T(0);
+            dv[u] = in ? a.A[i] - a.x[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kLbUnroll; ++u) acc += gv[u] * dv[u];
+    }
+    const double gd = lb_cluster_sum((double)acc, red, &part);
+    if (lb_leader()) {
+        LbfgsState* ls = a.ls;
+        const double Fn = a.sf->F_new;
+        ls->evals += 1;
+        if (Fn <= ls->F + 1e-4 * gd) {
+            ls->accepted = 1;
+            cudaGraphSetConditional(h, 0u);
+        } else {
+            ls->step *= 0.5;
+            ls->trial += 1;
+            cudaGraphSetConditional(h, ls->trial < 30 ? 1u : 0u);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_lbfgs_armijo(const LbfgsArgs<T>& a, cudaGraphConditionalHandle h, cudaStream_t st,
+                                int64_t* launches) {
+    k_lbfgs_armijo<T><<<kLbCluster, kLbThreads, 0, st>>>(a, h);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// After a line search: on acceptance store s = a+ - x, y = g(a+) - g in a free slot (kept when
+// s'y > 1e-12 ||s|| ||y||; the oldest pair leaves when m are stored) and move to a+; without an
+// acceptable step restore A <- x and stop the solve.
+template <typename T>
+__global__ void __cluster_dims__(kLbCluster, 1, 1) __launch_bounds__(kLbThreads) k_lbfgs_update(const LbfgsArgs<T> a) {
+    __shared__ double red[32];
+    __shared__ double part;
+    const LbfgsState* ls = a.ls;
+    // every CTA reads the state before the leader may write it (the barrier below), so that all
+    // CTAs take the same branches and meet at the same cluster barriers
+    const int done = ls->done, accepted = ls->accepted, np = ls->npairs;
+    int sl = 0;                  // the first slot not holding a stored pair (same in every thread)
+    for (bool used = true; used;) {
+        used = false;
+        for (int q = 0; q < np; ++q) used = used || ls->order[q] == sl;
+        if (used) ++sl;
+    }
+    cg::this_cluster().sync();
+    if (done) return;
+    if (!accepted) {
+        for (int64_t i = lb_first(); i < a.n; i += lb_stride()) a.A[i] = a.x[i];
+        if (lb_leader()) a.ls->done = 1;
+        return;
+    }
+    T* sv = a.S[sl];
+    T* yv = a.Y[sl];
+    T sy = T(0), ss = T(0), yy = T(0);
+    const int64_t S = lb_stride();
+    for (int64_t i = lb_first(); i < a.n; i += S) {
+        const T An = a.A[i], Gn = a.G[i];
+        const T si = An - a.x[i], yi = Gn - a.g[i];
+        sv[i] = si;
+        yv[i] = yi;
+        a.x[i] = An;
+        a.g[i] = Gn;
+        sy += si * yi;
+        ss += si * si;
+        yy += yi * yi;
+    }
+    const double sy_c = lb_cluster_sum((double)sy, red, &part);
+    const double ss_c = lb_cluster_sum((double)ss, red, &part);
+    const double yy_c = lb_cluster_sum((double)yy, red, &part);
+    if (lb_leader()) {
+        LbfgsState* lw = a.ls;
+        if (sy_c > 1e-12 * sqrt(ss_c) * sqrt(yy_c)) {
+            int n2 = np;
+            if (n2 == a.m) {
+                for (int q = 1; q < n2; ++q) lw->order[q - 1] = lw->order[q];
+                n2 -= 1;
+            }
+            lw->order[n2] = sl;
+            lw->npairs = n2 + 1;
+            lw->rho[sl] = 1.0 / sy_c;
+            lw->gamma = sy_c / yy_c;
+        }
+        lw->F = a.sf->F_new;
+        lw->iters += 1;
+    }
+}
+
+template <typename T>
+cudaError_t launch_lbfgs_update(const LbfgsArgs<T>& a, cudaStream_t st, int64_t* launches) {
+    k_lbfgs_update<T><<<kLbCluster, kLbThreads, 0, st>>>(a);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+__global__ void k_lbfgs_finish(const LbfgsState* ls, SolverState* sf) {
+    sf->F_cur = ls->F;
+    sf->epoch = ls->iters;
+    sf->evals = ls->evals;
+    sf->accept = 0u;
+    sf->done = 0;
+}
+
+cudaError_t launch_lbfgs_finish(LbfgsState* ls, SolverState* sf, cudaStream_t st, int64_t* launches) {
+    k_lbfgs_finish<<<1, 1, 0, st>>>(ls, sf);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
@@ -894,7 +1155,7 @@ cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, in
 
 #define SGCP_INST(T)                                                                                                  \
     template cudaError_t launch_gram<T>(const GramArgs<T>&, int64_t, cudaStream_t, int64_t*);                        \
-    template cudaError_t launch_hist_coeffs<T>(int, int, const double*, const double*, const int32_t*, T*, T*,       \
+    template cudaError_t launch_hist_coeffs<T>(int, int, const double*, int, const double*, const int32_t*, T*, T*,  \
                                                const int32_t*, cudaStream_t, int64_t*);                              \
     template cudaError_t launch_factor_update<T>(const FactorUpdateArgs<T>&, cudaStream_t, int64_t*);                \
     template cudaError_t launch_epoch_end<T>(SolverState*, int64_t, T*, T*, T*, T*, T*, T*, int, double, double,     \
@@ -908,10 +1169,12 @@ cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, in
     template cudaError_t launch_lsq_solve<T>(int, int, const double*, const T*, double, double, T*, double*, int*,   \
                                              cudaStream_t, int64_t*);                                                 \
     template cudaError_t launch_copy<T>(T*, const T*, int64_t, cudaStream_t, int64_t*);                          \
-    template cudaError_t launch_dot<T>(const T*, const T*, int64_t, double*, cudaStream_t, int64_t*);              \
-    template cudaError_t launch_axpby<T>(T*, const T*, double, double, int64_t, cudaStream_t, int64_t*);           \
-    template cudaError_t launch_project_step<T>(T*, const T*, const T*, double, double, int64_t, cudaStream_t,     \
+    template cudaError_t launch_lbfgs_begin<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                      \
+    template cudaError_t launch_lbfgs_direction<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                  \
+    template cudaError_t launch_lbfgs_trial<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                      \
+    template cudaError_t launch_lbfgs_armijo<T>(const LbfgsArgs<T>&, cudaGraphConditionalHandle, cudaStream_t,     \
                                                 int64_t*);                                                           \
+    template cudaError_t launch_lbfgs_update<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                     \
     template cudaError_t launch_hist_update<T>(int, T*, int64_t*, int32_t*, int, int64_t, int, const T*,            \
                                                cudaStream_t, int64_t*);
 

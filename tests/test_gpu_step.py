@@ -259,3 +259,39 @@ def test_dense_3way_fp32_lbfgs_decreases_the_objective(sg):
     F1 = solver.full_objective(Xo, [a.cpu().numpy().astype(np.float64) for a in A1], s1.cpu().numpy(), A0, [], [], P)
     assert st["epochs_f"] >= 1 and F1 < F0
     assert abs(st["F_f"] - F1) <= 1e-4 * abs(F1)
+
+
+def test_lbfgs_step_is_one_asynchronous_graph(sg):
+    """The L-BFGS factor solve runs inside the step's graph (line searches as device-side WHILE
+    loops): with a 0.2 s sleep kernel queued ahead of it on the context stream, sgcp_step returns
+    while the stream is still busy, i.e. without waiting for any result on the host; the step
+    then gives the same factors as a step taken on an idle stream."""
+    import time
+    cfg = S.workload("dense_gaussian_2way")
+    A0 = S.init_factors(cfg)
+    X1, X2 = S.dense_slice(cfg, 1)[0], S.dense_slice(cfg, 2)[0]
+    kw = dict(H=2, lam=0.05, lbfgs_iters=6, lbfgs_mem=3, seed=4)
+    p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=sg.PREC_F64, temporal=sg.TEMPORAL_LSQ,
+                  optimizer=sg.OPT_LBFGS, **kw)
+    with sg.Context(p, [dev(a) for a in A0]) as ref:
+        ref.step(X=dev(X1))
+        ref.step(X=dev(X2))
+        Ar, sr, _ = ref.factors()
+        st_r = ref.stats()
+    with sg.Context(p, [dev(a) for a in A0]) as ctx:
+        ctx.step(X=dev(X1))                 # builds the graph
+        ctx.check()
+        x2 = dev(X2)
+        with torch.cuda.stream(ctx.stream):
+            torch.cuda._sleep(int(0.2 * 2.0e9))
+        t0 = time.perf_counter()
+        ctx.step(X=x2)
+        host_s = time.perf_counter() - t0
+        busy = not ctx.stream.query()
+        A, s, _ = ctx.factors()
+        st = ctx.stats()
+    assert busy and host_s < 0.1, host_s
+    assert st["epochs_f"] == st_r["epochs_f"] >= 1
+    for a, b in zip(A, Ar):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
+    assert rel(s.cpu().numpy(), sr.cpu().numpy()) < 1e-12
