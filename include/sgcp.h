@@ -291,7 +291,34 @@ sgcp_status sgcp_gradient_sparse_noalloc(const sgcp_params* params, int64_t nnz,
                                          const sgcp_grad_opts* opts, float* const* G_out, float* gs_out,
                                          double* f_out, int32_t* err_out, void* cuda_stream);
 
-/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
+/* Result of a warm start: the final estimate of the stacked objective, the epochs run, and bit e
+ * set when epoch e was accepted. */
+typedef struct {
+    double F;
+    int32_t epochs;
+    uint32_t accept;
+} sgcp_warm_stats;
+
+/* Warm start (Sec. 4.4: the initial factor matrices come from a static fit of an initial set of
+ * slices; Sec. 6: every experiment starts that way and lets those slices form the first history
+ * window).  Fits the first n slices X[0..n-1] (host array of slices, each dense or each sparse,
+ * device or host data as in sgcp_step) stacked as a (d+1)-way tensor whose last mode indexes the
+ * slices, that mode's factor matrix S (n x R) holding the slices' temporal weights: GCP-SGD with
+ * the factor solver's settings (kappa_f epochs of tau_f ADAM iterations at alpha_f, rollback of
+ * rejected epochs, tol_f, lambda on every matrix of the stack including S), starting from the
+ * context's current factors and S_init (device, n x R; NULL = all ones).  Dense slices use the
+ * exact gradient and objective; sparse slices are sampled per slice (p + q gradient samples and
+ * p_obj + q_obj objective samples each, slice h at time index h + 1).
+ * Afterwards the context stands at t = n: its factor matrices are the fit, the history window
+ * holds S_h of the slices that the reservoir rule of Alg. 1 keeps as h = 1..n enter in order,
+ * s is S_n, and the next sgcp_step processes slice n + 1.  S_out (device, n x R, may be NULL)
+ * receives S; stats_out (host, may be NULL) the result.
+ * Needs a context that has processed no slice and was created without a history window.
+ * Synchronises the context stream (the call returns when the fit is done). */
+sgcp_status sgcp_warm_start(sgcp_ctx* ctx, int32_t n, const sgcp_slice* X, const void* S_init, void* S_out,
+                            sgcp_warm_stats* stats_out);
+
+/* Process the next slice: one pass of the loop body of Alg. 1 (temporal/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
  * solve, factor solve, reservoir history update, Abar <- A).  Asynchronous;
  * the whole solver sequence runs as CUDA graphs on the context stream. */
 sgcp_status sgcp_step(sgcp_ctx* ctx, const sgcp_slice* X_t);

@@ -399,3 +399,92 @@ class OnlineGCP:
         self.Abar = [a.copy() for a in A]
         self.s = s
         return {"F_w": F_w, "F_f": F_f, "s": s}
+
+
+# ----------------------------------------------------------------------------
+# Warm start: static GCP-SGD on the first slices stacked as a (d+1)-way tensor
+# (Sec. 4.4: the initial factors come from a static fit of an initial set of
+# slices; Sec. 6: every experiment starts from such a warm start, whose slices
+# also form the initial history window).
+# ----------------------------------------------------------------------------
+def stacked_loss_gradient(slices, A, S, P, draw, t0=1):
+    """Gradient of sum_h f(X_h, M_h), M_h = [[S_h; A^(1..d)]], the loss of the (d+1)-way tensor whose
+    last mode indexes the slices, with S (n x R) that mode's factor matrix:
+    dF/dA^(k) = sum_h Y_h(k) Z_k diag(S_h) and dF/dS_h = Z' vec(Y_h), one slice at a time.
+    Sparse slices are sampled per slice (strata: slice x {nonzero, zero}; p + q samples each, slice
+    h with time index t0 + h).  Returns (list of d gradients, n x R gradient of S)."""
+    G = [np.zeros(np.shape(a)) for a in A]
+    GS = np.zeros(np.shape(S))
+    for h, X in enumerate(slices):
+        Gh, gsh = loss_gradient(X, S[h], A, P, t0 + h, draw, temporal=False)
+        for k in range(len(A)):
+            G[k] += Gh[k]
+        GS[h] = gsh
+    return G, GS
+
+
+def stacked_objective(slices, A, S, P, t0=1):
+    """sum_h (sampled or exact) loss of slice h at (A, S_h) + lambda/2 (sum_k ||A^(k)||^2 + ||S||^2):
+    the stacked problem regularises every factor matrix, the slice mode's included."""
+    F = 0.0
+    for h, X in enumerate(slices):
+        F += _loss_estimate(X, S[h], A, P, t0 + h, temporal=False)
+    return F + gcp.regularization_objective(list(A) + [S], np.zeros(1), P.lam, 0.0)
+
+
+def static_gcp_sgd(slices, A0, S0, P, decisions=None, log=None, t0=1):
+    """GCP-SGD on the stacked tensor: the epoch / ADAM / rollback loop of Alg. 4 (Alg. 2 steps,
+    kappa_f epochs of tau_f iterations, rate alpha_f) over the variables (A^(1), ..., A^(d), S),
+    with no history term.  Returns (A, S, F)."""
+    log = [] if log is None else log
+    A = [np.array(a, np.float64, copy=True) for a in A0]
+    S = np.array(S0, np.float64, copy=True)
+    allv = A + [S]
+    adam = Adam(P.alpha_f, P.beta1, P.beta2, P.adam_eps, P.lower_bound(), P.alpha_decay)
+    a = _flat(allv)
+    adam.init(a)
+    F = stacked_objective(slices, A, S, P, t0)
+    i = 0
+    draw = 0          # never rolled back (R-draw): a re-run epoch draws fresh samples
+    epoch = 0
+    while F > P.tol_f and epoch < P.kappa_f:
+        F_old = F
+        for _ in range(P.tau_f):
+            cur = _unflat(a, allv)
+            G, GS = stacked_loss_gradient(slices, cur[:-1], cur[-1], P, draw, t0)
+            g = _flat([Gk + P.lam * ak for Gk, ak in zip(G, cur[:-1])] + [GS + P.lam * cur[-1]])
+            a = adam.step(a, g, i)
+            i += 1
+            draw += 1
+        cur = _unflat(a, allv)
+        F = stacked_objective(slices, cur[:-1], cur[-1], P, t0)
+        if not _decide(F, F_old, decisions, log):
+            a = adam.update(a, False)
+            F = F_old
+            i -= P.tau_f
+        else:
+            a = adam.update(a, True)
+        epoch += 1
+    cur = _unflat(a, allv)
+    return cur[:-1], cur[-1], F
+
+
+def warm_start(slices, A0, S0, P, decisions=None, log=None):
+    """The warm start of an OnlineGCP stream: static_gcp_sgd on slices 1..n (time indices 1..n),
+    then an OnlineGCP state at t = n whose factors are the fit and whose history window holds the
+    warm-start slices' weights S_h, entered in order h = 1..n by the reservoir rule of Alg. 1."""
+    A, S, F = static_gcp_sgd(slices, A0, S0, P, decisions, log)
+    og = OnlineGCP(P, A)
+    og.t = len(slices)
+    for h in range(1, len(slices) + 1):
+        if P.H > 0:
+            if len(og.hist_t) < P.H:
+                og.hist_t.append(h)
+                og.hist_s.append(S[h - 1].copy())
+            else:
+                j = reservoir_index(P.seed, h)
+                if j <= P.H:
+                    og.hist_t[j - 1] = h
+                    og.hist_s[j - 1] = S[h - 1].copy()
+    og.s = S[-1].copy()
+    return og, S, F

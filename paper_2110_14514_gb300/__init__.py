@@ -60,6 +60,10 @@ class sgcp_stats_t(ctypes.Structure):
                 ("kernels_launched", c_int64), ("evals_f", c_int32), ("pad", c_int32)]
 
 
+class sgcp_warm_stats(ctypes.Structure):
+    _fields_ = [("F", c_double), ("epochs", c_int32), ("accept", c_uint32)]
+
+
 class sgcp_tune_entry(ctypes.Structure):
     _fields_ = [("bucket", c_int32 * 3), ("rank", c_int32), ("loss", c_int32), ("b1log", c_int32),
                 ("n1", c_int32), ("n2", c_int32), ("us", ctypes.c_float)]
@@ -95,6 +99,8 @@ SIGNATURES = [
     ("sgcp_sample_coords", c_int32, [c_void_p, POINTER(sgcp_slice), c_int32, c_int64, c_uint32, c_void_p,
                                      c_void_p]),
     ("sgcp_step", c_int32, [c_void_p, POINTER(sgcp_slice)]),
+    ("sgcp_warm_start", c_int32, [c_void_p, c_int32, POINTER(sgcp_slice), c_void_p, c_void_p,
+                                  POINTER(sgcp_warm_stats)]),
     ("sgcp_factors", c_int32, [c_void_p, _PTRS, c_void_p, POINTER(c_int64)]),
     ("sgcp_history", c_int32, [c_void_p, POINTER(c_int64), c_void_p, POINTER(c_int32)]),
     ("sgcp_check", c_int32, [c_void_p]),
@@ -316,6 +322,27 @@ class Context:
         self._enter()
         _check(lib.sgcp_step(self.h, ctypes.byref(sl)), self.h)
         self._leave()
+
+    def warm_start(self, slices, S_init=None):
+        """Static fit of the first n slices stacked along a new last mode (sgcp_warm_start).
+        slices: dense tensors, or (idx, vals) pairs.  Returns (S as an n x R device tensor,
+        {"F", "epochs", "accept"})."""
+        import torch
+        n = len(slices)
+        arr = (sgcp_slice * n)()
+        keep = []
+        for h, x in enumerate(slices):
+            sl, k = make_slice(X=x) if not isinstance(x, (tuple, list)) else make_slice(idx=x[0], vals=x[1])
+            arr[h] = sl
+            keep.append(k)
+        S = torch.empty((n, self.R), dtype=self.dtype, device="cuda")
+        st = sgcp_warm_stats()
+        self._keep = keep
+        self._enter()
+        code = lib.sgcp_warm_start(self.h, n, arr, _ptr(S_init), _ptr(S), ctypes.byref(st))
+        self._leave()
+        _check(code, self.h)
+        return S, {"F": st.F, "epochs": st.epochs, "accept": st.accept}
 
     def gradient(self, s, A, X=None, idx=None, vals=None, want=WANT_FACTORS | WANT_TEMPORAL | WANT_LOSS,
                  sample_set=SAMPLES_FACTOR_GRAD, t=1, draw=0, G=None, gs=None, f=None, accumulate=False,

@@ -803,6 +803,239 @@ sgcp_status enqueue_lbfgs(sgcp_ctx* c) {
     return SGCP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Warm start: static GCP-SGD on the first n slices stacked as a (d+1)-way
+// tensor whose last mode indexes the slices (Sec. 4.4, Sec. 6), with S
+// (n x R) that mode's factor matrix.  The loss gradient of the stack splits by
+// slice: dF/dA^(k) = sum_h Y_h(k) Z_k diag(S_h) and dF/dS_h = Z' vec(Y_h), so
+// each iteration runs the fused gradient kernel once per slice at s = S_h,
+// accumulating G^(k) and writing row h of the S gradient.  The variables
+// [A^(1..d); S] sit in one buffer, so the ADAM row update, the epoch test and
+// the rollback are the factor solver's kernels (Alg. 2, Alg. 4 without the
+// history term); lambda regularises every matrix of the stack.  Sparse slices
+// are sampled per slice (p + q samples each, slice h at time index h), each
+// with its own nonzero hash.
+// ---------------------------------------------------------------------------
+template <typename T>
+sgcp_status warm_start_impl(sgcp_ctx* c, int n, const sgcp_slice* X, const void* S_init, void* S_out,
+                            sgcp_warm_stats* out) {
+    const int d = c->ndim, R = c->R;
+    const sgcp_params& P = c->P;
+    const bool sparse = X[0].is_sparse != 0;
+    const int64_t rows = c->nrows + n, N2 = rows * R;
+    const size_t nb = (size_t)N2 * sizeof(T);
+    cudaStream_t st = c->stream;
+    std::vector<void*> tmp;   // released (after the stream has drained) on every return path
+    auto grab = [&](void** p, size_t bytes) -> sgcp_status {
+        sgcp_status e = dalloc(c, p, bytes);
+        if (e == SGCP_OK) tmp.push_back(*p);
+        return e;
+    };
+    struct Release {
+        sgcp_ctx* c;
+        std::vector<void*>* v;
+        ~Release() {
+            if (c->stream) cudaStreamSynchronize(c->stream);
+            for (void* p : *v) dfree(c, p);
+        }
+    } release{c, &tmp};
+
+    void *W = nullptr, *G2 = nullptr, *u2 = nullptr, *v2 = nullptr, *uo2 = nullptr, *vo2 = nullptr, *ao2 = nullptr;
+    void *rates = nullptr, *sst = nullptr;
+    void** bufs[] = {&W, &G2, &u2, &v2, &uo2, &vo2, &ao2};
+    for (void** b : bufs)
+        if (sgcp_status e = grab(b, nb)) return e;
+    if (sgcp_status e = grab(&rates, (size_t)(P.tau_f > 0 ? P.tau_f : 1) * sizeof(double))) return e;
+    if (sgcp_status e = grab(&sst, sizeof(SolverState))) return e;
+    SolverState* sw = (SolverState*)sst;
+
+    // the slices on the device: descriptors, staged copies, hashes
+    std::vector<SliceDesc> desc(n);
+    std::vector<unsigned long long*> keys(n, nullptr);
+    std::vector<int> hl(n, 0);
+    for (int h = 0; h < n; ++h) {
+        const sgcp_slice& x = X[h];
+        const int64_t nnz = sparse ? x.nnz : omega_of(c);
+        const void* idx_d = x.idx;
+        const void* vals_d = x.vals;
+        const bool restage = !x.on_host && !sparse && c->tc && (reinterpret_cast<uintptr_t>(x.vals) & 15) != 0;
+        if (x.on_host || restage) {
+            const size_t ib = sparse ? (size_t)nnz * d * sizeof(int32_t) : 0;
+            const size_t vb = (size_t)nnz * (sparse ? sizeof(float) : c->esz);
+            const cudaMemcpyKind kind = x.on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+            void *ip = nullptr, *vp = nullptr;
+            if (ib) {
+                if (sgcp_status e = grab(&ip, ib)) return e;
+                CK(cudaMemcpyAsync(ip, x.idx, ib, kind, st), "stage slice idx");
+            }
+            if (vb) {
+                if (sgcp_status e = grab(&vp, vb)) return e;
+                CK(cudaMemcpyAsync(vp, x.vals, vb, kind, st), "stage slice vals");
+            }
+            idx_d = ip;
+            vals_d = vp;
+        }
+        desc[h].idx = (const int32_t*)idx_d;
+        desc[h].vals = vals_d;
+        desc[h].nnz = nnz;
+        desc[h].t = h + 1;
+        if (sparse && nnz > 0) {
+            int b = 10;
+            while (((int64_t)1 << b) < 2 * nnz) ++b;
+            hl[h] = b;
+            void* kp = nullptr;
+            if (sgcp_status e = grab(&kp, ((size_t)1 << b) * sizeof(unsigned long long))) return e;
+            keys[h] = (unsigned long long*)kp;
+            CK(cudaMemsetAsync(kp, 0xFF, ((size_t)1 << b) * sizeof(unsigned long long), st), "clear hash");
+            CK(launch_hash_build(desc[h], d, c->dims, keys[h], b, c->err, st), "hash");
+            c->launches += 1;
+        }
+    }
+
+    // the stacked variables: the context's factors, then S (given, or ones)
+    CK(cudaMemcpyAsync(W, c->A, (size_t)c->N * sizeof(T), cudaMemcpyDeviceToDevice, st), "stack factors");
+    T* S = (T*)offs(W, c->nrows * R, sizeof(T));
+    if (S_init) {
+        CK(cudaMemcpyAsync(S, S_init, (size_t)n * R * sizeof(T), cudaMemcpyDeviceToDevice, st), "stack S");
+    } else {
+        std::vector<T> ones((size_t)n * R, T(1));
+        CK(cudaMemcpyAsync(S, ones.data(), ones.size() * sizeof(T), cudaMemcpyHostToDevice, st), "stack S");
+        CK(cudaStreamSynchronize(st), "stack S");   // the host vector dies here
+    }
+    CK(cudaMemsetAsync(G2, 0, nb, st), "clear G");
+    CK(launch_adam_reset<T>(N2, (const T*)W, (T*)u2, (T*)v2, (T*)ao2, (T*)uo2, (T*)vo2, 0, (T*)W, st, &c->launches),
+       "adam init");
+    SolverState s0{};
+    s0.b1pow = 1.0;
+    s0.b2pow = 1.0;
+    CK(cudaMemcpyAsync(sw, &s0, sizeof(s0), cudaMemcpyHostToDevice, st), "solver state");
+    CK(cudaStreamSynchronize(st), "solver state");
+    CK(launch_solver_init(sw, P.alpha_f, 1, st, &c->launches), "solver init");
+
+    const void* Aw[4];
+    void* Gw[4];
+    for (int k = 0; k < d; ++k) {
+        Aw[k] = offs(W, c->row_off[k] * R, sizeof(T));
+        Gw[k] = offs(G2, c->row_off[k] * R, sizeof(T));
+    }
+    // one slice's fused kernel at s = S_h
+    auto slice_grad = [&](int h, int set, uint32_t draw, int want, void* gs, double* f,
+                          const int32_t* skip) -> sgcp_status {
+        const void* sh = offs(S, (int64_t)h * R, sizeof(T));
+        if (sparse) {
+            SparseGradArgs a = sparse_args(c, nullptr, set, draw, want, sh, Aw, Gw, gs, f, P.loss, nullptr, skip);
+            a.inline_slice = desc[h];
+            a.hkeys = keys[h];
+            a.hlog2 = hl[h];
+            a.nhot = 0;
+            const bool obj = set == SGCP_SAMPLES_FACTOR_OBJ;
+            CK(launch_sparse_grad(a, obj ? P.p_obj + P.q_obj : P.p + P.q, st, &c->launches), "sparse gradient");
+        } else if (c->f64) {
+            DenseGradArgs<double> a = dense_args<double>(c, nullptr, want, sh, Aw, Gw, gs, f, P.loss, nullptr, skip);
+            a.inline_slice = desc[h];
+            a.xmap = nullptr;
+            CK(launch_dense_grad<double>(a, st, &c->launches), "dense gradient");
+        } else {
+            DenseGradArgs<float> a = dense_args<float>(c, nullptr, want, sh, Aw, Gw, gs, f, P.loss, nullptr, skip);
+            a.inline_slice = desc[h];
+            a.xmap = nullptr;
+            if (c->tc)
+                CK(launch_dense_grad_tc(a, P.precision == SGCP_PREC_BF16_MTTKRP, c->err, st, &c->launches),
+                   "dense tensor-core gradient");
+            else
+                CK(launch_dense_grad<float>(a, st, &c->launches), "dense gradient");
+        }
+        return SGCP_OK;
+    };
+    auto objective = [&](int set_cur, const int32_t* skip) -> sgcp_status {
+        CK(cudaMemsetAsync(&sw->F_new, 0, sizeof(double), st), "clear F");
+        for (int h = 0; h < n; ++h)
+            if (sgcp_status e = slice_grad(h, SGCP_SAMPLES_FACTOR_OBJ, 0, SGCP_WANT_LOSS, nullptr, &sw->F_new, skip))
+                return e;
+        CK(launch_reg_objective<T>(sw, (const T*)W, N2, P.lambda, set_cur, c->err, skip, st, &c->launches),
+           "objective");
+        return SGCP_OK;
+    };
+    if (sgcp_status e = objective(1, nullptr)) return e;
+    FactorUpdateArgs<T> fu{};
+    fu.ndim = d;
+    fu.R = R;
+    fu.nrows = rows;
+    for (int k = 0; k < 4; ++k) fu.row_off[k] = k < d ? c->row_off[k] : c->nrows;
+    fu.A = (T*)W;
+    fu.Abar = (const T*)W;   // no history term: the reference factors are not read
+    fu.G = (T*)G2;
+    fu.u = (T*)u2;
+    fu.v = (T*)v2;
+    fu.B = nullptr;
+    fu.C = nullptr;
+    fu.hist_len = c->hist_len_dev;
+    fu.lam = P.lambda;
+    fu.beta1 = P.beta1;
+    fu.beta2 = P.beta2;
+    fu.eps = P.adam_eps;
+    fu.lower = c->lower;
+    const int32_t* skip = &sw->done;
+    fu.skip = skip;
+    for (int e = 0; e < P.kappa_f; ++e) {
+        CK(launch_epoch_begin(sw, P.tol_f, (double*)rates, P.tau_f, P.beta1, P.beta2, st, &c->launches),
+           "epoch begin");
+        for (int it = 0; it < P.tau_f; ++it) {
+            for (int h = 0; h < n; ++h)
+                if (sgcp_status e2 = slice_grad(h, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
+                                                SGCP_WANT_FACTORS | SGCP_WANT_TEMPORAL,
+                                                offs(G2, (c->nrows + h) * R, sizeof(T)), nullptr, skip))
+                    return e2;
+            fu.rate = (const double*)rates + it;
+            CK(launch_factor_update<T>(fu, st, &c->launches), "stacked update");
+        }
+        if (sgcp_status e2 = objective(0, skip)) return e2;
+        CK(launch_epoch_end<T>(sw, N2, (T*)W, (T*)u2, (T*)v2, (T*)ao2, (T*)uo2, (T*)vo2, P.tau_f, P.alpha_decay,
+                               P.beta1, P.beta2, st, &c->launches),
+           "epoch end");
+    }
+    // the stream's state at t = n: factors (also Abar and the ADAM checkpoint), s = S_n, and the
+    // window filled by the reservoir rule of Alg. 1 as the warm-start slices enter in order
+    const size_t na = (size_t)c->N * sizeof(T);
+    CK(cudaMemcpyAsync(c->A, W, na, cudaMemcpyDeviceToDevice, st), "factors");
+    CK(cudaMemcpyAsync(c->Abar, W, na, cudaMemcpyDeviceToDevice, st), "Abar");
+    CK(cudaMemcpyAsync(c->a_o, W, na, cudaMemcpyDeviceToDevice, st), "checkpoint");
+    CK(cudaMemcpyAsync(c->s, offs(S, (int64_t)(n - 1) * R, sizeof(T)), (size_t)R * sizeof(T),
+                       cudaMemcpyDeviceToDevice, st),
+       "s");
+    if (S_out) CK(cudaMemcpyAsync(S_out, S, (size_t)n * R * sizeof(T), cudaMemcpyDeviceToDevice, st), "S out");
+    for (int h = 1; h <= n && P.H > 0; ++h) {
+        int slot = -1;
+        int len = (int)c->hist_t.size();
+        if (len < P.H) {
+            slot = len;
+            c->hist_t.push_back(h);
+            len += 1;
+        } else {
+            const uint32_t j = reservoir_index(P.seed, h);
+            if ((int64_t)j <= P.H) {
+                slot = (int)j - 1;
+                c->hist_t[slot] = h;
+            }
+        }
+        if (slot >= 0)
+            CK(launch_hist_update<T>(R, (T*)c->s_hist, c->h_dev, c->hist_len_dev, slot, h, len,
+                                     (const T*)offs(S, (int64_t)(h - 1) * R, sizeof(T)), st, &c->launches),
+               "history");
+    }
+    SolverState fin{};
+    CK(cudaMemcpyAsync(&fin, sw, sizeof(fin), cudaMemcpyDeviceToHost, st), "read state");
+    CK(cudaStreamSynchronize(st), "warm start");
+    if (out) {
+        out->F = fin.F_cur;
+        out->epochs = fin.epoch;
+        out->accept = fin.accept;
+    }
+    c->t = n;
+    c->loaded = false;
+    return SGCP_OK;
+}
+
 sgcp_status build_graph(sgcp_ctx* c, bool sparse) {
     const int gi = sparse ? 1 : 0;
     cudaGraph_t g = nullptr;
@@ -1203,6 +1436,32 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
     }
     c->t = t;
     return SGCP_OK;
+}
+
+sgcp_status sgcp_warm_start(sgcp_ctx* c, int32_t n, const sgcp_slice* X, const void* S_init, void* S_out,
+                            sgcp_warm_stats* stats_out) {
+    if (sgcp_status st = check_ready(c)) return st;
+    if (n < 1 || !X) return fail(c, SGCP_ERR_ARG, "warm start: need n >= 1 slices");
+    if (c->t != 0 || !c->hist_t.empty())
+        return fail(c, SGCP_ERR_ARG, "warm start: the context has processed slices or holds a history window");
+    const bool sparse = X[0].is_sparse != 0;
+    for (int h = 0; h < n; ++h) {
+        const sgcp_slice& x = X[h];
+        if ((x.is_sparse != 0) != sparse) return fail(c, SGCP_ERR_ARG, "warm start: mixed sparse and dense slices");
+        if (sparse) {
+            if (c->f64) return fail(c, SGCP_ERR_UNSUPPORTED, "warm start: sparse slices need a float context");
+            if (x.nnz < 0 || x.nnz > omega_of(c) || x.nnz >= (int64_t)1 << 31)
+                return fail(c, SGCP_ERR_ARG, "warm start: slice %d nnz out of range", h);
+            if (x.nnz > 0 && (!x.idx || !x.vals)) return fail(c, SGCP_ERR_ARG, "warm start: slice %d without data", h);
+        } else {
+            if (!x.vals) return fail(c, SGCP_ERR_ARG, "warm start: dense slice %d without vals", h);
+            if (c->ndim > 3) return fail(c, SGCP_ERR_UNSUPPORTED, "warm start: dense slices support ndim <= 3");
+        }
+    }
+    if (sparse && (c->P.p + c->P.q == 0 || c->P.p_obj + c->P.q_obj == 0))
+        return fail(c, SGCP_ERR_ARG, "warm start: sparse slices need p + q > 0 and p_obj + q_obj > 0");
+    return c->f64 ? warm_start_impl<double>(c, n, X, S_init, S_out, stats_out)
+                  : warm_start_impl<float>(c, n, X, S_init, S_out, stats_out);
 }
 
 sgcp_status sgcp_factors(sgcp_ctx* c, void* const* A_out, void* s_out, int64_t* t_out) {

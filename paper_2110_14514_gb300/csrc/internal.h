@@ -271,6 +271,11 @@ cudaError_t launch_lbfgs_update(const LbfgsArgs<T>& a, cudaStream_t st, int64_t*
 // Report the solve like an epoch summary: F_cur <- F, epoch <- iterations.
 cudaError_t launch_lbfgs_finish(LbfgsState* ls, SolverState* sf, cudaStream_t st, int64_t* launches);
 
+// Warm start (stacked static fit): F_new += lambda/2 ||W||^2 over n elements; F_cur <- F_new if set_cur.
+template <typename T>
+cudaError_t launch_reg_objective(SolverState* st, const T* W, int64_t n, double lam, int set_cur, int* err,
+                                 const int32_t* skip, cudaStream_t stream, int64_t* launches);
+
 // Small helpers.
 template <typename T>
 cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, int64_t* launches);

@@ -1137,6 +1137,33 @@ cudaError_t launch_lbfgs_finish(LbfgsState* ls, SolverState* sf, cudaStream_t st
     return cudaGetLastError();
 }
 
+// Objective finish of the warm start's stacked problem: F_new += lambda/2 ||W||^2 over every
+// factor matrix of the stack (one 8-CTA cluster; per-thread sums in T, the rest in double).
+template <typename T>
+__global__ void __cluster_dims__(kLbCluster, 1, 1) __launch_bounds__(kLbThreads)
+    k_reg_objective(SolverState* st, const T* W, int64_t n, double lam, int set_cur, int* err, const int32_t* skip) {
+    __shared__ double red[32];
+    __shared__ double part;
+    if (skip && *skip) return;
+    T acc = T(0);
+    for (int64_t i = lb_first(); i < n; i += lb_stride()) acc += W[i] * W[i];
+    const double ss = lb_cluster_sum((double)acc, red, &part);
+    if (lb_leader()) {
+        const double F = st->F_new + 0.5 * lam * ss;
+        st->F_new = F;
+        if (!isfinite(F)) set_err(err, ERRB_NUMERIC);
+        if (set_cur) st->F_cur = F;
+    }
+}
+
+template <typename T>
+cudaError_t launch_reg_objective(SolverState* st, const T* W, int64_t n, double lam, int set_cur, int* err,
+                                 const int32_t* skip, cudaStream_t stream, int64_t* launches) {
+    k_reg_objective<T><<<kLbCluster, kLbThreads, 0, stream>>>(st, W, n, lam, set_cur, err, skip);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_copy(T* dst, const T* src, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1169,6 +1196,8 @@ cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, in
     template cudaError_t launch_lsq_solve<T>(int, int, const double*, const T*, double, double, T*, double*, int*,   \
                                              cudaStream_t, int64_t*);                                                 \
     template cudaError_t launch_copy<T>(T*, const T*, int64_t, cudaStream_t, int64_t*);                          \
+    template cudaError_t launch_reg_objective<T>(SolverState*, const T*, int64_t, double, int, int*, const int32_t*, \
+                                                 cudaStream_t, int64_t*);                                            \
     template cudaError_t launch_lbfgs_begin<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                      \
     template cudaError_t launch_lbfgs_direction<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                  \
     template cudaError_t launch_lbfgs_trial<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                      \
