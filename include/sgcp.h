@@ -318,7 +318,31 @@ typedef struct {
 sgcp_status sgcp_warm_start(sgcp_ctx* ctx, int32_t n, const sgcp_slice* X, const void* S_init, void* S_out,
                             sgcp_warm_stats* stats_out);
 
-/* Process the next slice: one pass of the loop body of Alg. 1 (temporal/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
+/* Reconstruction loss of a slice at the model M = [[s; A]] (Sec. 6, eq. local_loss): out (host,
+ * 2 doubles) receives sum_i f(x_i, m_i) and ||X||_F^2; their ratio is the local loss of a slice
+ * at the factors of its own time step, and -- with the last step's factors -- the slice's term of
+ * the global loss.  exact = 0: dense slices are summed over every entry, sparse slices estimated
+ * with the objective sample set (p_obj + q_obj stratified samples at time index t, draw 0; Alg. 5
+ * without the history and regularisation terms).  exact = 1: every entry, zeros included (for a
+ * sparse slice the model is evaluated over the whole index space, which needs ndim <= 3).  s and
+ * A as in sgcp_gradient.  Synchronises the context stream. */
+sgcp_status sgcp_slice_loss(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, const void* const* A, int32_t exact,
+                            int64_t t, double* out);
+
+/* K-tensor score (Sec. 6.1): the congruence between the rank-one components of two K-tensors with
+ * nmodes factor matrices each (device, A[k] and B[k] both I_k x rank, row-major, element type
+ * float for SGCP_PREC_F32 or double for SGCP_PREC_F64; the temporal mode may be one of them):
+ * Q[r][c] = prod_k |cos(a_r^(k), b_c^(k))|, and the score = the mean of Q over the best matching
+ * of components -- all rank! matchings for rank <= 8, greedy (largest remaining entry first)
+ * above.  score_out (host) receives it, perm_out (host, rank int32, may be NULL) the matching
+ * (component r of A to component perm_out[r] of B); 1 means the same components up to order and
+ * scale.  1 <= nmodes <= 8, 1 <= rank <= 128.  Uses a small stream-ordered scratch allocation and
+ * synchronises cuda_stream (NULL = the legacy default stream). */
+sgcp_status sgcp_kruskal_score(int32_t nmodes, int32_t rank, const int64_t* dims, int32_t precision,
+                               const void* const* A, const void* const* B, double* score_out, int32_t* perm_out,
+                               void* cuda_stream);
+
+/* Process the next slice: one pass of the loop body of Alg. 1 (temporal/* Process the next slice: one pass of the loop body of Alg. 1 (temporal/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
  * solve, factor solve, reservoir history update, Abar <- A).  Asynchronous;
  * the whole solver sequence runs as CUDA graphs on the context stream. */
 sgcp_status sgcp_step(sgcp_ctx* ctx, const sgcp_slice* X_t);

@@ -420,3 +420,76 @@ def regularization_objective(A, s, lam, mu):
 def kruskal_full(s, A):
     """Full Kruskal tensor (alias of the explicit outer-product sum)."""
     return kruskal_full_bruteforce(s, A)
+
+
+# ----------------------------------------------------------------------------
+# Reconstruction losses and the K-tensor score (Sec. 6)
+# ----------------------------------------------------------------------------
+def coo_to_dense(coo_idx, coo_val, dims):
+    """The full slice of a COO slice (small sizes only)."""
+    X = np.zeros(dims)
+    idx = np.asarray(coo_idx, np.int64).reshape(-1, len(dims))
+    X[tuple(idx.T)] = np.asarray(coo_val, np.float64)
+    return X
+
+
+def exact_slice_loss(X, s, A, loss, eps=1e-10):
+    """sum over every entry i of f(x_i, m_i) (a dense array X), and ||X||_F^2: the numerator and
+    denominator of eq. local_loss evaluated exactly (the global loss of Sec. 6 uses this for every
+    earlier slice with the final factors)."""
+    X = np.asarray(X, np.float64)
+    return dense_objective(X, s, A, loss, eps), float((X * X).sum())
+
+
+def sampled_slice_loss(coo_idx, coo_val, dims, s, A, loss, p_obj, q_obj, seed, t, eps=1e-10, cap=64):
+    """The sampled numerator of eq. local_loss for a sparse slice: Alg. 5's sample sum with the
+    factor solver's objective samples (draw 0, time index t), no history or regularisation term;
+    and ||X||_F^2 = sum of the squared nonzeros."""
+    coords, x, w = stratified_samples(coo_idx, coo_val, dims, p_obj, q_obj, seed, t, 0, PURPOSE["obj_nz"],
+                                      PURPOSE["obj_z"], cap)
+    return sampled_loss(coords, x, w, s, A, loss, eps), float((np.asarray(coo_val, np.float64) ** 2).sum())
+
+
+def congruence_matrix(A, B):
+    """Q[r, c] = prod_k |cos(a_r^(k), b_c^(k))| between the columns of two K-tensors' factor
+    matrices (Tomasi and Bro's congruence of rank-one components; weights play no part)."""
+    R = np.shape(A[0])[1]
+    Q = np.ones((R, R))
+    for Ak, Bk in zip(A, B):
+        Ak = np.asarray(Ak, np.float64)
+        Bk = np.asarray(Bk, np.float64)
+        na = np.linalg.norm(Ak, axis=0)
+        nb = np.linalg.norm(Bk, axis=0)
+        Q *= np.abs(Ak.T @ Bk) / np.outer(na, nb)
+    return Q
+
+
+def kruskal_score(A, B):
+    """K-tensor score (Sec. 6.1): the mean congruence over matched components.  R <= 8: the best
+    of all R! matchings; larger R: greedy (repeatedly the largest remaining entry of Q, ties to
+    the smallest row-major index).  Returns (score, perm) with component r of A matched to
+    component perm[r] of B."""
+    import itertools
+    Q = congruence_matrix(A, B)
+    R = Q.shape[0]
+    if R <= 8:
+        best, bperm = -1.0, None
+        for perm in itertools.permutations(range(R)):   # lexicographic order: ties keep the first
+            v = sum(Q[r, perm[r]] for r in range(R))
+            if v > best:
+                best, bperm = v, perm
+        return best / R, list(bperm)
+    perm = [-1] * R
+    rows, cols = set(range(R)), set(range(R))
+    tot = 0.0
+    for _ in range(R):
+        bv, br, bc = -1.0, -1, -1
+        for r in sorted(rows):
+            for c in sorted(cols):
+                if Q[r, c] > bv:
+                    bv, br, bc = Q[r, c], r, c
+        perm[br] = bc
+        tot += bv
+        rows.discard(br)
+        cols.discard(bc)
+    return tot / R, perm

@@ -101,6 +101,10 @@ SIGNATURES = [
     ("sgcp_step", c_int32, [c_void_p, POINTER(sgcp_slice)]),
     ("sgcp_warm_start", c_int32, [c_void_p, c_int32, POINTER(sgcp_slice), c_void_p, c_void_p,
                                   POINTER(sgcp_warm_stats)]),
+    ("sgcp_slice_loss", c_int32, [c_void_p, POINTER(sgcp_slice), c_void_p, _PTRS, c_int32, c_int64,
+                                  POINTER(c_double)]),
+    ("sgcp_kruskal_score", c_int32, [c_int32, c_int32, POINTER(c_int64), c_int32, _PTRS, _PTRS, POINTER(c_double),
+                                     POINTER(c_int32), c_void_p]),
     ("sgcp_factors", c_int32, [c_void_p, _PTRS, c_void_p, POINTER(c_int64)]),
     ("sgcp_history", c_int32, [c_void_p, POINTER(c_int64), c_void_p, POINTER(c_int32)]),
     ("sgcp_check", c_int32, [c_void_p]),
@@ -344,6 +348,17 @@ class Context:
         _check(code, self.h)
         return S, {"F": st.F, "epochs": st.epochs, "accept": st.accept}
 
+    def slice_loss(self, s, A, X=None, idx=None, vals=None, exact=False, t=1):
+        """(sum_i f(x_i, m_i), ||X||_F^2) of a slice at M = [[s; A]] (sgcp_slice_loss); their ratio is
+        the local / global reconstruction loss of Sec. 6."""
+        out = (c_double * 2)()
+        sl = self._slice(X, idx, vals)
+        self._enter()
+        code = lib.sgcp_slice_loss(self.h, ctypes.byref(sl), _ptr(s), _ptr_array(A), int(bool(exact)), int(t), out)
+        self._leave()
+        _check(code, self.h)
+        return out[0], out[1]
+
     def gradient(self, s, A, X=None, idx=None, vals=None, want=WANT_FACTORS | WANT_TEMPORAL | WANT_LOSS,
                  sample_set=SAMPLES_FACTOR_GRAD, t=1, draw=0, G=None, gs=None, f=None, accumulate=False,
                  y_scale=None):
@@ -417,6 +432,22 @@ class Context:
     def state_import(self, data):
         buf = ctypes.create_string_buffer(data, len(data))
         _check(lib.sgcp_state_import(self.h, buf, len(data)), self.h)
+
+
+def kruskal_score(A, B, stream=None):
+    """K-tensor score of Sec. 6.1 between two lists of device factor matrices (same shapes, float32
+    or float64): (score, perm) with component r of A matched to component perm[r] of B."""
+    import torch
+    n = len(A)
+    R = A[0].shape[1]
+    dims = (c_int64 * n)(*[a.shape[0] for a in A])
+    prec = PREC_F64 if A[0].dtype == torch.float64 else PREC_F32
+    score = c_double()
+    perm = (c_int32 * R)()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.sgcp_kruskal_score(n, R, dims, prec, _ptr_array(A), _ptr_array(B), ctypes.byref(score), perm,
+                                  c_void_p(st.cuda_stream)))
+    return score.value, list(perm)
 
 
 def _entry_dict(e):

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsgcp.so")
 
 SOURCES = ["capi.cu", "k_sparse.cu", "k_dense.cu", "k_dense_tc.cu", "k_solver.cu", "noalloc.cu", "batch.cu",
-           "k_batch.cu"]
+           "k_batch.cu", "k_score.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", INCLUDE]

@@ -62,6 +62,7 @@ struct sgcp_ctx {
     double* rates_f = nullptr;
     int* err = nullptr;
     SliceDesc* slice_dev = nullptr;
+    double* metric = nullptr;    // [2]: loss sum and ||X||^2 of sgcp_slice_loss
 
     // sparse-slice structures
     unsigned long long* hkeys = nullptr;
@@ -1249,6 +1250,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         (st = dalloc_t(c, &c->rates_w, (P.tau_w > 0 ? P.tau_w : 1) * sizeof(double))) ||
         (st = dalloc_t(c, &c->rates_f, (P.tau_f > 0 ? P.tau_f : 1) * sizeof(double))) ||
         (st = dalloc_t(c, &c->err, sizeof(int))) || (st = dalloc_t(c, &c->slice_dev, sizeof(SliceDesc))) ||
+        (st = dalloc_t(c, &c->metric, 2 * sizeof(double))) ||
         (st = dalloc_t(c, &c->counts, c->nrows * sizeof(int32_t))) ||
         (st = dalloc_t(c, &c->hot, c->nrows * sizeof(int32_t))) ||
         (st = dalloc_t(c, &c->hot_rows, c->ndim * kMaxHot * sizeof(int32_t))) ||
@@ -1462,6 +1464,94 @@ sgcp_status sgcp_warm_start(sgcp_ctx* c, int32_t n, const sgcp_slice* X, const v
         return fail(c, SGCP_ERR_ARG, "warm start: sparse slices need p + q > 0 and p_obj + q_obj > 0");
     return c->f64 ? warm_start_impl<double>(c, n, X, S_init, S_out, stats_out)
                   : warm_start_impl<float>(c, n, X, S_init, S_out, stats_out);
+}
+
+sgcp_status sgcp_slice_loss(sgcp_ctx* c, const sgcp_slice* X, const void* s, const void* const* A, int32_t exact,
+                            int64_t t, double* out) {
+    if (sgcp_status st = check_ready(c)) return st;
+    if (!X || !s || !A || !out) return fail(c, SGCP_ERR_ARG, "slice_loss: NULL argument");
+    if ((reinterpret_cast<uintptr_t>(s) & 15) != 0) return fail(c, SGCP_ERR_ARG, "slice_loss: s is not 16-byte aligned");
+    for (int k = 0; k < c->ndim; ++k)
+        if (!A[k] || (reinterpret_cast<uintptr_t>(A[k]) & 15) != 0)
+            return fail(c, SGCP_ERR_ARG, "slice_loss: A[%d] is NULL or not 16-byte aligned", k);
+    const bool sparse = X->is_sparse != 0;
+    if (sparse && exact && c->ndim > 3)
+        return fail(c, SGCP_ERR_UNSUPPORTED, "slice_loss: the exact loss of a sparse slice needs ndim <= 3");
+    if (sparse && !exact && c->P.p_obj + c->P.q_obj == 0)
+        return fail(c, SGCP_ERR_ARG, "slice_loss: the sampled loss needs p_obj + q_obj > 0");
+    if (sgcp_status st = load_slice(c, X, t, false)) return st;
+    if (!sparse)
+        if (sgcp_status st = prepare_xmap(c)) return st;
+    CK(cudaMemsetAsync(c->metric, 0, 2 * sizeof(double), c->stream), "clear loss");
+    if (sparse)
+        CK(launch_sum_squares<float>((const float*)c->cur.vals, c->cur.nnz, c->metric + 1, c->stream, &c->launches),
+           "norm");
+    else if (c->f64)
+        CK(launch_sum_squares<double>((const double*)c->cur.vals, c->cur.nnz, c->metric + 1, c->stream, &c->launches),
+           "norm");
+    else
+        CK(launch_sum_squares<float>((const float*)c->cur.vals, c->cur.nnz, c->metric + 1, c->stream, &c->launches),
+           "norm");
+    if (!sparse || !exact) {
+        // dense: the exact sum over every entry; sparse: the objective sample set at time index t
+        sgcp_status st = enqueue_gradient(c, sparse, nullptr, SGCP_SAMPLES_FACTOR_OBJ, 0, SGCP_WANT_LOSS, s, A, nullptr,
+                                          nullptr, c->metric, c->P.loss, nullptr, nullptr);
+        if (st) return st;
+    } else {
+        // every entry of a sparse slice: sum_i f(0, m_i) over the whole index space (the dense loss
+        // kernel on the all-zero slice), plus f(x, m) - f(0, m) over the nonzeros
+        DenseGradArgs<float> z = dense_args<float>(c, nullptr, SGCP_WANT_LOSS, s, A, nullptr, nullptr, c->metric,
+                                                   c->P.loss, nullptr, nullptr);
+        z.inline_slice.vals = nullptr;
+        z.inline_slice.nnz = omega_of(c);
+        z.xmap = nullptr;
+        CK(launch_dense_grad<float>(z, c->stream, &c->launches), "model loss");
+        SparseGradArgs a = sparse_args(c, nullptr, SGCP_SAMPLES_FACTOR_OBJ, 0, SGCP_WANT_LOSS, s, A, nullptr, nullptr,
+                                       c->metric, c->P.loss, nullptr, nullptr);
+        a.all_nnz = 1;
+        a.f_minus_zero = 1;
+        CK(launch_sparse_grad(a, (int64_t)1 << 40, c->stream, &c->launches), "nonzero loss");
+    }
+    CK(cudaMemcpyAsync(out, c->metric, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read loss");
+    CK(cudaStreamSynchronize(c->stream), "slice loss");
+    return SGCP_OK;
+}
+
+sgcp_status sgcp_kruskal_score(int32_t nmodes, int32_t rank, const int64_t* dims, int32_t precision,
+                               const void* const* A, const void* const* B, double* score_out, int32_t* perm_out,
+                               void* cuda_stream) {
+    if (nmodes < 1 || nmodes > 8 || rank < 1 || rank > 128 || !dims || !A || !B || !score_out) return SGCP_ERR_ARG;
+    if (precision != SGCP_PREC_F32 && precision != SGCP_PREC_F64) return SGCP_ERR_ARG;
+    for (int k = 0; k < nmodes; ++k)
+        if (dims[k] < 1 || !A[k] || !B[k]) return SGCP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t RR = (size_t)rank * rank;
+    const size_t bytes = (nmodes * RR + 2 * (size_t)nmodes * rank + 1) * sizeof(double) + rank * sizeof(int32_t);
+    void* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SGCP_ERR_OOM;
+    }
+    double* C = (double*)scratch;
+    double* na = C + nmodes * RR;
+    double* nb = na + (size_t)nmodes * rank;
+    double* sc = nb + (size_t)nmodes * rank;
+    int32_t* pm = (int32_t*)(sc + 1);
+    cudaError_t e = precision == SGCP_PREC_F64
+                        ? launch_congruence<double>(nmodes, rank, dims, (const double* const*)A,
+                                                    (const double* const*)B, C, na, nb, sc, pm, st)
+                        : launch_congruence<float>(nmodes, rank, dims, (const float* const*)A, (const float* const*)B,
+                                                   C, na, nb, sc, pm, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(score_out, sc, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && perm_out)
+        e = cudaMemcpyAsync(perm_out, pm, rank * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SGCP_ERR_CUDA;
+    }
+    return SGCP_OK;
 }
 
 sgcp_status sgcp_factors(sgcp_ctx* c, void* const* A_out, void* s_out, int64_t* t_out) {

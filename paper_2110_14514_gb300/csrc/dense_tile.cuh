@@ -191,7 +191,8 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
             for (int i = tid; i < 64 * 32; i += kBoxThreads) {   // a warp reads 32 consecutive i3: 128 bytes
                 const int row = i >> 5, col = i & 31;
                 const int i1 = i1b + (row >> lb2), i2 = i2b + (row & (B2 - 1)), i3 = g.o3 + col;
-                Yn[i] = (i1 < I1 && i2 < I2 && i3 < I3) ? __ldg(g.X + ((int64_t)i1 * I2 + i2) * I3 + i3) : 0.f;
+                Yn[i] = (g.X && i1 < I1 && i2 < I2 && i3 < I3) ? __ldg(g.X + ((int64_t)i1 * I2 + i2) * I3 + i3)
+                                                                : 0.f;   // X == nullptr: the all-zero slice
             }
             __syncthreads();
             // Khatri-Rao panel, natural layout (lanes along j) and k-major layout (lanes along rows)

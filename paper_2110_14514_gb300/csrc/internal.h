@@ -43,6 +43,7 @@ struct SparseGradArgs {
     int tstep_on;                    // fuse the temporal ADAM step into the last block
     TemporalStep<float> tstep;
     int cpl;                         // columns per lane (4, 8, 16; 0 = default for R)
+    int f_minus_zero;                // loss: add f(x, m) - f(0, m) per sample (the nonzeros' part of an exact loss)
 };
 
 // Arguments of the dense fused gradient kernels (3-way tiled and the 2-way path).
@@ -67,6 +68,7 @@ struct DenseGradArgs {
     TemporalStep<T> tstep;
     const void* xmap;        // tensor-core path: device CUtensorMap of the slice (nullptr = plain loads)
 };
+// (the CUDA-core dense kernels read a slice whose vals pointer is nullptr as the all-zero slice)
 
 struct IngestArgs {
     SliceDesc slice;
@@ -275,6 +277,18 @@ cudaError_t launch_lbfgs_finish(LbfgsState* ls, SolverState* sf, cudaStream_t st
 template <typename T>
 cudaError_t launch_reg_objective(SolverState* st, const T* W, int64_t n, double lam, int set_cur, int* err,
                                  const int32_t* skip, cudaStream_t stream, int64_t* launches);
+
+// ---------------------------------------------------------------------------
+// Evaluation metrics (k_score.cu): reconstruction losses and the K-tensor score of Sec. 6
+// ---------------------------------------------------------------------------
+// *out += sum_i x_i^2 over n elements.
+template <typename T>
+cudaError_t launch_sum_squares(const T* x, int64_t n, double* out, cudaStream_t st, int64_t* launches);
+// Congruence of two K-tensors (nm modes, I_k x R factor matrices A[k], B[k], element T): per-mode
+// cross-Grams C = [nm][R][R], column norms^2 na, nb = [nm][R] (scratch), then score and perm.
+template <typename T>
+cudaError_t launch_congruence(int nm, int R, const int64_t* dims, const T* const* A, const T* const* B,
+                              double* C, double* na, double* nb, double* score, int32_t* perm, cudaStream_t st);
 
 // Small helpers.
 template <typename T>

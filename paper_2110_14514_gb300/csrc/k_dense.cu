@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_dense3(const DenseGradArgs<T> a, int n1
             for (int i = tid; i < C::TR * C::TC; i += 256) {
                 const int row = i >> 5, col = i & 31;
                 const int64_t i1 = i1b + row / B2, i2 = i2b + row % B2, i3 = o3 + col;
-                Ys[row * 33 + col] = (i1 < I1 && i2 < I2 && i3 < I3) ? X[(i1 * I2 + i2) * I3 + i3] : T(0);
+                Ys[row * 33 + col] = (X && i1 < I1 && i2 < I2 && i3 < I3) ? X[(i1 * I2 + i2) * I3 + i3] : T(0);
             }
             __syncthreads();
             for (int i = tid; i < C::TR * RMAX; i += 256) {

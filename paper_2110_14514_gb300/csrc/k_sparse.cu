@@ -264,6 +264,11 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
             if (wantF && gl == 0 && okj) {
                 float f, yy;
                 loss_eval<float>(a.loss, xj, mp, a.eps, f, yy);
+                if (a.f_minus_zero) {
+                    float f0;
+                    loss_eval<float>(a.loss, 0.0f, mp, a.eps, f0, yy);
+                    f -= f0;
+                }
                 fl += wj * f * ysc;
             }
             if (wantS) {
