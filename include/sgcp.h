@@ -81,6 +81,14 @@ typedef enum {
     SGCP_TEMPORAL_LSQ = 1       /* Gaussian least-squares solve (Sec. 5) */
 } sgcp_temporal;
 
+/* History term of the factor solve (Sec. 4.1). */
+typedef enum {
+    SGCP_HISTORY_MODEL = 0,     /* 1/2 sum_h w_h ||Mbar_h - M_h||^2, no slice kept (eq. gcp_stream_problem_2) */
+    SGCP_HISTORY_SLICES = 1     /* sum_h w_h sum_i f(x_ih, m_ih) over the window's stored slices X_h with
+                                   M_h = [[s_h; A]] (eq. gcp_stream_problem_1): the context keeps up to H
+                                   slices on the device; ADAM factor solver only, no checkpoint */
+} sgcp_history_kind;
+
 typedef enum {
     SGCP_OPT_ADAM = 0,          /* Alg. 4 */
     SGCP_OPT_LBFGS = 1          /* projected L-BFGS on the exact objective (dense slices; not in the paper) */
@@ -115,6 +123,8 @@ typedef struct {
     int32_t sparse_cpl;       /* tuning: factor columns per lane in the sparse kernel (4, 8, 16; 0 = auto) */
     int32_t hot_rows;         /* tuning: rows per mode accumulated in shared memory by the sparse kernel
                                  (0..64; -1 = 16); results do not depend on it */
+    int32_t history_kind;     /* SGCP_HISTORY_MODEL (default) or SGCP_HISTORY_SLICES */
+    int32_t reserved;         /* must be 0 */
     uint64_t seed;            /* Philox4x32-10 key for every random draw */
 } sgcp_params;
 

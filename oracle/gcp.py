@@ -49,6 +49,9 @@ LOSSES = ("gaussian", "poisson", "bernoulli_odds", "bernoulli_logit")
 PURPOSE = {
     "grad_nz": 0, "grad_z": 1, "obj_nz": 2, "obj_z": 3, "reservoir": 4,
     "tgrad_nz": 5, "tgrad_z": 6, "tobj_nz": 7, "tobj_z": 8,
+    # stored history slices (eq. gcp_stream_problem_1): counter t-field = the stored slice's own
+    # time index h, draw = t * kappa_f * tau_f + (iteration of the factor solve at step t)
+    "hgrad_nz": 9, "hgrad_z": 10, "hobj_nz": 11, "hobj_z": 12,
 }
 
 
@@ -332,7 +335,7 @@ def sampled_loss(coords, x, weight, s, A, loss, eps=1e-10):
 
 
 def sampled_gradient(coo_idx, coo_val, dims, s, A, loss, p, q, seed, t, draw,
-                     temporal=False, eps=1e-10, cap=64):
+                     temporal=False, eps=1e-10, cap=64, purposes=None):
     """Stochastic gradient from one stratified draw (Alg. 6 then eq. gcp_grad_A / gcp_grad_lambda).
 
     temporal=False uses purposes grad_nz/grad_z and returns the factor
@@ -340,6 +343,8 @@ def sampled_gradient(coo_idx, coo_val, dims, s, A, loss, p, q, seed, t, draw,
     temporal-solver purposes.  Returns (G list, gs, sampled loss on the same samples).
     """
     pn, pz = ("tgrad_nz", "tgrad_z") if temporal else ("grad_nz", "grad_z")
+    if purposes is not None:
+        pn, pz = purposes
     coords, x, w = stratified_samples(coo_idx, coo_val, dims, p, q, seed, t, draw,
                                       PURPOSE[pn], PURPOSE[pz], cap)
     uc, yt = strat_grad_tensor(coords, x, w, s, A, loss, eps)

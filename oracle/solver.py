@@ -80,6 +80,7 @@ class Params:
     lbfgs_mem: int = 5
     lbfgs_iters: int = 10
     seed: int = 0
+    history: str = "model"       # "model": eq. gcp_stream_problem_2; "slices": eq. gcp_stream_problem_1
 
     def lower_bound(self):
         return gcp.default_lower_bound(self.loss) if self.lower is None else self.lower
@@ -181,6 +182,41 @@ def factor_gradient(X, A, s, Abar, s_hist, w_h, P, t, draw):
     return out
 
 
+# ----------------------------------------------------------------------------
+# Stored-slice history (Sec. 4.1, eq. gcp_stream_problem_1): the window keeps the slices X_h
+# themselves and the history term is sum_h w_h sum_i f(x_ih, m_ih) with M_h = [[s_h; A]] (old
+# weights, current factors).  Sparse stored slices are sampled like the current one, with their
+# own purposes, counter t-field h and draw t * kappa_f * tau_f + d (d = 0 for the objective).
+# ----------------------------------------------------------------------------
+def stored_history_gradient(A, hist_X, hist_t, s_hist, w_h, P, t, draw):
+    """sum_h w_h Y_h(k) Z_k diag(s_h), k = 1..d, over the stored slices."""
+    G = [np.zeros(np.shape(a)) for a in A]
+    base = t * P.kappa_f * P.tau_f
+    for X, h, sh, wh in zip(hist_X, hist_t, s_hist, w_h):
+        if X.dense:
+            Gh, _, _ = gcp.dense_gradient(X.X, sh, A, P.loss, P.eps)
+        else:
+            Gh, _, _ = gcp.sampled_gradient(X.idx, X.val, X.dims, sh, A, P.loss, P.p, P.q, P.seed, h, base + draw,
+                                            eps=P.eps, cap=P.cap, purposes=("hgrad_nz", "hgrad_z"))
+        for k in range(len(A)):
+            G[k] += wh * Gh[k]
+    return G
+
+
+def stored_history_objective(A, hist_X, hist_t, s_hist, w_h, P, t):
+    """sum_h w_h sum_i f(x_ih, m_ih) (sampled for sparse stored slices)."""
+    F = 0.0
+    base = t * P.kappa_f * P.tau_f
+    for X, h, sh, wh in zip(hist_X, hist_t, s_hist, w_h):
+        if X.dense:
+            F += wh * gcp.dense_objective(X.X, sh, A, P.loss, P.eps)
+        else:
+            coords, x, w = gcp.stratified_samples(X.idx, X.val, X.dims, P.p_obj, P.q_obj, P.seed, h, base,
+                                                  gcp.PURPOSE["hobj_nz"], gcp.PURPOSE["hobj_z"], P.cap)
+            F += wh * gcp.sampled_loss(coords, x, w, sh, A, P.loss, P.eps)
+    return F
+
+
 def _decide(F_new, F_old, decisions, log):
     own = not (F_new > F_old)
     passed = own if decisions is None else bool(next(decisions))
@@ -248,22 +284,39 @@ def _unflat(v, A):
     return out
 
 
-def fac_gcp_sgd(X, A, s, Abar, s_hist, w_h, P, t, i, adam, decisions=None, log=None):
-    """Alg. 4.  ``adam`` is the persistent AdamFac instance; returns (A, i, F)."""
+def fac_gcp_sgd(X, A, s, Abar, s_hist, w_h, P, t, i, adam, decisions=None, log=None, hist_X=None, hist_t=None):
+    """Alg. 4.  ``adam`` is the persistent AdamFac instance; returns (A, i, F).  With hist_X (the
+    stored slices of the window, P.history == "slices") the history term is that of eq.
+    gcp_stream_problem_1 instead of the model-based penalty."""
     log = [] if log is None else log
     adam.alpha = adam.alpha0
     a = _flat(A)
-    F = estimate_objective(X, A, s, Abar, s_hist, w_h, P.lam, 0.0, P, t, temporal=False)
+    stored = hist_X is not None
+
+    def objective(Av):
+        if stored:
+            return (estimate_objective(X, Av, s, None, [], [], P.lam, 0.0, P, t, temporal=False) +
+                    stored_history_objective(Av, hist_X, hist_t, s_hist, w_h, P, t))
+        return estimate_objective(X, Av, s, Abar, s_hist, w_h, P.lam, 0.0, P, t, temporal=False)
+
+    def gradient(Av, draw):
+        if stored:
+            G = factor_gradient(X, Av, s, None, [], [], P, t, draw)
+            H = stored_history_gradient(Av, hist_X, hist_t, s_hist, w_h, P, t, draw)
+            return [g + h for g, h in zip(G, H)]
+        return factor_gradient(X, Av, s, Abar, s_hist, w_h, P, t, draw)
+
+    F = objective(A)
     draw = 0
     epoch = 0
     while F > P.tol_f and epoch < P.kappa_f:
         F_old = F
         for _ in range(P.tau_f):
-            G = factor_gradient(X, _unflat(a, A), s, Abar, s_hist, w_h, P, t, draw)
+            G = gradient(_unflat(a, A), draw)
             a = adam.step(a, _flat(G), i)
             i += 1
             draw += 1
-        F = estimate_objective(X, _unflat(a, A), s, Abar, s_hist, w_h, P.lam, 0.0, P, t, temporal=False)
+        F = objective(_unflat(a, A))
         if not _decide(F, F_old, decisions, log):
             a = adam.update(a, False)
             F = F_old
@@ -364,6 +417,7 @@ class OnlineGCP:
         self.Abar = [np.array(a, np.float64, copy=True) for a in A0]
         self.hist_t = list(hist_t)
         self.hist_s = [np.array(h, np.float64) for h in hist_s]
+        self.hist_X = []          # stored slices of the window (P.history == "slices")
         self.adam_f = Adam(P.alpha_f, P.beta1, P.beta2, P.adam_eps, P.lower_bound(), P.alpha_decay)
         self.adam_f.init(_flat(self.Abar))
         self.i = 0
@@ -385,20 +439,31 @@ class OnlineGCP:
         if P.optimizer == "lbfgs":
             A, F_f = fac_lbfgs(X, A, s, self.Abar, self.hist_s, w_h, P, t)
         else:
+            stored = P.history == "slices"
             A, self.i, F_f = fac_gcp_sgd(X, A, s, self.Abar, self.hist_s, w_h, P, t, self.i,
-                                         self.adam_f, decisions_f, self.log_f)
-        if P.H > 0:
-            if len(self.hist_t) < P.H:
-                self.hist_t.append(t)
-                self.hist_s.append(s.copy())
-            else:
-                j = reservoir_index(P.seed, t)
-                if j <= P.H:
-                    self.hist_t[j - 1] = t
-                    self.hist_s[j - 1] = s.copy()
+                                         self.adam_f, decisions_f, self.log_f,
+                                         hist_X=self.hist_X if stored else None,
+                                         hist_t=self.hist_t if stored else None)
+        self.enter_window(t, s, X)
         self.Abar = [a.copy() for a in A]
         self.s = s
         return {"F_w": F_w, "F_f": F_f, "s": s}
+
+    def enter_window(self, t, s, X=None):
+        """Alg. 1's reservoir update of the history window with step t (weights s, slice X)."""
+        P = self.P
+        if P.H <= 0:
+            return
+        if len(self.hist_t) < P.H:
+            self.hist_t.append(t)
+            self.hist_s.append(np.array(s, np.float64, copy=True))
+            self.hist_X.append(X)
+        else:
+            j = reservoir_index(P.seed, t)
+            if j <= P.H:
+                self.hist_t[j - 1] = t
+                self.hist_s[j - 1] = np.array(s, np.float64, copy=True)
+                self.hist_X[j - 1] = X
 
 
 # ----------------------------------------------------------------------------
@@ -477,14 +542,6 @@ def warm_start(slices, A0, S0, P, decisions=None, log=None):
     og = OnlineGCP(P, A)
     og.t = len(slices)
     for h in range(1, len(slices) + 1):
-        if P.H > 0:
-            if len(og.hist_t) < P.H:
-                og.hist_t.append(h)
-                og.hist_s.append(S[h - 1].copy())
-            else:
-                j = reservoir_index(P.seed, h)
-                if j <= P.H:
-                    og.hist_t[j - 1] = h
-                    og.hist_s[j - 1] = S[h - 1].copy()
+        og.enter_window(h, S[h - 1], slices[h - 1])
     og.s = S[-1].copy()
     return og, S, F

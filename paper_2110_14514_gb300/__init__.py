@@ -25,6 +25,7 @@ LOSS = {"gaussian": 0, "poisson": 1, "bernoulli_odds": 2, "bernoulli_logit": 3}
 PREC_F32, PREC_F64, PREC_BF16_MTTKRP, PREC_F16_MTTKRP = 0, 1, 2, 3
 TEMPORAL_ADAM, TEMPORAL_LSQ = 0, 1
 OPT_ADAM, OPT_LBFGS = 0, 1
+HISTORY_MODEL, HISTORY_SLICES = 0, 1
 WANT_FACTORS, WANT_TEMPORAL, WANT_LOSS = 1, 2, 4
 SAMPLES_FACTOR_GRAD, SAMPLES_FACTOR_OBJ, SAMPLES_TEMPORAL_GRAD, SAMPLES_TEMPORAL_OBJ = 0, 1, 2, 3
 
@@ -39,7 +40,8 @@ class sgcp_params(ctypes.Structure):
         ("tau_w", c_int32), ("tau_f", c_int32), ("alpha_w", c_double), ("alpha_f", c_double),
         ("beta1", c_double), ("beta2", c_double), ("adam_eps", c_double), ("alpha_decay", c_double),
         ("zero_attempt_cap", c_int32), ("optimizer", c_int32), ("lbfgs_mem", c_int32), ("lbfgs_iters", c_int32),
-        ("sparse_cpl", c_int32), ("hot_rows", c_int32), ("seed", c_uint64),
+        ("sparse_cpl", c_int32), ("hot_rows", c_int32), ("history_kind", c_int32), ("reserved", c_int32),
+        ("seed", c_uint64),
     ]
 
 

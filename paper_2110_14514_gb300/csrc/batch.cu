@@ -185,6 +185,9 @@ sgcp_status check_params(const sgcp_params& p, int s, std::string& why) {
         why = buf;
     };
     if (p.ndim != 3) return bad("batched streams take 3-way slices"), SGCP_ERR_UNSUPPORTED;
+    if (p.reserved != 0) return bad("reserved field not 0"), SGCP_ERR_ARG;
+    if (p.history_kind != SGCP_HISTORY_MODEL)
+        return bad("batched streams use the model-based history penalty"), SGCP_ERR_UNSUPPORTED;
     if (p.precision != SGCP_PREC_F32) return bad("batched streams run in FP32"), SGCP_ERR_UNSUPPORTED;
     if (p.temporal != SGCP_TEMPORAL_ADAM || p.optimizer != SGCP_OPT_ADAM)
         return bad("batched streams use the ADAM temporal and factor solvers"), SGCP_ERR_UNSUPPORTED;

@@ -63,6 +63,16 @@ struct sgcp_ctx {
     int* err = nullptr;
     SliceDesc* slice_dev = nullptr;
     double* metric = nullptr;    // [2]: loss sum and ||X||^2 of sgcp_slice_loss
+    // stored-slice history (SGCP_HISTORY_SLICES): the window's slices themselves, one slot each
+    bool stored_hist = false;
+    int hist_sparse = -1;                  // kind of the stored slices (-1 while none is stored)
+    std::vector<void*> hs_idx, hs_vals;
+    std::vector<size_t> hs_idx_cap, hs_vals_cap, hs_keys_cap;
+    std::vector<void*> hs_keys;
+    SliceDesc* hist_desc = nullptr;        // [H] device descriptors of the slots
+    void* hist_w = nullptr;                // [H] slot weights w theta^(t - h), element type
+    int32_t* hist_skip = nullptr;          // [H] 1: slot inactive or solver finished
+    int32_t* zero_i = nullptr;             // a device 0: the model-based terms see an empty window
 
     // sparse-slice structures
     unsigned long long* hkeys = nullptr;
@@ -291,6 +301,12 @@ sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_i
         ia.err = c->err;
         if (nnz > 0) CK(launch_ingest(ia, nnz, c->stream, &c->launches), "ingest");
     }
+    // The step graph reads the slice through its device descriptor, so the descriptor carries the
+    // hash as well: a larger slice reallocates the table, and the graph (captured once) must not
+    // keep the old table's address and size.
+    c->cur.hkeys = sparse ? c->hkeys : nullptr;
+    c->cur.hlog2 = sparse ? c->hlog2 : 0;
+    c->cur.draw_base = 0;
     c->loaded = true;
     c->loaded_sparse = (int)sparse;
     c->loaded_user_idx = X->idx;
@@ -450,6 +466,85 @@ sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_de
 // One OnlineGCP step (Alg. 1 body minus the host-side reservoir choice),
 // enqueued on c->stream; captured into a graph by build_graph.
 // ---------------------------------------------------------------------------
+// Stored-slice history: the fused kernel on the slice kept in window slot j, at (A, s_h), every y
+// and f scaled by the slot weight w_h; skipped while the slot is inactive or the solver is done.
+// Its samples use their own purposes, the slot's time index and the step's draw base.
+template <typename T>
+sgcp_status enqueue_stored(sgcp_ctx* c, bool sparse, int j, bool obj, uint32_t draw, int want, const void* const* A,
+                           void* const* G, double* f) {
+    const SliceDesc* sd = c->hist_desc + j;
+    const void* sh = offs(c->s_hist, (int64_t)j * c->R, c->esz);
+    const void* wj = offs(c->hist_w, j, c->esz);
+    const int32_t* sk = c->hist_skip + j;
+    if (sparse) {
+        SparseGradArgs a = sparse_args(c, sd, SGCP_SAMPLES_FACTOR_GRAD, draw, want, sh, A, G, nullptr, f, c->P.loss,
+                                       wj, sk);
+        a.pur_nz = obj ? PUR_HOBJ_NZ : PUR_HGRAD_NZ;
+        a.pur_z = a.pur_nz + 1;
+        a.p = obj ? c->P.p_obj : c->P.p;
+        a.q = obj ? c->P.q_obj : c->P.q;
+        a.nhot = 0;
+        CK(launch_sparse_grad(a, a.p + a.q, c->stream, &c->launches), "stored-slice gradient");
+    } else if (c->f64) {
+        DenseGradArgs<double> a = dense_args<double>(c, sd, want, sh, A, G, nullptr, f, c->P.loss, wj, sk);
+        a.xmap = nullptr;
+        CK(launch_dense_grad<double>(a, c->stream, &c->launches), "stored-slice gradient");
+    } else {
+        DenseGradArgs<float> a = dense_args<float>(c, sd, want, sh, A, G, nullptr, f, c->P.loss, wj, sk);
+        a.xmap = nullptr;
+        if (c->tc)
+            CK(launch_dense_grad_tc(a, c->P.precision == SGCP_PREC_BF16_MTTKRP, c->err, c->stream, &c->launches),
+               "stored-slice gradient");
+        else
+            CK(launch_dense_grad<float>(a, c->stream, &c->launches), "stored-slice gradient");
+    }
+    return SGCP_OK;
+}
+
+// Grow a slot buffer to at least `bytes` (contents not kept).
+sgcp_status slot_buffer(sgcp_ctx* c, void** p, size_t* cap, size_t bytes) {
+    if (bytes <= *cap && *p) return SGCP_OK;
+    dfree(c, *p);
+    *p = nullptr;
+    *cap = 0;
+    if (sgcp_status st = dalloc(c, p, bytes)) return st;
+    *cap = bytes;
+    return SGCP_OK;
+}
+
+// Keep slice src (time index t) in window slot `slot`: a copy of its data, its own nonzero hash
+// (sparse), and its device descriptor.  Queued on the context stream after the work that reads it.
+sgcp_status store_slice(sgcp_ctx* c, int slot, bool sparse, const SliceDesc& src, int64_t t) {
+    SliceDesc d{};
+    d.nnz = src.nnz;
+    d.t = t;
+    const size_t vb = (size_t)src.nnz * (sparse ? sizeof(float) : c->esz);
+    if (sgcp_status st = slot_buffer(c, &c->hs_vals[slot], &c->hs_vals_cap[slot], vb)) return st;
+    if (vb) CK(cudaMemcpyAsync(c->hs_vals[slot], src.vals, vb, cudaMemcpyDeviceToDevice, c->stream), "store slice");
+    d.vals = c->hs_vals[slot];
+    if (sparse) {
+        const size_t ib = (size_t)src.nnz * c->ndim * sizeof(int32_t);
+        if (sgcp_status st = slot_buffer(c, &c->hs_idx[slot], &c->hs_idx_cap[slot], ib)) return st;
+        if (ib) CK(cudaMemcpyAsync(c->hs_idx[slot], src.idx, ib, cudaMemcpyDeviceToDevice, c->stream), "store slice");
+        d.idx = (const int32_t*)c->hs_idx[slot];
+        int hl = 10;
+        while (((int64_t)1 << hl) < 2 * src.nnz) ++hl;
+        const size_t kb = ((size_t)1 << hl) * sizeof(unsigned long long);
+        if (sgcp_status st = slot_buffer(c, &c->hs_keys[slot], &c->hs_keys_cap[slot], kb)) return st;
+        CK(cudaMemsetAsync(c->hs_keys[slot], 0xFF, kb, c->stream), "clear slot hash");
+        if (src.nnz > 0) {
+            CK(launch_hash_build(d, c->ndim, c->dims, (unsigned long long*)c->hs_keys[slot], hl, c->err, c->stream),
+               "slot hash");
+            c->launches += 1;
+        }
+        d.hkeys = (const unsigned long long*)c->hs_keys[slot];
+        d.hlog2 = hl;
+    }
+    CK(launch_write_desc(c->hist_desc + slot, d, c->stream, &c->launches), "slot descriptor");
+    c->hist_sparse = sparse ? 1 : 0;
+    return SGCP_OK;
+}
+
 template <typename T>
 sgcp_status enqueue_lbfgs(sgcp_ctx* c);
 
@@ -491,6 +586,12 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     CK(launch_history_SH<T>(R, (const T*)c->s_hist, c->h_dev, c->hist_len_dev, c->slice_dev, P.w, P.theta, c->SH,
                             c->stream, &c->launches),
        "S_H");
+    const bool stored = c->stored_hist;
+    if (stored)
+        CK(launch_hist_slots_begin<T>(c->hist_desc, (T*)c->hist_w, c->hist_skip, c->hist_len_dev, c->h_dev,
+                                      c->slice_dev, P.w, P.theta, P.H, (uint32_t)((int64_t)P.kappa_f * P.tau_f),
+                                      c->stream, &c->launches),
+           "history slots");
 
     // ---------------- temporal weights (Alg. 3, or the least-squares solve) ----------------
     if (P.temporal == SGCP_TEMPORAL_LSQ) {
@@ -549,13 +650,30 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     // ---------------- factor matrices (Alg. 4) ----------------
     SolverState* sf = c->st_f;
     const int32_t* skip = &sf->done;
-    const bool hist_possible = P.H > 0;
+    const bool hist_possible = P.H > 0 && !stored;   // the model-based history terms
     CK(launch_solver_init(sf, P.alpha_f, 0, c->stream, &c->launches), "solver init");
     auto objective_f = [&](int set_cur, const int32_t* sk) -> sgcp_status {
         CK(fork(), "fork");
         sgcp_status st2 = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_OBJ, 0, SGCP_WANT_LOSS, c->s,
                                            Aptr, nullptr, nullptr, &sf->F_new, loss, nullptr, sk);
         if (st2) return st2;
+        if (stored) {
+            // sum_h w_h sum_i f(x_ih, m_ih) over the stored slices, then lambda/2 ||A||^2 from A'A
+            for (int j = 0; j < P.H; ++j)
+                if ((st2 = enqueue_stored<T>(c, sparse, j, true, 0, SGCP_WANT_LOSS, Aptr, nullptr, &sf->F_new)))
+                    return st2;
+            GramArgs<T> g1 = ga;
+            g1.npairs = 1;
+            g1.sel_u[0] = SEL_A;
+            g1.sel_v[0] = SEL_A;
+            g1.skip = sk;
+            CK(launch_gram<T>(g1, c->nrows, c->side, &c->launches), "gram");
+            CK(join(), "join");
+            CK(launch_obj_finish_f(sf, d, R, c->grams, c->SH, c->zero_i, P.lambda, set_cur, c->err, sk, c->stream,
+                                   &c->launches),
+               "obj f");
+            return SGCP_OK;
+        }
         GramArgs<T> g6 = ga;
         g6.npairs = 6;
         const int su[6] = {SEL_A, SEL_ABAR, SEL_ABAR, SEL_D, SEL_D, SEL_ABAR};
@@ -609,6 +727,9 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     for (int e = 0; e < P.kappa_f; ++e) {
         CK(launch_epoch_begin(sf, P.tol_f, c->rates_f, P.tau_f, P.beta1, P.beta2, c->stream, &c->launches),
            "epoch begin");
+        if (stored)
+            CK(launch_hist_slots_skip(c->hist_skip, c->hist_len_dev, &sf->done, P.H, c->stream, &c->launches),
+               "history slots");
         for (int it = 0; it < P.tau_f; ++it) {
             fu.rate = c->rates_f + it;
             if (fused) {
@@ -622,6 +743,10 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
                                   SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip);
             if (st) return st;
+            for (int j = 0; stored && j < P.H; ++j)   // + sum_h w_h Y_h(k) Z_k diag(s_h)
+                if ((st = enqueue_stored<T>(c, sparse, j, false, (uint32_t)(e * P.tau_f + it), SGCP_WANT_FACTORS, Aptr,
+                                            Gptr, nullptr)))
+                    return st;
             if (chain) {
                 // history coefficients from the current A, beside the gradient kernel
                 GramArgs<T> g2 = ga;
@@ -1019,10 +1144,13 @@ sgcp_status warm_start_impl(sgcp_ctx* c, int n, const sgcp_slice* X, const void*
                 c->hist_t[slot] = h;
             }
         }
-        if (slot >= 0)
+        if (slot >= 0) {
             CK(launch_hist_update<T>(R, (T*)c->s_hist, c->h_dev, c->hist_len_dev, slot, h, len,
                                      (const T*)offs(S, (int64_t)(h - 1) * R, sizeof(T)), st, &c->launches),
                "history");
+            if (c->stored_hist)
+                if (sgcp_status e = store_slice(c, slot, sparse, desc[h - 1], h)) return e;
+        }
     }
     SolverState fin{};
     CK(cudaMemcpyAsync(&fin, sw, sizeof(fin), cudaMemcpyDeviceToHost, st), "read state");
@@ -1174,6 +1302,9 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     for (int k = 0; k < P.ndim; ++k)   // row offsets are 32-bit inside the kernels
         if ((double)P.dims[k] * P.rank >= 2147483648.0) return SGCP_ERR_UNSUPPORTED;
     if (P.sparse_cpl != 0 && P.sparse_cpl != 4 && P.sparse_cpl != 8 && P.sparse_cpl != 16) return SGCP_ERR_ARG;
+    if ((P.history_kind != SGCP_HISTORY_MODEL && P.history_kind != SGCP_HISTORY_SLICES) || P.reserved != 0)
+        return SGCP_ERR_ARG;
+    if (P.history_kind == SGCP_HISTORY_SLICES && P.optimizer != SGCP_OPT_ADAM) return SGCP_ERR_UNSUPPORTED;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1183,6 +1314,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     sgcp_ctx* c = new (std::nothrow) sgcp_ctx();
     if (!c) return SGCP_ERR_OOM;
     c->P = P;
+    c->stored_hist = P.history_kind == SGCP_HISTORY_SLICES && P.H > 0;
     if (allocator) {
         c->ualloc = *allocator;
         c->custom_alloc = true;
@@ -1243,8 +1375,13 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
         (st = dalloc_t(c, &c->grams, 6 * c->ndim * RR * sizeof(double))) ||
         (st = dalloc(c, &c->gpart, (size_t)6 * c->ndim * c->gram_nblk * RR * c->esz)) ||
         (st = dalloc(c, &c->Bc, c->ndim * RR * c->esz)) || (st = dalloc(c, &c->Cc, c->ndim * RR * c->esz)) ||
-        (c->esz == 4 && c->R <= 32 && P.H > 0 &&
+        (c->esz == 4 && c->R <= 32 && P.H > 0 && !c->stored_hist &&
          (st = dalloc_t(c, &c->gacc, 4 * (size_t)c->ndim * RR * sizeof(float)))) ||
+        (c->stored_hist &&
+         ((st = dalloc_t(c, &c->hist_desc, (size_t)P.H * sizeof(SliceDesc))) ||
+          (st = dalloc(c, &c->hist_w, (size_t)P.H * c->esz)) ||
+          (st = dalloc_t(c, &c->hist_skip, (size_t)P.H * sizeof(int32_t))) ||
+          (st = dalloc_t(c, &c->zero_i, sizeof(int32_t))))) ||
         (st = dalloc_t(c, &c->lsq_work, (RR + c->R) * sizeof(double))) ||
         (st = dalloc_t(c, &c->st_w, sizeof(SolverState))) || (st = dalloc_t(c, &c->st_f, sizeof(SolverState))) ||
         (st = dalloc_t(c, &c->rates_w, (P.tau_w > 0 ? P.tau_w : 1) * sizeof(double))) ||
@@ -1294,6 +1431,17 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(int), s);
     if (e == cudaSuccess && c->gacc) e = cudaMemsetAsync(c->gacc, 0, 4 * (size_t)c->ndim * RR * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->Bc, 0, c->ndim * RR * c->esz, s);
+    if (c->stored_hist) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_desc, 0, (size_t)P.H * sizeof(SliceDesc), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->hist_skip, 0xFF, (size_t)P.H * sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->zero_i, 0, sizeof(int32_t), s);
+        c->hs_idx.assign(P.H, nullptr);
+        c->hs_vals.assign(P.H, nullptr);
+        c->hs_keys.assign(P.H, nullptr);
+        c->hs_idx_cap.assign(P.H, 0);
+        c->hs_vals_cap.assign(P.H, 0);
+        c->hs_keys_cap.assign(P.H, 0);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->Cc, 0, c->ndim * RR * c->esz, s);
     std::vector<int64_t> hv(Hs, 0);
     for (int i = 0; i < n_hist; ++i) {
@@ -1402,6 +1550,8 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
         return fail(c, SGCP_ERR_ARG, "step: sparse slices need p + q > 0 and p_obj + q_obj > 0");
     if (sparse && c->P.optimizer == SGCP_OPT_LBFGS)
         return fail(c, SGCP_ERR_UNSUPPORTED, "step: the L-BFGS factor solver needs dense slices");
+    if (c->stored_hist && c->hist_sparse >= 0 && c->hist_sparse != (sparse ? 1 : 0))
+        return fail(c, SGCP_ERR_ARG, "step: a stored-slice history holds slices of one kind (all dense or all sparse)");
     if (sgcp_status st = load_slice(c, X, t, false)) return st;
     CK(launch_write_desc(c->slice_dev, c->cur, c->stream, &c->launches), "slice descriptor");
     if (!sparse)
@@ -1434,6 +1584,8 @@ sgcp_status sgcp_step(sgcp_ctx* c, const sgcp_slice* X) {
                                                                slot, t, len, (const float*)c->s, c->stream,
                                                                &c->launches);
             if (e != cudaSuccess) return cuda_fail(c, e, "history update");
+            if (c->stored_hist)
+                if (sgcp_status st = store_slice(c, slot, sparse, c->cur, t)) return st;
         }
     }
     c->t = t;
@@ -1643,12 +1795,14 @@ static size_t ckpt_size(const sgcp_ctx* c) {
 
 sgcp_status sgcp_state_size(const sgcp_ctx* c, size_t* size) {
     if (!c || !size) return SGCP_ERR_ARG;
+    if (c->stored_hist) return SGCP_ERR_UNSUPPORTED;   // the stored slices are not part of a checkpoint
     *size = ckpt_size(c);
     return SGCP_OK;
 }
 
 sgcp_status sgcp_state_export(sgcp_ctx* c, void* buf, size_t size) {
     if (!c || !buf) return SGCP_ERR_ARG;
+    if (c->stored_hist) return fail(c, SGCP_ERR_UNSUPPORTED, "state_export: a stored-slice history is not checkpointed");
     if (size < ckpt_size(c)) return fail(c, SGCP_ERR_ARG, "state_export: buffer too small");
     if (sgcp_status st = sgcp_check(c)) return st;
     const int Hs = c->P.H > 0 ? c->P.H : 1;
@@ -1682,6 +1836,7 @@ sgcp_status sgcp_state_export(sgcp_ctx* c, void* buf, size_t size) {
 
 sgcp_status sgcp_state_import(sgcp_ctx* c, const void* buf, size_t size) {
     if (!c || !buf) return SGCP_ERR_ARG;
+    if (c->stored_hist) return fail(c, SGCP_ERR_UNSUPPORTED, "state_import: a stored-slice history is not checkpointed");
     if (sgcp_status st = check_ready(c)) return st;
     if (size < ckpt_size(c)) return fail(c, SGCP_ERR_ARG, "state_import: buffer too small");
     const CkptHeader* h = (const CkptHeader*)buf;

@@ -26,7 +26,8 @@ enum ErrBits : int {
 // Purposes of the Philox counter (high byte of counter word 3).
 enum Purpose : uint32_t {
     PUR_GRAD_NZ = 0, PUR_GRAD_Z = 1, PUR_OBJ_NZ = 2, PUR_OBJ_Z = 3, PUR_RESERVOIR = 4,
-    PUR_TGRAD_NZ = 5, PUR_TGRAD_Z = 6, PUR_TOBJ_NZ = 7, PUR_TOBJ_Z = 8
+    PUR_TGRAD_NZ = 5, PUR_TGRAD_Z = 6, PUR_TOBJ_NZ = 7, PUR_TOBJ_Z = 8,
+    PUR_HGRAD_NZ = 9, PUR_HGRAD_Z = 10, PUR_HOBJ_NZ = 11, PUR_HOBJ_Z = 12   // stored history slices
 };
 
 // Loss ids; LOSS_IDENTITY_X is internal: y = x, f = 0 (gives Z' vec(X) for the
@@ -133,7 +134,12 @@ struct SliceDesc {
     const int32_t* idx;   // sparse: [nnz][ndim]
     const void* vals;     // sparse: [nnz]; dense: full slice, C order
     int64_t nnz;          // sparse: number of nonzeros; dense: prod I_k
-    int64_t t;            // time index of the slice
+    int64_t t;            // time index of the slice (the sample counter's t-field)
+    // A slice kept in the history window (stored-slice history) carries its own nonzero hash and
+    // a draw base added to every sample draw index; both are null / 0 for the current slice.
+    const unsigned long long* hkeys;
+    int32_t hlog2;
+    uint32_t draw_base;
 };
 
 // Device-resident scalars of one solver (Alg. 2-4).

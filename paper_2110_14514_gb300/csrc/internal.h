@@ -290,6 +290,15 @@ template <typename T>
 cudaError_t launch_congruence(int nm, int R, const int64_t* dims, const T* const* A, const T* const* B,
                               double* C, double* na, double* nb, double* score, int32_t* perm, cudaStream_t st);
 
+// Stored-slice history: per-step slot weights / draw bases / skip flags, and the skip flags after
+// each epoch test (inactive slot or finished solver).
+template <typename T>
+cudaError_t launch_hist_slots_begin(SliceDesc* desc, T* wts, int32_t* skip, const int32_t* hist_len,
+                                    const int64_t* h_dev, const SliceDesc* cur, double w, double theta, int H,
+                                    uint32_t per_step, cudaStream_t st, int64_t* launches);
+cudaError_t launch_hist_slots_skip(int32_t* skip, const int32_t* hist_len, const int32_t* done, int H,
+                                   cudaStream_t st, int64_t* launches);
+
 // Small helpers.
 template <typename T>
 cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, int64_t* launches);

@@ -1164,6 +1164,46 @@ cudaError_t launch_reg_objective(SolverState* st, const T* W, int64_t n, double 
     return cudaGetLastError();
 }
 
+// Stored-slice history (eq. gcp_stream_problem_1), at the start of a step: window slot j is
+// active when j < |window|; its weight w_j = w theta^(t - h_j) becomes the y_scale of its launches,
+// its descriptor's draw base t * per_step keeps its samples distinct from every other step's,
+// and its skip flag is set when it is inactive.
+template <typename T>
+__global__ void k_hist_slots_begin(SliceDesc* desc, T* wts, int32_t* skip, const int32_t* hist_len,
+                                   const int64_t* h_dev, const SliceDesc* cur, double w, double theta, int H,
+                                   uint32_t per_step) {
+    const int n = *hist_len;
+    const int64_t t = cur->t;
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+        const bool on = j < n;
+        wts[j] = on ? (T)(w * pow(theta, (double)(t - h_dev[j]))) : T(0);
+        skip[j] = on ? 0 : 1;
+        desc[j].draw_base = (uint32_t)((uint64_t)t * per_step);
+    }
+}
+
+template <typename T>
+cudaError_t launch_hist_slots_begin(SliceDesc* desc, T* wts, int32_t* skip, const int32_t* hist_len,
+                                    const int64_t* h_dev, const SliceDesc* cur, double w, double theta, int H,
+                                    uint32_t per_step, cudaStream_t st, int64_t* launches) {
+    k_hist_slots_begin<T><<<1, 128, 0, st>>>(desc, wts, skip, hist_len, h_dev, cur, w, theta, H, per_step);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// After each epoch test of the factor solver: a slot also skips once the solver has finished.
+__global__ void k_hist_slots_skip(int32_t* skip, const int32_t* hist_len, const int32_t* done, int H) {
+    const int n = *hist_len, d = *done;
+    for (int j = threadIdx.x; j < H; j += blockDim.x) skip[j] = (j >= n || d) ? 1 : 0;
+}
+
+cudaError_t launch_hist_slots_skip(int32_t* skip, const int32_t* hist_len, const int32_t* done, int H,
+                                   cudaStream_t st, int64_t* launches) {
+    k_hist_slots_skip<<<1, 128, 0, st>>>(skip, hist_len, done, H);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_copy(T* dst, const T* src, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1196,6 +1236,9 @@ cudaError_t launch_copy(T* dst, const T* src, int64_t n, cudaStream_t stream, in
     template cudaError_t launch_lsq_solve<T>(int, int, const double*, const T*, double, double, T*, double*, int*,   \
                                              cudaStream_t, int64_t*);                                                 \
     template cudaError_t launch_copy<T>(T*, const T*, int64_t, cudaStream_t, int64_t*);                          \
+    template cudaError_t launch_hist_slots_begin<T>(SliceDesc*, T*, int32_t*, const int32_t*, const int64_t*,     \
+                                                    const SliceDesc*, double, double, int, uint32_t, cudaStream_t, \
+                                                    int64_t*);                                                       \
     template cudaError_t launch_reg_objective<T>(SolverState*, const T*, int64_t, double, int, int*, const int32_t*, \
                                                  cudaStream_t, int64_t*);                                            \
     template cudaError_t launch_lbfgs_begin<T>(const LbfgsArgs<T>&, cudaStream_t, int64_t*);                      \

@@ -77,10 +77,11 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
     for (int k = 0; k < D; ++k) ci[k] = 0;
     if (c >= z.total) return;
     const float* vals = (const float*)sd.vals;
+    const uint32_t draw = a.draw + sd.draw_base;
     if (a.all_nnz || c < z.p_eff) {
         int64_t e = c;
         if (!a.all_nnz) {
-            uint32_t ctr[4] = {(uint32_t)c, 0u, a.draw, counter_word3(a.pur_nz, sd.t)};
+            uint32_t ctr[4] = {(uint32_t)c, 0u, draw, counter_word3(a.pur_nz, sd.t)};
             philox4x32_10(ctr, a.key0, a.key1);
             e = bounded_u32(ctr[0], (uint32_t)sd.nnz);
         }
@@ -105,8 +106,10 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
     }
     const uint32_t cz = (uint32_t)(c - z.p_eff);
     const uint32_t w3 = counter_word3(a.pur_z, sd.t);
+    const unsigned long long* hk = sd.hkeys ? sd.hkeys : a.hkeys;   // a stored slice's own hash
+    const int hl = sd.hkeys ? sd.hlog2 : a.hlog2;
     for (int att = 0; att < a.cap; ++att) {
-        uint32_t ctr[4] = {cz, (uint32_t)att, a.draw, w3};
+        uint32_t ctr[4] = {cz, (uint32_t)att, draw, w3};
         philox4x32_10(ctr, a.key0, a.key1);
         unsigned long long key = 0;
 #pragma unroll
@@ -114,7 +117,7 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
             ci[k] = (int)bounded_u32(ctr[k], (uint32_t)a.dims[k]);
             key = key * (unsigned long long)a.dims[k] + (unsigned long long)ci[k];
         }
-        if (!hash_contains(a.hkeys, a.hlog2, key)) {
+        if (!hash_contains(hk, hl, key)) {
             w = z.w_z;
             attempt = att;
             ok = true;

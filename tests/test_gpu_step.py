@@ -129,7 +129,9 @@ def test_sparse_stream_matches_oracle(sg, loss):
     A0 = [(0.3 * rng.random((n, R)) + 0.05).astype(np.float32) for n in dims]
     slices = []
     for t in range(1, 5):
-        idx, val = S.sparse_slice(cfg, t, nnz=4000, dims=dims)
+        # growing slices: the second one needs a larger nonzero hash (2^14 slots instead of 2^13),
+        # which the step graph, captured at the first step, must then use
+        idx, val = S.sparse_slice(cfg, t, nnz=3000 + 800 * t, dims=dims)
         slices.append({"idx": idx, "val": val})
     kw = dict(H=2, w=1.0, kappa_w=2, tau_w=6, alpha_w=0.05, kappa_f=2, tau_f=6, alpha_f=0.01,
               p=800, q=800, p_obj=1500, q_obj=1500, seed=99)
@@ -295,3 +297,62 @@ def test_lbfgs_step_is_one_asynchronous_graph(sg):
     for a, b in zip(A, Ar):
         assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
     assert rel(s.cpu().numpy(), sr.cpu().numpy()) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["dense_fp64", "dense_fp32", "sparse"])
+def test_stored_slice_history_stream_matches_oracle(sg, kind):
+    """The stored-slice history of eq. gcp_stream_problem_1: the window keeps the slices, and the
+    factor solve adds sum_h w_h sum_i f(x_ih, m_ih) at (A, s_h) (sampled per stored slice for
+    sparse slices).  H = 2 over 5 slices so the reservoir replaces stored slices; FP64 with the
+    GPU's own decisions, FP32 teacher-forced."""
+    if kind == "sparse":
+        dims, R = (120, 90, 60), 8
+        cfg = S.workload("sparse_binary_zipf")
+        rng = np.random.default_rng(8)
+        A0 = [(0.3 * rng.random((n, R)) + 0.05).astype(np.float32) for n in dims]
+        slices = [dict(zip(("idx", "val"), S.sparse_slice(cfg, t, nnz=3000 + 500 * t, dims=dims)))
+                  for t in range(1, 6)]
+        kw = dict(H=2, w=1.5, theta=0.8, kappa_w=2, tau_w=5, alpha_w=0.05, kappa_f=2, tau_f=5, alpha_f=0.01,
+                  p=700, q=700, p_obj=1200, q_obj=1200, seed=19)
+        loss, prec, tol, ftol = "bernoulli_logit", sg.PREC_F32, 2e-4, 1e-4
+    elif kind == "dense_fp32":
+        dims, R = (30, 25, 20), 8
+        rng = np.random.default_rng(9)
+        At = [rng.random((n, R)) for n in dims]
+        A0 = [(a + 0.1 * rng.random(a.shape)).astype(np.float32) for a in At]
+        slices = [{"X": rng.poisson(np.einsum("ir,jr,kr,r->ijk", *At, rng.random(R))).astype(np.float32)}
+                  for _ in range(5)]
+        kw = dict(H=2, w=2.0, theta=0.9, kappa_w=2, tau_w=8, alpha_w=0.05, kappa_f=2, tau_f=8, alpha_f=0.005, seed=5)
+        loss, prec, tol, ftol = "poisson", sg.PREC_F32, 2e-4, 1e-4
+    else:
+        cfg = S.workload("dense_gaussian_2way")
+        dims, R = cfg["dims"], cfg["rank"]
+        A0 = S.init_factors(cfg)
+        slices = [{"X": S.dense_slice(cfg, t)[0]} for t in range(1, 6)]
+        kw = dict(H=2, w=1.0, theta=0.9, lam=0.01, kappa_w=2, tau_w=6, alpha_w=0.05, kappa_f=3, tau_f=6,
+                  alpha_f=0.02, seed=23)
+        loss, prec, tol, ftol = "gaussian", sg.PREC_F64, 1e-9, 1e-9
+    p = sg.params(dims, R, loss, precision=prec, history_kind=sg.HISTORY_SLICES, **kw)
+    okw = dict(dims=dims, rank=R, loss=loss, history="slices", **kw)
+    run_stream(sg, p, A0, slices, okw, tol=tol, ftol=ftol, check_own=(kind == "dense_fp64"))
+
+
+def test_stored_slice_history_rejects_lbfgs_mixed_slices_and_checkpoints(sg):
+    cfg = S.workload("dense_gaussian_2way")
+    A0 = [dev(a) for a in S.init_factors(cfg)]
+    with pytest.raises(sg.SgcpError) as e:
+        sg.Context(sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=sg.PREC_F64, H=2,
+                             history_kind=sg.HISTORY_SLICES, optimizer=sg.OPT_LBFGS), A0)
+    assert e.value.status == sg.ERR_UNSUPPORTED
+    p = sg.params(cfg["dims"], cfg["rank"], "gaussian", H=2, history_kind=sg.HISTORY_SLICES, kappa_w=1, tau_w=2,
+                  kappa_f=1, tau_f=2, p=10, q=10, p_obj=10, q_obj=10)
+    A32 = [a.float() for a in A0]
+    with sg.Context(p, A32) as ctx:
+        ctx.step(X=dev(S.dense_slice(cfg, 1)[0].astype(np.float32)))
+        idx = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(sg.SgcpError) as e:
+            ctx.step(idx=idx, vals=torch.ones(1, device="cuda"))
+        assert e.value.status == sg.ERR_ARG
+        with pytest.raises(sg.SgcpError) as e:
+            ctx.state_export()
+        assert e.value.status == sg.ERR_UNSUPPORTED
