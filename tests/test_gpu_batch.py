@@ -56,7 +56,7 @@ def make_streams(n_steps, seed=3, shapes=SHAPES):
     return streams
 
 
-def run_and_compare(sg, streams, n_steps, tol, batch_kw=None, host=False, ftol=1e-4):
+def run_and_compare(sg, streams, n_steps, tol, batch_kw=None, host=False, ftol=1e-5):
     """Every stream against its own oracle stream after every step: s and the factor matrices within
     `tol` (per-array relative Frobenius error), the objective estimates within `ftol`."""
     plist = [sg.params(st["dims"], st["R"], st["loss"], seed=st["seed"], **KW) for st in streams]
@@ -89,7 +89,7 @@ def run_and_compare(sg, streams, n_steps, tol, batch_kw=None, host=False, ftol=1
 
 def test_batched_streams_match_their_oracles(sg):
     streams = make_streams(3)
-    run_and_compare(sg, streams, 3, tol=2e-4)
+    run_and_compare(sg, streams, 3, tol=2e-5)
 
 
 # the large end of the batched workload: ranks 48 and 64 (the 64-column register tiles), modes of
@@ -99,25 +99,27 @@ SHAPES_LARGE = [((130, 40, 36), 48, "gaussian"), ((33, 150, 47), 64, "poisson"),
 
 
 def test_batched_streams_at_ranks_48_and_64_with_long_modes(sg):
+    """(Every gradient element of these slices sums up to 2e5 FP32 terms -- 130 x 40 x 36 -- whose
+    rounding errors add up to ~sqrt(n) 2^-24 ~ 3e-5 relative, hence 1e-4 for the state.)"""
     streams = make_streams(2, seed=13, shapes=SHAPES_LARGE)
-    run_and_compare(sg, streams, 2, tol=2e-4)
+    run_and_compare(sg, streams, 2, tol=1e-4)
 
 
 def test_batched_streams_host_slices(sg):
     """x_on_host = 1: the call copies the host slices itself."""
     streams = make_streams(2, seed=5)
-    run_and_compare(sg, streams, 2, tol=2e-4, host=True)
+    run_and_compare(sg, streams, 2, tol=2e-5, host=True)
 
 
 def test_autotuned_unit_shapes_keep_parity(sg):
     streams = make_streams(2, seed=7, shapes=SHAPES[:3])
-    table, cfg = run_and_compare(sg, streams, 2, tol=2e-4, batch_kw=dict(autotune=True, tune_reps=2))
+    table, cfg = run_and_compare(sg, streams, 2, tol=2e-5, batch_kw=dict(autotune=True, tune_reps=2))
     assert len(table) == 3 and all(e["us"] > 0 for e in table)
     for e in cfg:
         assert 2 <= e["b1log"] <= 4 and (1 << e["b1log"]) * e["n1"] <= 32 and (64 >> e["b1log"]) * e["n2"] <= 32
     # a later batch reuses the table without timing again
     streams2 = make_streams(1, seed=8, shapes=SHAPES[:3])
-    table2, cfg2 = run_and_compare(sg, streams2, 1, tol=2e-4, batch_kw=dict(table=table))
+    table2, cfg2 = run_and_compare(sg, streams2, 1, tol=2e-5, batch_kw=dict(table=table))
     assert cfg2 == cfg and len(table2) == 3
 
 
@@ -127,7 +129,7 @@ def test_single_shape_choice_across_tiles(sg):
     streams = make_streams(1, seed=9, shapes=[((45, 37, 40), 8, "gaussian")])
     key = dict(bucket=(2, 2, 2), rank=8, loss=0, us=0.0)
     for b1log, n1, n2 in [(2, 1, 1), (2, 8, 2), (3, 2, 1), (4, 2, 8)]:
-        run_and_compare(sg, streams, 1, tol=2e-4, batch_kw=dict(table=[dict(key, b1log=b1log, n1=n1, n2=n2)]))
+        run_and_compare(sg, streams, 1, tol=2e-5, batch_kw=dict(table=[dict(key, b1log=b1log, n1=n1, n2=n2)]))
 
 
 def test_spin_limit_reports_timeout_without_hanging(sg):

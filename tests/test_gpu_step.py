@@ -118,7 +118,7 @@ def test_dense_3way_fp32_poisson_stream(sg):
     kw = dict(H=2, w=2.0, kappa_w=2, tau_w=10, alpha_w=0.05, kappa_f=2, tau_f=10, alpha_f=0.005, seed=5)
     p = sg.params(dims, R, "poisson", **kw)
     okw = dict(dims=dims, rank=R, loss="poisson", **kw)
-    run_stream(sg, p, A0, slices, okw, tol=2e-4, ftol=1e-4)
+    run_stream(sg, p, A0, slices, okw, tol=2e-5, ftol=1e-5)
 
 
 @pytest.mark.parametrize("loss", ["bernoulli_logit", "poisson"])
@@ -137,7 +137,7 @@ def test_sparse_stream_matches_oracle(sg, loss):
               p=800, q=800, p_obj=1500, q_obj=1500, seed=99)
     p = sg.params(dims, R, loss, **kw)
     okw = dict(dims=dims, rank=R, loss=loss, **kw)
-    run_stream(sg, p, A0, slices, okw, tol=2e-4, ftol=1e-4)
+    run_stream(sg, p, A0, slices, okw, tol=2e-5, ftol=1e-5)
 
 
 @pytest.mark.parametrize("R,alpha_f", [(12, 0.01), (32, 0.01), (32, 3.0)])
@@ -158,7 +158,7 @@ def test_sparse_fp32_history_factor_update_ranks_and_rollbacks(sg, R, alpha_f):
               p=900, q=900, p_obj=1500, q_obj=1500, seed=31)
     p = sg.params(dims, R, "bernoulli_logit", **kw)
     okw = dict(dims=dims, rank=R, loss="bernoulli_logit", **kw)
-    ctx = run_stream(sg, p, A0, slices, okw, tol=2e-4, ftol=1e-4)
+    ctx = run_stream(sg, p, A0, slices, okw, tol=2e-5, ftol=1e-5)
     if alpha_f > 1.0:
         st = ctx.last_stats
         assert st["epochs_f"] > 0 and st["accept_f"] != (1 << st["epochs_f"]) - 1, "no epoch was rejected"
@@ -180,7 +180,7 @@ def test_sparse_fp32_history_two_and_four_way(sg, dims, nnz, pq):
               p=pq, q=pq, p_obj=pq, q_obj=pq, seed=17)
     p = sg.params(dims, R, "bernoulli_logit", **kw)
     okw = dict(dims=dims, rank=R, loss="bernoulli_logit", **kw)
-    run_stream(sg, p, A0, slices, okw, tol=2e-4, ftol=1e-4)
+    run_stream(sg, p, A0, slices, okw, tol=2e-5, ftol=1e-5)
 
 
 def test_full_size_sparse_step_with_history(sg):
@@ -200,7 +200,7 @@ def test_full_size_sparse_step_with_history(sg):
               p=cfg["p"], q=cfg["q"], p_obj=cfg["p_obj"], q_obj=cfg["q_obj"], seed=2025)
     p = sg.params(dims, R, cfg["loss"], **kw)
     okw = dict(dims=dims, rank=R, loss=cfg["loss"], **kw)
-    ctx = run_stream(sg, p, A0, slices, okw, tol=2e-4, ftol=1e-4)
+    ctx = run_stream(sg, p, A0, slices, okw, tol=2e-5, ftol=1e-5)
     assert ctx.last_stats["hist_len"] == 2   # step 2 solved against the window {1}, then added itself
 
 
@@ -314,7 +314,7 @@ def test_stored_slice_history_stream_matches_oracle(sg, kind):
                   for t in range(1, 6)]
         kw = dict(H=2, w=1.5, theta=0.8, kappa_w=2, tau_w=5, alpha_w=0.05, kappa_f=2, tau_f=5, alpha_f=0.01,
                   p=700, q=700, p_obj=1200, q_obj=1200, seed=19)
-        loss, prec, tol, ftol = "bernoulli_logit", sg.PREC_F32, 2e-4, 1e-4
+        loss, prec, tol, ftol = "bernoulli_logit", sg.PREC_F32, 2e-5, 1e-5
     elif kind == "dense_fp32":
         dims, R = (30, 25, 20), 8
         rng = np.random.default_rng(9)
@@ -323,7 +323,7 @@ def test_stored_slice_history_stream_matches_oracle(sg, kind):
         slices = [{"X": rng.poisson(np.einsum("ir,jr,kr,r->ijk", *At, rng.random(R))).astype(np.float32)}
                   for _ in range(5)]
         kw = dict(H=2, w=2.0, theta=0.9, kappa_w=2, tau_w=8, alpha_w=0.05, kappa_f=2, tau_f=8, alpha_f=0.005, seed=5)
-        loss, prec, tol, ftol = "poisson", sg.PREC_F32, 2e-4, 1e-4
+        loss, prec, tol, ftol = "poisson", sg.PREC_F32, 2e-5, 1e-5
     else:
         cfg = S.workload("dense_gaussian_2way")
         dims, R = cfg["dims"], cfg["rank"]

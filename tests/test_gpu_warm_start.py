@@ -106,7 +106,7 @@ def test_warm_start_dense_3way_fp32_poisson_from_given_weights(sg):
         og, S_o, F_o = solver.warm_start([solver.Slice(dims=dims, X=x) for x in Xs], A0, S0,
                                          solver.Params(dims=dims, rank=R, loss="poisson", **kw),
                                          decisions=iter(bits(st["accept"], st["epochs"])))
-        check_warm(sg, ctx, og, S_gpu, S_o, st, F_o, 2e-4, 1e-4)
+        check_warm(sg, ctx, og, S_gpu, S_o, st, F_o, 2e-5, 1e-5)
 
 
 def test_warm_start_sparse_fp32_with_host_slices_then_the_stream(sg):
@@ -125,8 +125,8 @@ def test_warm_start_sparse_fp32_with_host_slices_then_the_stream(sg):
         S_gpu, st = ctx.warm_start([(torch.from_numpy(i), torch.from_numpy(v)) for i, v in sl[:n]])
         og, S_o, F_o = solver.warm_start([solver.Slice(dims=dims, idx=i, val=v) for i, v in sl[:n]], A0,
                                          np.ones((n, R)), P, decisions=iter(bits(st["accept"], st["epochs"])))
-        check_warm(sg, ctx, og, S_gpu, S_o, st, F_o, 2e-4, 1e-4)
-        continue_stream(ctx, og, [{"idx": i, "val": v} for i, v in sl[n:]], 2e-4, 1e-4)
+        check_warm(sg, ctx, og, S_gpu, S_o, st, F_o, 2e-5, 1e-5)
+        continue_stream(ctx, og, [{"idx": i, "val": v} for i, v in sl[n:]], 2e-5, 1e-5)
 
 
 def test_warm_start_needs_a_fresh_context(sg):
