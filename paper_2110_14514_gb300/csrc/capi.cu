@@ -425,10 +425,11 @@ TemporalStep<T> make_tstep(sgcp_ctx* c, const TStepSpec* ts) {
 sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_dev, int set, uint32_t draw, int want,
                              const void* s, const void* const* A, void* const* G, void* gs, double* f, int loss,
                              const void* y_scale, const int32_t* skip, int all_nnz = 0,
-                             const TStepSpec* tstep = nullptr) {
+                             const TStepSpec* tstep = nullptr, bool overlap = false) {
     if (sparse) {
         SparseGradArgs a = sparse_args(c, slice_dev, set, draw, want, s, A, G, gs, f, loss, y_scale, skip);
         a.all_nnz = all_nnz;
+        a.overlap = overlap ? 1 : 0;
         if (tstep) {
             a.tstep_on = 1;
             a.tstep = make_tstep<float>(c, tstep);
@@ -625,9 +626,10 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
                "epoch begin");
             for (int it = 0; it < P.tau_w; ++it) {
                 tsw.rate = c->rates_w + it;
+                // a chain of gradient kernels: each one's sampling overlaps the one before
                 st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD, (uint32_t)(e * P.tau_w + it),
                                       SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs, nullptr, loss, nullptr, skip, 0,
-                                      &tsw);
+                                      &tsw, true);
                 if (st) return st;
             }
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s, Aptr,
@@ -740,8 +742,11 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
             }
             const bool chain = hist_possible && (!fused || it == 0);
             if (chain) CK(fork(), "fork");
+            // gradient and update overlap their neighbours in the chain (the update only when no
+            // side-stream join precedes it)
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
-                                  SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip);
+                                  SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip, 0,
+                                  nullptr, true);
             if (st) return st;
             for (int j = 0; stored && j < P.H; ++j)   // + sum_h w_h Y_h(k) Z_k diag(s_h)
                 if ((st = enqueue_stored<T>(c, sparse, j, false, (uint32_t)(e * P.tau_f + it), SGCP_WANT_FACTORS, Aptr,
@@ -762,6 +767,7 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
                    "hist coeffs");
                 CK(join(), "join");
             }
+            fu.overlap = chain ? 0 : 1;
             CK(launch_factor_update<T>(fu, c->stream, &c->launches), "factor update");
         }
         st = objective_f(0, skip);

@@ -239,4 +239,16 @@ __device__ __forceinline__ void set_err(int* err, int bits) {
     if (err) atomicOr(err, bits);
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the kernel before it in the stream is still
+// running; grid_dep_wait() returns once that kernel has completed and its
+// writes are visible (at once for a kernel launched without the attribute).
+// Everything before the wait may read only data that no kernel of the last
+// two in the stream writes, and may write nothing in global memory.
+// grid_dep_launch() lets the next kernel start; it is issued after the wait,
+// so a kernel that starts early always finds every kernel but its immediate
+// predecessor complete.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace sgcp

@@ -9,6 +9,25 @@
 
 namespace sgcp {
 
+// Launches kern<<<grid, block, smem, st>>>(args...) with programmatic stream serialization: the
+// kernel may start while the previous kernel in the stream runs, so it must call grid_dep_wait()
+// before it touches anything that kernel writes or reads.
+template <typename... P, typename... Args>
+inline cudaError_t launch_after_prev(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
 // Arguments of the fused sparse sample -> model -> y -> MTTKRP kernel.
 struct SparseGradArgs {
     const SliceDesc* slice;          // device descriptor (graph path) or nullptr
@@ -44,6 +63,7 @@ struct SparseGradArgs {
     TemporalStep<float> tstep;
     int cpl;                         // columns per lane (4, 8, 16; 0 = default for R)
     int f_minus_zero;                // loss: add f(x, m) - f(0, m) per sample (the nonzeros' part of an exact loss)
+    int overlap;                     // host: launch with launch_after_prev (a kernel of a solve's chain)
 };
 
 // Arguments of the dense fused gradient kernels (3-way tiled and the 2-way path).
@@ -158,6 +178,7 @@ struct FactorUpdateArgs {
     float* gzero;
     const double* SH;
     SolverState* tk;
+    int overlap;              // host: launch with launch_after_prev when the FP32 row kernel applies
 };
 
 template <typename T>

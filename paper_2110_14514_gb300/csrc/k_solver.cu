@@ -347,9 +347,10 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     if (k < 0) return;   // the grid is sized from the same geometry
     const int RR = R * R;
     const int nrows = (int)(b1 - b0);
-    // The skip flag, the history length, the rate, the coefficients and the rows are all
-    // requested before any of them is used, so the block waits for one round trip, not four.
-    const int32_t skipv = a.skip ? *a.skip : 0;
+    // Up to grid_dep_wait() the block reads what the gradient kernel before it leaves alone (the
+    // history length, the rate, the coefficients or the previous update's Gram sums, the rows of
+    // A, Abar, u and v) and forms the history term of every row; G and the skip flag come after
+    // the wait.  The requests of each phase are issued before any of them is used.
     const int32_t hlen = a.B != nullptr ? *a.hist_len : 0;
     const double rate = *a.rate;
     // B_k, C_k entries i = tid + 256 q of the padded 32 x 32 tiles: read (an epoch's first update),
@@ -378,18 +379,16 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     float* ub = a.u + b0 * R;
     float* vb = a.v + b0 * R;
     const int g0 = warp * kFuGroup;   // this warp's rows of the block
-    float av[kFuGroup], gv[kFuGroup], uv[kFuGroup], vv[kFuGroup], xbv[kFuGroup];
+    float av[kFuGroup], uv[kFuGroup], vv[kFuGroup], xbv[kFuGroup];
 #pragma unroll
     for (int r = 0; r < kFuGroup; ++r) {
         const bool act = on && g0 + r < nrows;
         const int o = act ? (g0 + r) * R + j : 0;
         av[r] = act ? Ab[o] : 0.0f;
         xbv[r] = act ? Abarb[o] : 0.0f;
-        gv[r] = act ? Gb[o] : 0.0f;
         uv[r] = act && step ? ub[o] : 0.0f;
         vv[r] = act && step ? vb[o] : 0.0f;
     }
-    if (skipv) return;   // the solver has finished: nothing is written
     const bool hist = hlen > 0;
     if (a.gprev)   // B_k = Gamma_k * S_H, C_k = (Gamma_k - Gammabar_k) * S_H of this block's mode
 #pragma unroll
@@ -408,8 +407,7 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
         sD[warp][r][lane] = av[r] - xbv[r];   // zero outside the rank and the block's rows
         sAb[warp][r][lane] = xbv[r];
         sRow[0][warp][r][lane] = av[r];       // parked in shared memory: the matrix products
-        sRow[1][warp][r][lane] = gv[r];       // below then run without them in registers
-        sRow[2][warp][r][lane] = uv[r];
+        sRow[2][warp][r][lane] = uv[r];       // below then run without them in registers
         sRow[3][warp][r][lane] = vv[r];
     }
     __syncthreads();   // B_k, C_k and every warp's rows are staged
@@ -433,6 +431,15 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
             }
         }
     }
+    grid_dep_wait();   // the gradient kernel's G is complete and visible from here
+    grid_dep_launch();
+    if (a.skip && *a.skip) return;   // the solver has finished: nothing is written
+    float gv[kFuGroup];
+#pragma unroll
+    for (int r = 0; r < kFuGroup; ++r) {
+        const bool act = on && g0 + r < nrows;
+        gv[r] = act ? Gb[(g0 + r) * R + j] : 0.0f;
+    }
 #pragma unroll
     for (int r = 0; r < kFuGroup; ++r) {
         const bool act = on && g0 + r < nrows;
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
         if (act) {
             const int o = (g0 + r) * R + j;
             const float x = sRow[0][warp][r][lane];
-            const float g = sRow[1][warp][r][lane] + lam * x + (acc[r].x + acc[r].y);
+            const float g = gv[r] + lam * x + (acc[r].x + acc[r].y);
             if (!step) {
                 Gb[o] = g;
             } else {
@@ -555,8 +562,12 @@ static bool factor_update_rows(const FactorUpdateArgs<T>& a, cudaStream_t st, cu
         if (blocks < 1 || blocks > 0x7fffffff) return false;
         const size_t smem = (a.gacc ? 6 : 4) * kFuBlockRows * 32 * sizeof(float);
         cudaFuncSetAttribute(k_factor_update_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_factor_update_rows<<<(int)blocks, 32 * kFuWarps, smem, st>>>(a);
-        *err = cudaGetLastError();
+        if (a.overlap) {
+            *err = launch_after_prev(k_factor_update_rows, dim3((unsigned)blocks), dim3(32 * kFuWarps), smem, st, a);
+        } else {
+            k_factor_update_rows<<<(int)blocks, 32 * kFuWarps, smem, st>>>(a);
+            *err = cudaGetLastError();
+        }
         return true;
     } else {
         (void)a, (void)st, (void)err;

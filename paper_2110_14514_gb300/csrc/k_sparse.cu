@@ -66,9 +66,11 @@ __device__ __forceinline__ DrawSizes draw_sizes(const SparseGradArgs& a, const S
 }
 
 // Draw sample slot c (Alg. 6 with the counter layout (slot, attempt, draw, purpose<<24 | t)).
+// Error bits (a bad coordinate, an exhausted zero-sample search) are ORed into errb.
 template <int D>
 __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceDesc& sd, const DrawSizes& z,
-                                           int64_t c, int (&ci)[D], float& x, float& w, int& attempt, bool& ok) {
+                                           int64_t c, int (&ci)[D], float& x, float& w, int& attempt, bool& ok,
+                                           int& errb) {
     ok = false;
     x = 0.0f;
     w = 0.0f;
@@ -96,7 +98,7 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
         if (!inb) {
 #pragma unroll
             for (int k = 0; k < D; ++k) ci[k] = 0;
-            set_err(a.err, ERRB_COORD);
+            errb |= ERRB_COORD;
             return;
         }
         x = __ldg(vals + e);
@@ -126,7 +128,7 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) ci[k] = 0;
-    set_err(a.err, ERRB_SAMPLING);
+    errb |= ERRB_SAMPLING;
 }
 
 // G row += c, 16 bytes at once, as a reduction without a returned value (red, not atom: the
@@ -167,7 +169,9 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(16) int srec[8 * 32 * RS];   // 8 warps x 32 records
     __shared__ DrawSizes zs;
-    if (a.skip && *a.skip) return;
+    // Up to grid_dep_wait() the kernel reads only the slice (its descriptor, COO arrays, nonzero
+    // hash and hot-row tables, none of which a kernel of a solve writes) and writes only shared
+    // memory: the set-up and the first chunk's draw overlap the previous kernel of the solve.
     const SliceDesc sd = a.slice ? *a.slice : a.inline_slice;
     const bool wantG = (a.want & SGCP_WANT_FACTORS) != 0;
     const bool wantS = (a.want & SGCP_WANT_TEMPORAL) != 0;
@@ -192,11 +196,7 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     float4 sv[NV];
     bool vact[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        vact[v] = j0 + 4 * v < R;
-        sv[v] = vact[v] ? *reinterpret_cast<const float4*>(a.s + j0 + 4 * v) : zero4;
-    }
-    const float ysc = a.y_scale ? *a.y_scale : 1.0f;
+    for (int v = 0; v < NV; ++v) vact[v] = j0 + 4 * v < R;
     float4 gsl[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) gsl[v] = zero4;
@@ -211,14 +211,21 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     // hot-table loads) is drawn while the current chunk's rows are processed.
     int ci[D], hs[D];
     float x = 0.0f, w = 0.0f;
-    int att;
+    int att, errb = 0;
     bool ok = false;
     auto draw = [&](int64_t c) {
-        gen_sample<D>(a, sd, z, c * 32 + lane, ci, x, w, att, ok);
+        gen_sample<D>(a, sd, z, c * 32 + lane, ci, x, w, att, ok, errb);
 #pragma unroll
         for (int k = 0; k < D; ++k) hs[k] = (nhot && ok) ? __ldg(a.hot[k] + ci[k]) : -1;
     };
     if (ch < nchunks) draw(ch);
+
+    grid_dep_wait();     // the previous kernel's s, factors, outputs and flags are visible from here
+    grid_dep_launch();
+    if (a.skip && *a.skip) return;   // uniform over the grid: the solver has finished
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sv[v] = vact[v] ? *reinterpret_cast<const float4*>(a.s + j0 + 4 * v) : zero4;
+    const float ysc = a.y_scale ? *a.y_scale : 1.0f;
 
     for (; ch < nchunks; ch += stride) {
         // stage the 32 records of this chunk: [coords | hot slots | x | w], w == 0 marks an empty slot
@@ -320,6 +327,7 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
         }
     }
 
+    if (errb) set_err(a.err, errb);
     // temporal gradient: reduce over the groups of the warp, then the block
     if (wantS) {
 #pragma unroll
@@ -378,9 +386,10 @@ __global__ void k_sample_coords(const SparseGradArgs a) {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < z.total; c += (int64_t)gridDim.x * blockDim.x) {
         int ci[D];
         float x, w;
-        int att;
+        int att, errb = 0;
         bool ok;
-        gen_sample<D>(a, sd, z, c, ci, x, w, att, ok);
+        gen_sample<D>(a, sd, z, c, ci, x, w, att, ok, errb);
+        if (errb) set_err(a.err, errb);
 #pragma unroll
         for (int k = 0; k < D; ++k) a.coords_out[c * D + k] = ok ? ci[k] : -1;
         if (a.attempt_out) a.attempt_out[c] = att;
@@ -538,6 +547,7 @@ static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream
     int64_t want = (chunks + (threads / 32) - 1) / (threads / 32);
     const int64_t cap = (int64_t)occ * num_sms();
     const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    if (a.overlap) return launch_after_prev(k_sparse_grad<D, RP, CPL>, dim3(blocks), dim3(threads), smem, st, a);
     k_sparse_grad<D, RP, CPL><<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
