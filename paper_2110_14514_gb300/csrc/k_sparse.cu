@@ -159,7 +159,7 @@ __device__ __forceinline__ int hot_pos(int k, int slot, int nhot, int RP, int j)
 // spilling much (<= 3 modes, <= 8 columns per lane): the kernel is bound by the
 // latency of its L2 row gathers, and a third block cut the R = 32 factor
 // gradient from 39.5 to 32.1 us on GB300.
-template <int D, int RP, int CPL>
+template <int D, int RP, int CPL, bool WG = true>
 __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_grad(const SparseGradArgs a) {
     constexpr int G = RP / CPL;      // lanes per sample
     constexpr int SPW = 32 / G;      // samples per warp step
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     // hash and hot-row tables, none of which a kernel of a solve writes) and writes only shared
     // memory: the set-up and the first chunk's draw overlap the previous kernel of the solve.
     const SliceDesc sd = a.slice ? *a.slice : a.inline_slice;
-    const bool wantG = (a.want & SGCP_WANT_FACTORS) != 0;
+    const bool wantG = WG && (a.want & SGCP_WANT_FACTORS) != 0;
     const bool wantS = (a.want & SGCP_WANT_TEMPORAL) != 0;
     const bool wantF = (a.want & SGCP_WANT_LOSS) != 0;
     const int nhot = wantG ? a.nhot : 0;
@@ -529,7 +529,7 @@ cudaError_t launch_ingest(const IngestArgs& a, int64_t nnz, cudaStream_t st, int
     return cudaGetLastError();
 }
 
-template <int D, int RP, int CPL>
+template <int D, int RP, int CPL, bool WG = true>
 static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
     const int threads = 256;
     const int nhot = (a.want & SGCP_WANT_FACTORS) ? a.nhot : 0;
@@ -538,8 +538,8 @@ static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream
     static size_t occ_smem = 0;
     if (occ == 0 || occ_smem != smem) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_sparse_grad<D, RP, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sparse_grad<D, RP, CPL>, threads, smem);
+            cudaFuncSetAttribute(k_sparse_grad<D, RP, CPL, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sparse_grad<D, RP, CPL, WG>, threads, smem);
         if (occ < 1) occ = 1;
         occ_smem = smem;
     }
@@ -547,8 +547,8 @@ static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream
     int64_t want = (chunks + (threads / 32) - 1) / (threads / 32);
     const int64_t cap = (int64_t)occ * num_sms();
     const int blocks = (int)(want < 1 ? 1 : (want > cap ? cap : want));
-    if (a.overlap) return launch_after_prev(k_sparse_grad<D, RP, CPL>, dim3(blocks), dim3(threads), smem, st, a);
-    k_sparse_grad<D, RP, CPL><<<blocks, threads, smem, st>>>(a);
+    if (a.overlap) return launch_after_prev(k_sparse_grad<D, RP, CPL, WG>, dim3(blocks), dim3(threads), smem, st, a);
+    k_sparse_grad<D, RP, CPL, WG><<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -558,6 +558,8 @@ static cudaError_t run_sparse(const SparseGradArgs& a, int64_t total, cudaStream
 // the 10000 x 5000 x 2000, R = 32 workload.
 template <int D, int RP>
 static cudaError_t run_sparse_cpl(const SparseGradArgs& a, int64_t total, cudaStream_t st) {
+    if (a.cpl == 0 && !(a.want & SGCP_WANT_FACTORS))   // gather-only launches at the default width
+        return run_sparse<D, RP, (RP >= 16 ? 8 : 4), false>(a, total, st);
     int cpl = a.cpl ? a.cpl : ((a.want & SGCP_WANT_FACTORS) ? 4 : (RP >= 16 ? 8 : 4));
     if (cpl > RP) cpl = RP;
     if (RP / cpl > 32) cpl = RP / 32;
