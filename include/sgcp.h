@@ -122,7 +122,7 @@ typedef struct {
     int32_t lbfgs_iters;      /* L-BFGS iterations per slice */
     int32_t sparse_cpl;       /* tuning: factor columns per lane in the sparse kernel (4, 8, 16; 0 = auto) */
     int32_t hot_rows;         /* tuning: rows per mode accumulated in shared memory by the sparse kernel
-                                 (0..64; -1 = 16); results do not depend on it */
+                                 (0..64; -1 = 4); results do not depend on it */
     int32_t history_kind;     /* SGCP_HISTORY_MODEL (default) or SGCP_HISTORY_SLICES */
     int32_t reserved;         /* must be 0 */
     uint64_t seed;            /* Philox4x32-10 key for every random draw */

@@ -1342,7 +1342,7 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     for (int k = c->ndim; k < 4; ++k) c->row_off[k] = c->nrows;
     c->N = c->nrows * c->R;
     c->device = dev;
-    c->nhot = P.hot_rows < 0 ? 16 : (P.hot_rows > kMaxHot ? kMaxHot : P.hot_rows);
+    c->nhot = P.hot_rows < 0 ? 4 : (P.hot_rows > kMaxHot ? kMaxHot : P.hot_rows);
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
     } else {

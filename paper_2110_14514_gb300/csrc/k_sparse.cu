@@ -354,16 +354,17 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
         if (lane == 0) fb[warp] = fd;
     }
     __syncthreads();
-    if (nhot) {
-        for (int i = threadIdx.x; i < D * nhot * RP; i += blockDim.x) {
-            const float val = hacc[i];
-            const int k = i / (nhot * RP), rem = i - k * nhot * RP;
-            const int slot = rem / RP, p = rem - slot * RP;
-            const int j = (p - slot) & (RP - 1);     // undo the column rotation
-            if (val != 0.0f && j < R) {
-                const int row = a.hot_rows[k * kMaxHot + slot];
-                if (row >= 0) atomicAdd(a.G[k] + (int64_t)row * R + j, val);
-            }
+    if (nhot) {   // one 16-byte reduction per four columns of a hot row (the rows are R-aligned, R % 4 == 0)
+        constexpr int QPR = RP / 4;
+        for (int i = threadIdx.x; i < D * nhot * QPR; i += blockDim.x) {
+            const int k = i / (nhot * QPR), rem = i - k * nhot * QPR;
+            const int slot = rem / QPR, j = (rem - slot * QPR) * 4;
+            if (j >= R) continue;
+            const float4 t = make_float4(hacc[hot_pos(k, slot, nhot, RP, j)], hacc[hot_pos(k, slot, nhot, RP, j + 1)],
+                                         hacc[hot_pos(k, slot, nhot, RP, j + 2)], hacc[hot_pos(k, slot, nhot, RP, j + 3)]);
+            const int row = a.hot_rows[k * kMaxHot + slot];
+            if (row >= 0 && (t.x != 0.f || t.y != 0.f || t.z != 0.f || t.w != 0.f))
+                red_add_f4(a.G[k] + (int64_t)row * R + j, t);
         }
     }
     if (wantS) {

@@ -254,24 +254,32 @@ def test_host_slice_matches_device_slice(sg):
             assert rel(Gh[k].cpu().numpy(), Gd[k].cpu().numpy()) < 1e-6
 
 
-def test_full_size_sparse_binary_zipf_gradient(sg):
-    """The benchmark workload itself: 10000 x 5000 x 2000, 1e6 Zipf nonzeros, R = 32,
-    Bernoulli-logit, 1e5 + 1e5 samples, in the launch configuration the bench times."""
+@pytest.fixture(scope="module")
+def full_size_case():
     cfg = S.workload("sparse_binary_zipf")
     idx, val = S.sparse_slice(cfg, 1)
     A = S.init_factors(cfg)
     rng = np.random.default_rng(5)
     s = (rng.random(cfg["rank"]) + 0.5).astype(np.float32)
+    Go, gso, Fo = gcp.sampled_gradient(idx, val, cfg["dims"], s, A, cfg["loss"], cfg["p"], cfg["q"], 2024, 1, 0)
+    return cfg, idx, val, A, s, (Go, gso, Fo)
+
+
+@pytest.mark.parametrize("hot_rows", [-1, 0, 64])
+def test_full_size_sparse_binary_zipf_gradient(sg, full_size_case, hot_rows):
+    """The benchmark workload itself: 10000 x 5000 x 2000, 1e6 Zipf nonzeros, R = 32,
+    Bernoulli-logit, 1e5 + 1e5 samples, in the launch configuration the bench times; with the
+    default number of shared-memory hot rows per mode, none, and the most."""
+    cfg, idx, val, A, s, (Go, gso, Fo) = full_size_case
     dims, R = cfg["dims"], cfg["rank"]
     with make_ctx(sg, dims, R, cfg["loss"], A, p=cfg["p"], q=cfg["q"], p_obj=cfg["p_obj"], q_obj=cfg["q_obj"],
-                  seed=2024) as ctx:
+                  seed=2024, hot_rows=hot_rows) as ctx:
         # factor gradient alone (the launch the factor solver makes), then temporal gradient + loss
         G, _, _ = ctx.gradient(dev(s), [dev(a) for a in A], idx=dev(idx), vals=dev(val), t=1, draw=0,
                                want=sg.WANT_FACTORS)
         _, gs, f = ctx.gradient(dev(s), [dev(a) for a in A], idx=dev(idx), vals=dev(val), t=1, draw=0,
                                 want=sg.WANT_TEMPORAL | sg.WANT_LOSS)
         ctx.check()
-    Go, gso, Fo = gcp.sampled_gradient(idx, val, dims, s, A, cfg["loss"], cfg["p"], cfg["q"], 2024, 1, 0)
     for k in range(3):
         assert rel(G[k].cpu().numpy(), Go[k]) < TOL_G, (k, rel(G[k].cpu().numpy(), Go[k]))
         # every row, cold rows included (the hot-row shared-memory flush and the direct scatters)
