@@ -33,6 +33,12 @@
  *    (synchronising the stream) and from then on the context answers
  *    SGCP_ERR_STATE until it is destroyed.
  *  - One context must be used by one host thread at a time.
+ *  - Inside a slice update the gradient and factor-update kernels of a solver
+ *    chain are launched with programmatic stream serialization, each starting
+ *    its independent set-up while the kernel before it finishes.  A library
+ *    built with SGCP_BUILD_SERIAL=1 in the environment launches every kernel
+ *    with full serialization instead (same arithmetic and results; the build
+ *    kernel profilers replay).
  *
  * Limits: 2 <= ndim <= 4; rank R a multiple of 4 with 4 <= R <= 128; dense
  * slices need ndim <= 3; I_k * R < 2^31 for every mode; the product of the

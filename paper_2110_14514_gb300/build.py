@@ -38,12 +38,18 @@ def _deps():
     return max(os.path.getmtime(h) for h in hdrs)
 
 
+def _flags():
+    """SGCP_BUILD_SERIAL=1: the serial build (no programmatic dependent launch), which kernel
+    profilers can replay; same kernels and results otherwise."""
+    return FLAGS + (["-DSGCP_NO_GRID_DEP"] if os.environ.get("SGCP_BUILD_SERIAL") == "1" else [])
+
+
 def _compile(src, verbose):
     obj = os.path.join(BUILD, src.replace(".cu", ".o"))
     srcp = os.path.join(CSRC, src)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(srcp), _deps()):
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", srcp, "-o", obj]
+    cmd = [nvcc()] + ARCH + _flags() + (["-Xptxas", "-v"] if verbose else []) + ["-c", srcp, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -55,9 +61,15 @@ def _compile(src, verbose):
 def build(verbose=False, force=False):
     """Compile and link libsgcp.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "flags.txt")   # a build with other flags starts from scratch
+    want = " ".join(_flags())
+    if not os.path.exists(stamp) or open(stamp).read() != want:
+        force = True
     if force:
         for f in os.listdir(BUILD):
             os.remove(os.path.join(BUILD, f))
+    with open(stamp, "w") as fh:
+        fh.write(want)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):

@@ -248,7 +248,14 @@ __device__ __forceinline__ void set_err(int* err, int bits) {
 // grid_dep_launch() lets the next kernel start; it is issued after the wait,
 // so a kernel that starts early always finds every kernel but its immediate
 // predecessor complete.
+// A build with SGCP_NO_GRID_DEP defined (the serial profiling build) has neither the instructions
+// nor programmatic launches.
+#ifndef SGCP_NO_GRID_DEP
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#else
+__device__ __forceinline__ void grid_dep_wait() {}
+__device__ __forceinline__ void grid_dep_launch() {}
+#endif
 
 }  // namespace sgcp

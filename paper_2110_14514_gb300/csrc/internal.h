@@ -15,6 +15,10 @@ namespace sgcp {
 template <typename... P, typename... Args>
 inline cudaError_t launch_after_prev(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                                      Args&&... args) {
+#ifdef SGCP_NO_GRID_DEP
+    kern<<<grid, block, smem, st>>>(static_cast<Args&&>(args)...);
+    return cudaGetLastError();
+#else
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -26,6 +30,7 @@ inline cudaError_t launch_after_prev(void (*kern)(P...), dim3 grid, dim3 block, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+#endif
 }
 
 // Arguments of the fused sparse sample -> model -> y -> MTTKRP kernel.
