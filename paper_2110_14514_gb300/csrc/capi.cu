@@ -425,11 +425,14 @@ TemporalStep<T> make_tstep(sgcp_ctx* c, const TStepSpec* ts) {
 sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_dev, int set, uint32_t draw, int want,
                              const void* s, const void* const* A, void* const* G, void* gs, double* f, int loss,
                              const void* y_scale, const int32_t* skip, int all_nnz = 0,
-                             const TStepSpec* tstep = nullptr, bool overlap = false) {
+                             const TStepSpec* tstep = nullptr, bool overlap = false, float* zero_buf = nullptr,
+                             int zero_n = 0) {
     if (sparse) {
         SparseGradArgs a = sparse_args(c, slice_dev, set, draw, want, s, A, G, gs, f, loss, y_scale, skip);
         a.all_nnz = all_nnz;
         a.overlap = overlap ? 1 : 0;
+        a.zero_buf = zero_buf;
+        a.zero_n = zero_buf ? zero_n : 0;
         if (tstep) {
             a.tstep_on = 1;
             a.tstep = make_tstep<float>(c, tstep);
@@ -716,9 +719,10 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
     // With gacc each update also sums the Grams of the factors it writes (two alternating buffers)
     // and the next update forms its B_k, C_k from them, so the Gram / history-coefficient chain
     // beside the gradient runs only for an epoch's first iteration (whose A may have been rolled
-    // back).  Both buffers are zero at every epoch start: the update of iteration it accumulates
-    // into buffer it % 2 (except the epoch's last update, whose sums no update would read) and
-    // clears the buffer it read.
+    // back).  The update of iteration it accumulates into buffer it % 2 (except the epoch's last
+    // update, whose sums no update would read), which is zero when it starts: cleared by the
+    // sparse gradient kernel of the same iteration, or (dense) by the last block of the update
+    // that read it.
     const bool fused = hist_possible && c->gacc != nullptr;
     const size_t gsz = 2 * (size_t)d * R * R;
     if (fused) {
@@ -734,11 +738,15 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
                "history slots");
         for (int it = 0; it < P.tau_f; ++it) {
             fu.rate = c->rates_f + it;
+            float* gclear = nullptr;   // sparse: the gradient kernel clears the buffer this update sums into
             if (fused) {
                 float* prev = c->gacc + gsz * ((it + 1) & 1);   // written by the update of it - 1
                 fu.gprev = it > 0 ? prev : nullptr;
-                fu.gzero = it > 0 ? prev : nullptr;
                 fu.gacc = it + 1 < P.tau_f ? c->gacc + gsz * (it & 1) : nullptr;
+                // the buffer update it - 1 read is cleared before update it adds into it: by the
+                // gradient kernel between the two (sparse), else by update it - 1's last block
+                fu.gzero = (it > 0 && !sparse) ? prev : nullptr;
+                if (sparse) gclear = fu.gacc;
             }
             const bool chain = hist_possible && (!fused || it == 0);
             if (chain) CK(fork(), "fork");
@@ -746,7 +754,7 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
             // side-stream join precedes it)
             st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_FACTOR_GRAD, (uint32_t)(e * P.tau_f + it),
                                   SGCP_WANT_FACTORS, c->s, Aptr, Gptr, nullptr, nullptr, loss, nullptr, skip, 0,
-                                  nullptr, true);
+                                  nullptr, true, gclear, (int)gsz);
             if (st) return st;
             for (int j = 0; stored && j < P.H; ++j)   // + sum_h w_h Y_h(k) Z_k diag(s_h)
                 if ((st = enqueue_stored<T>(c, sparse, j, false, (uint32_t)(e * P.tau_f + it), SGCP_WANT_FACTORS, Aptr,

@@ -69,6 +69,8 @@ struct SparseGradArgs {
     int cpl;                         // columns per lane (4, 8, 16; 0 = default for R)
     int f_minus_zero;                // loss: add f(x, m) - f(0, m) per sample (the nonzeros' part of an exact loss)
     int overlap;                     // host: launch with launch_after_prev (a kernel of a solve's chain)
+    float* zero_buf;                 // cleared after grid_dep_wait (the next factor update's Gram sums) or nullptr
+    int zero_n;
 };
 
 // Arguments of the dense fused gradient kernels (3-way tiled and the 2-way path).
@@ -177,7 +179,8 @@ struct FactorUpdateArgs {
     //   gprev: Gram sums of the factors this update starts from (written by the previous update);
     //          when set, B_k and C_k are formed from them and SH instead of read from B, C;
     //   gacc:  zero on entry; receives the Grams of the rows this update writes;
-    //   gzero: cleared by the last block (ticket tk) once every block has read gprev.
+    //   gzero: cleared by the last block (ticket tk) once every block has read gprev (or nullptr
+    //          when the kernel between two updates clears it).
     const float* gprev;
     float* gacc;
     float* gzero;

@@ -469,17 +469,17 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
     if (gram) {
 
         // ---- Grams of the block's updated rows.  Thread = 4 x 4 tile (l4, m4) of A'A and of D'A over
-        // one half of the rows; pairs (x_l, x_l+1) * (a_m, a_m+1) give the diagonal entries of a 2 x 2
-        // block and (x_l, x_l+1) * (a_m+1, a_m) the off-diagonal ones, two packed FMAs each.
+        // one quarter of the rows; pairs (x_l, x_l+1) * (a_m, a_m+1) give the diagonal entries of a
+        // 2 x 2 block and (x_l, x_l+1) * (a_m+1, a_m) the off-diagonal ones, two packed FMAs each.
         __syncthreads();
-        const int tq = R >> 2, half = threadIdx.x >> 6, tile = threadIdx.x & 63;
+        const int tq = R >> 2, part = threadIdx.x >> 6, tile = threadIdx.x & 63;
         const int l4 = (tile / 8) * 4, m4 = (tile % 8) * 4;
         float2 pd[4], po[4], ed[4], eo[4];   // [2 x 2 block (lb, mb)]: diagonal, off-diagonal
 #pragma unroll
         for (int q = 0; q < 4; ++q) pd[q] = po[q] = ed[q] = eo[q] = make_float2(0.f, 0.f);
-        const bool tile_on = half < 2 && tile / 8 < tq && tile % 8 < tq;
+        const bool tile_on = tile / 8 < tq && tile % 8 < tq;
         if (tile_on) {
-            const int rb = half * (kFuBlockRows / 2), re = min(nrows, rb + kFuBlockRows / 2);
+            const int rb = part * (kFuBlockRows / 4), re = min(nrows, rb + kFuBlockRows / 4);
 #pragma unroll 2
             for (int r = rb; r < re; ++r) {
                 const float4 al = *reinterpret_cast<const float4*>(&sA[r][l4]);
@@ -499,27 +499,32 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
                 ed[3] = fma2(dl1, am1, ed[3]), eo[3] = fma2(dl1, as1, eo[3]);
             }
         }
-        // the two halves meet in shared memory (sD / sAb are free), then one float4 atomic per row
-        float2* hs = reinterpret_cast<float2*>(&sD[0][0][0]);   // [16 values][64 tiles]: the second half's
-        if (tile_on && half == 1)                               // tiles, consecutive tiles in consecutive words
+        // quarters 1..3 meet quarter 0 in shared memory (the parked rows' planes are free now), then
+        // one float4 atomic per row of the tile
+        float2* hs = reinterpret_cast<float2*>(&sRow[0][0][0][0]);   // [3 parts][16 values][64 tiles]
+        if (tile_on && part > 0)                                      // consecutive tiles, consecutive words
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                hs[q * 64 + tile] = pd[q];
-                hs[(4 + q) * 64 + tile] = po[q];
-                hs[(8 + q) * 64 + tile] = ed[q];
-                hs[(12 + q) * 64 + tile] = eo[q];
+                float2* hp = hs + (part - 1) * 16 * 64;
+                hp[q * 64 + tile] = pd[q];
+                hp[(4 + q) * 64 + tile] = po[q];
+                hp[(8 + q) * 64 + tile] = ed[q];
+                hp[(12 + q) * 64 + tile] = eo[q];
             }
         __syncthreads();
-        if (tile_on && half == 0) {
+        if (tile_on && part == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 a0 = hs[q * 64 + tile];
-                const float2 a1 = hs[(4 + q) * 64 + tile];
-                const float2 a2 = hs[(8 + q) * 64 + tile];
-                const float2 a3 = hs[(12 + q) * 64 + tile];
-                pd[q].x += a0.x, pd[q].y += a0.y, po[q].x += a1.x, po[q].y += a1.y;
-                ed[q].x += a2.x, ed[q].y += a2.y, eo[q].x += a3.x, eo[q].y += a3.y;
-            }
+            for (int p2 = 0; p2 < 3; ++p2)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2* hp = hs + p2 * 16 * 64;
+                    const float2 a0 = hp[q * 64 + tile];
+                    const float2 a1 = hp[(4 + q) * 64 + tile];
+                    const float2 a2 = hp[(8 + q) * 64 + tile];
+                    const float2 a3 = hp[(12 + q) * 64 + tile];
+                    pd[q].x += a0.x, pd[q].y += a0.y, po[q].x += a1.x, po[q].y += a1.y;
+                    ed[q].x += a2.x, ed[q].y += a2.y, eo[q].x += a3.x, eo[q].y += a3.y;
+                }
             // block (lb, mb) = q: rows l4 + 2 lb + {0, 1}, columns m4 + 2 mb + {0, 1}
             float P4[4][4], E4[4][4];
 #pragma unroll

@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     grid_dep_wait();     // the previous kernel's s, factors, outputs and flags are visible from here
     grid_dep_launch();
     if (a.skip && *a.skip) return;   // uniform over the grid: the solver has finished
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.zero_n; i += gridDim.x * blockDim.x) a.zero_buf[i] = 0.0f;
 #pragma unroll
     for (int v = 0; v < NV; ++v) sv[v] = vact[v] ? *reinterpret_cast<const float4*>(a.s + j0 + 4 * v) : zero4;
     const float ysc = a.y_scale ? *a.y_scale : 1.0f;
