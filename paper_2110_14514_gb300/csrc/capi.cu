@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,6 +41,9 @@ struct sgcp_ctx {
     // temporal-solver state (R each)
     void *s = nullptr, *s_u = nullptr, *s_v = nullptr, *s_uo = nullptr, *s_vo = nullptr, *s_ao = nullptr,
          *gs = nullptr;
+    // sparse temporal solve with the step deferred to the next kernel: a second (s, u, v) and
+    // three gradient sums in rotation
+    void *s2 = nullptr, *gs3 = nullptr;
     // history window
     void* s_hist = nullptr;
     int64_t* h_dev = nullptr;
@@ -406,6 +410,16 @@ struct TStepSpec {
     const double* rate;
 };
 
+// A deferred ADAM step on s (sparse kernels): state in (s, u, v), previous gradient sum g,
+// state out (written by one block); apply = 0 copies the state unchanged.
+struct PendSpec {
+    int apply;
+    void *s, *u, *v;
+    const double* rate;
+    const void* g;
+    void *s_out, *u_out, *v_out;
+};
+
 template <typename T>
 TemporalStep<T> make_tstep(sgcp_ctx* c, const TStepSpec* ts) {
     TemporalStep<T> t{};
@@ -426,13 +440,23 @@ sgcp_status enqueue_gradient(sgcp_ctx* c, bool sparse, const SliceDesc* slice_de
                              const void* s, const void* const* A, void* const* G, void* gs, double* f, int loss,
                              const void* y_scale, const int32_t* skip, int all_nnz = 0,
                              const TStepSpec* tstep = nullptr, bool overlap = false, float* zero_buf = nullptr,
-                             int zero_n = 0) {
+                             int zero_n = 0, const PendSpec* pend = nullptr) {
     if (sparse) {
         SparseGradArgs a = sparse_args(c, slice_dev, set, draw, want, s, A, G, gs, f, loss, y_scale, skip);
         a.all_nnz = all_nnz;
         a.overlap = overlap ? 1 : 0;
         a.zero_buf = zero_buf;
         a.zero_n = zero_buf ? zero_n : 0;
+        if (pend) {
+            const TStepSpec in{pend->s, pend->u, pend->v, nullptr, pend->rate};
+            a.pend_on = 1;
+            a.pend_apply = pend->apply;
+            a.pend = make_tstep<float>(c, &in);
+            a.pend_g = (const float*)pend->g;
+            a.pend_s_out = (float*)pend->s_out;
+            a.pend_u_out = (float*)pend->u_out;
+            a.pend_v_out = (float*)pend->v_out;
+        }
         if (tstep) {
             a.tstep_on = 1;
             a.tstep = make_tstep<float>(c, tstep);
@@ -624,19 +648,57 @@ sgcp_status enqueue_step(sgcp_ctx* c, bool sparse, bool with_factor) {
                                           Aptr, nullptr, nullptr, &sw->F_new, loss, nullptr, nullptr);
         if (st) return st;
         CK(launch_obj_finish_w<T>(sw, (const T*)c->s, R, P.mu, 1, c->err, nullptr, c->stream, &c->launches), "obj");
+        // Sparse slices: the ADAM step on s of gradient kernel it runs at the start of kernel it + 1
+        // (every block forms the new s itself), and the epoch's objective kernel applies the last
+        // one.  The state after `it` steps lives in SP[(it + tau) % 2], so the state after tau steps
+        // is in SP[0] = (s, s_u, s_v); gradient sums rotate over three buffers G3[it % 3], each
+        // cleared by the kernel before the one that sums into it (the epoch's first by k_epoch_begin).
+        const bool defer = sparse;
+        const int tau = P.tau_w;
+        float* G3 = (float*)c->gs3;
+        void* SP[2][3] = {{c->s, c->s_u, c->s_v}, {c->s2, offs(c->s2, R, esz), offs(c->s2, 2 * R, esz)}};
+        auto g3 = [&](int i) { return G3 + (size_t)(i % 3) * R; };
         for (int e = 0; e < P.kappa_w; ++e) {
-            CK(launch_epoch_begin(sw, P.tol_w, c->rates_w, P.tau_w, P.beta1, P.beta2, c->stream, &c->launches),
+            CK(launch_epoch_begin(sw, P.tol_w, c->rates_w, P.tau_w, P.beta1, P.beta2, c->stream, &c->launches,
+                                  defer ? g3(0) : nullptr, R),
                "epoch begin");
             for (int it = 0; it < P.tau_w; ++it) {
                 tsw.rate = c->rates_w + it;
                 // a chain of gradient kernels: each one's sampling overlaps the one before
-                st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD, (uint32_t)(e * P.tau_w + it),
-                                      SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs, nullptr, loss, nullptr, skip, 0,
-                                      &tsw, true);
+                if (defer) {
+                    PendSpec ps{};
+                    const PendSpec* pp = nullptr;
+                    const int cur = (it + tau) & 1;
+                    if (it == 0 && cur == 1) {   // odd tau: the epoch's start state copied into SP[1]
+                        ps = PendSpec{0, SP[0][0], SP[0][1], SP[0][2], nullptr, nullptr, SP[1][0], SP[1][1], SP[1][2]};
+                        pp = &ps;
+                    } else if (it > 0) {
+                        const int prev = cur ^ 1;
+                        ps = PendSpec{1,       SP[prev][0], SP[prev][1], SP[prev][2], c->rates_w + it - 1,
+                                      g3(it - 1), SP[cur][0], SP[cur][1], SP[cur][2]};
+                        pp = &ps;
+                    }
+                    st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD,
+                                          (uint32_t)(e * P.tau_w + it), SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, g3(it),
+                                          nullptr, loss, nullptr, skip, 0, nullptr, true,
+                                          it + 1 < tau ? g3(it + 1) : nullptr, R, pp);
+                } else {
+                    st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_GRAD,
+                                          (uint32_t)(e * P.tau_w + it), SGCP_WANT_TEMPORAL, c->s, Aptr, nullptr, c->gs,
+                                          nullptr, loss, nullptr, skip, 0, &tsw, true);
+                }
                 if (st) return st;
             }
-            st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s, Aptr,
-                                  nullptr, nullptr, &sw->F_new, loss, nullptr, skip);
+            if (defer) {   // the epoch's last step (from SP[1]) lands in SP[0] as the objective is estimated
+                const PendSpec ps{1,         SP[1][0], SP[1][1], SP[1][2], c->rates_w + tau - 1,
+                                  g3(tau - 1), SP[0][0], SP[0][1], SP[0][2]};
+                st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s,
+                                      Aptr, nullptr, nullptr, &sw->F_new, loss, nullptr, skip, 0, nullptr, true,
+                                      nullptr, 0, &ps);
+            } else {
+                st = enqueue_gradient(c, sparse, c->slice_dev, SGCP_SAMPLES_TEMPORAL_OBJ, 0, SGCP_WANT_LOSS, c->s, Aptr,
+                                      nullptr, nullptr, &sw->F_new, loss, nullptr, skip);
+            }
             if (st) return st;
             CK(launch_obj_finish_w<T>(sw, (const T*)c->s, R, P.mu, 0, c->err, skip, c->stream, &c->launches), "obj");
             CK(launch_epoch_end<T>(sw, R, (T*)c->s, (T*)c->s_u, (T*)c->s_v, (T*)c->s_ao, (T*)c->s_uo, (T*)c->s_vo,
@@ -1381,6 +1443,8 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     void** vecR[] = {&c->s, &c->s_u, &c->s_v, &c->s_uo, &c->s_vo, &c->s_ao, &c->gs};
     for (void** p : vecR)
         if (sgcp_status st = dalloc(c, p, rb)) return bail(st);
+    for (void** p : {&c->s2, &c->gs3})
+        if (sgcp_status st = dalloc(c, p, 3 * rb)) return bail(st);
     const int Hs = P.H > 0 ? P.H : 1;
     const size_t RR = (size_t)c->R * c->R;
     sgcp_status st = SGCP_OK;
@@ -1435,6 +1499,8 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
     void* zeroR[] = {c->s, c->s_u, c->s_v, c->s_uo, c->s_vo, c->s_ao, c->gs};
     for (void* p : zeroR)
         if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, rb, s);
+    for (void* p : {c->s2, c->gs3})
+        if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, 3 * rb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->s_hist, 0, (size_t)Hs * rb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->SH, 0, RR * sizeof(double), s);
     SolverState st0{};

@@ -200,17 +200,26 @@ __device__ __forceinline__ bool last_block_ticket(SolverState* st) {
     return last != 0;
 }
 
+// One element of the ADAM step on s (Alg. 3): g = gsum + mu s, moments, bias-corrected rate,
+// projection onto s >= lower.
+template <typename T>
+__device__ __forceinline__ void adam_s_elem(const TemporalStep<T>& ts, double rate, T gsum, T s, T u0, T v0, T& s1,
+                                            T& u1, T& v1) {
+    const T g = gsum + (T)ts.mu * s;
+    u1 = (T)ts.beta1 * u0 + (T)(1.0 - ts.beta1) * g;
+    v1 = (T)ts.beta2 * v0 + (T)(1.0 - ts.beta2) * g * g;
+    s1 = s - (T)rate * u1 / (sqrt(v1) + (T)ts.eps);
+    if (s1 < (T)ts.lower) s1 = (T)ts.lower;
+}
+
 // Run by all threads of the elected last block of a temporal-gradient kernel:
 // g = gs + mu s, ADAM step on s with the bias-corrected rate, gs <- 0.
 template <typename T>
 __device__ void temporal_step_tail(const TemporalStep<T>& ts, T* gs, int R) {
     const double rate = *ts.rate;
     for (int j = threadIdx.x; j < R; j += blockDim.x) {
-        const T g = __ldcg(gs + j) + (T)ts.mu * ts.s[j];
-        const T u = (T)ts.beta1 * ts.u[j] + (T)(1.0 - ts.beta1) * g;
-        const T v = (T)ts.beta2 * ts.v[j] + (T)(1.0 - ts.beta2) * g * g;
-        T sn = ts.s[j] - (T)rate * u / (sqrt(v) + (T)ts.eps);
-        if (sn < (T)ts.lower) sn = (T)ts.lower;
+        T sn, u, v;
+        adam_s_elem<T>(ts, rate, __ldcg(gs + j), ts.s[j], ts.u[j], ts.v[j], sn, u, v);
         ts.u[j] = u;
         ts.v[j] = v;
         ts.s[j] = sn;

@@ -71,6 +71,15 @@ struct SparseGradArgs {
     int overlap;                     // host: launch with launch_after_prev (a kernel of a solve's chain)
     float* zero_buf;                 // cleared after grid_dep_wait (the next factor update's Gram sums) or nullptr
     int zero_n;
+    // Deferred ADAM step on s (Alg. 3): with pend_on every block forms, after grid_dep_wait, the s
+    // it uses from the state (s, u, v) in pend (rate = pend.rate) and the previous gradient sum
+    // pend_g (pend_apply = 0: the state unchanged); block 0 writes that state to pend_out.  So the
+    // step of one temporal-gradient kernel runs at the start of the next, with no last-block
+    // election at the end of the first.
+    int pend_on, pend_apply;
+    TemporalStep<float> pend;        // s, u, v in; st unused
+    const float* pend_g;
+    float *pend_s_out, *pend_u_out, *pend_v_out;
 };
 
 // Arguments of the dense fused gradient kernels (3-way tiled and the 2-way path).
@@ -205,8 +214,9 @@ cudaError_t launch_factor_update(const FactorUpdateArgs<T>& a, cudaStream_t st, 
 cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter, cudaStream_t stream,
                                int64_t* launches);
 // Alg. 3/4 loop test and the epoch's per-iteration learning rates rates[j], j < tau.
+// zero (nzero floats, optional) is cleared as well: a buffer the epoch's first kernel sums into.
 cudaError_t launch_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2,
-                               cudaStream_t stream, int64_t* launches);
+                               cudaStream_t stream, int64_t* launches, float* zero = nullptr, int nzero = 0);
 template <typename T>
 cudaError_t launch_epoch_end(SolverState* st, int64_t n, T* a, T* u, T* v, T* a_o, T* u_o, T* v_o, int tau,
                              double decay, double beta1, double beta2, cudaStream_t stream, int64_t* launches);

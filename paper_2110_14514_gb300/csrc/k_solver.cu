@@ -623,13 +623,15 @@ cudaError_t launch_solver_init(SolverState* st, double alpha, int reset_counter,
 
 // Alg. 3/4 loop test "while F > tol": once it fails, every later kernel of
 // the solver call is skipped through st->done.
-__global__ void k_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2) {
+__global__ void k_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2,
+                              float* zero, int nzero) {
+    for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0.0f;
     epoch_begin_block(st, tol, rates, tau, beta1, beta2);
 }
 
 cudaError_t launch_epoch_begin(SolverState* st, double tol, double* rates, int tau, double beta1, double beta2,
-                               cudaStream_t stream, int64_t* launches) {
-    k_epoch_begin<<<1, 128, 0, stream>>>(st, tol, rates, tau, beta1, beta2);
+                               cudaStream_t stream, int64_t* launches, float* zero, int nzero) {
+    k_epoch_begin<<<1, 128, 0, stream>>>(st, tol, rates, tau, beta1, beta2, zero, zero ? nzero : 0);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(16) int srec[8 * 32 * RS];   // 8 warps x 32 records
     __shared__ DrawSizes zs;
+    __shared__ __align__(16) float spend[RP];           // s after a deferred step
     // Up to grid_dep_wait() the kernel reads only the slice (its descriptor, COO arrays, nonzero
     // hash and hot-row tables, none of which a kernel of a solve writes) and writes only shared
     // memory: the set-up and the first chunk's draw overlap the previous kernel of the solve.
@@ -224,8 +225,26 @@ __global__ void __launch_bounds__(256, (D <= 3 && CPL <= 8) ? 3 : 2) k_sparse_gr
     grid_dep_launch();
     if (a.skip && *a.skip) return;   // uniform over the grid: the solver has finished
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.zero_n; i += gridDim.x * blockDim.x) a.zero_buf[i] = 0.0f;
+    if (a.pend_on) {   // the previous kernel's ADAM step on s, formed by every block for its own use
+        const TemporalStep<float>& ps = a.pend;
+        const double rate = a.pend_apply ? __ldcg(ps.rate) : 0.0;
+        for (int j = threadIdx.x; j < R; j += blockDim.x) {   // one element per thread
+            float s1 = __ldcg(ps.s + j), u1 = __ldcg(ps.u + j), v1 = __ldcg(ps.v + j);
+            if (a.pend_apply) adam_s_elem<float>(ps, rate, __ldcg(a.pend_g + j), s1, u1, v1, s1, u1, v1);
+            spend[j] = s1;
+            if (blockIdx.x == 0) {
+                a.pend_s_out[j] = s1;
+                a.pend_u_out[j] = u1;
+                a.pend_v_out[j] = v1;
+            }
+        }
+        __syncthreads();
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sv[v] = vact[v] ? *reinterpret_cast<const float4*>(a.s + j0 + 4 * v) : zero4;
+        for (int v = 0; v < NV; ++v) sv[v] = vact[v] ? *reinterpret_cast<const float4*>(spend + j0 + 4 * v) : zero4;
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sv[v] = vact[v] ? *reinterpret_cast<const float4*>(a.s + j0 + 4 * v) : zero4;
+    }
     const float ysc = a.y_scale ? *a.y_scale : 1.0f;
 
     for (; ch < nchunks; ch += stride) {
