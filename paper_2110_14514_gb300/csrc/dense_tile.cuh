@@ -35,19 +35,21 @@ struct TileLayout {
     static constexpr int A3t = A3n + 32 * LDR;     // [RT][32]
     static constexpr int KRn = A3t + RT * 32;      // [64][LDR]
     static constexpr int KRt = KRn + 64 * LDR;     // [RT][64]; then T as [64][LDR]
-    static constexpr int Yn = KRt + 64 * LDR;      // [64][32]
-    static constexpr int Yt = Yn + 64 * 32;        // [32][64]
+    static constexpr int LDY = 34;                 // Yn row stride: the 4 x 2 tiles' float2 stores hit 2 ways, not 8
+    static constexpr int Yn = KRt + 64 * LDR;      // [64][LDY]
+    static constexpr int Yt = Yn + 64 * LDY;       // [32][64]
     static constexpr int A1 = Yt + 32 * 64;        // [16][LDR]
     static constexpr int A1s = A1 + 16 * LDR;      // [16][LDR]
     static constexpr int A2 = A1s + 16 * LDR;      // [16][LDR]
     static constexpr int SV = A2 + 16 * LDR;       // [RT]
     static constexpr int ACC1 = SV + RT;           // [32][RT]
     static constexpr int ACC2 = ACC1 + kBoxMaxS * RT;   // [32][RT]
-    static constexpr int RED = ACC2 + kBoxMaxS * RT;    // 8 doubles
+    static constexpr int GSB = ACC2 + kBoxMaxS * RT;    // [2][RT]: the box's gradient of s, per warp parity
+    static constexpr int RED = GSB + 2 * RT;            // 8 doubles
     static constexpr int TOTAL = RED + 16;
     static_assert(RT * 64 <= 64 * LDR, "T fits the KRt region");
     static_assert(RED % 2 == 0 && A3t % 4 == 0 && KRn % 4 == 0 && KRt % 4 == 0 && Yn % 4 == 0 && Yt % 4 == 0 &&
-                      A1 % 4 == 0 && A1s % 4 == 0 && A2 % 4 == 0,
+                      A1 % 4 == 0 && A1s % 4 == 0 && A2 % 4 == 0 && GSB % 4 == 0,
                   "16-byte aligned regions");
 };
 
@@ -154,22 +156,29 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
     const bool wantG = (want & SGCP_WANT_FACTORS) != 0, wantY = wantG || wantS;
     const float ysc = g.ysc;
 
-    for (int i = tid; i < 32 * RT; i += kBoxThreads) {
+    for (int i = tid; i < 32 * RT; i += kBoxThreads) {   // lanes along j: coalesced rows of A3
         const int c = i / RT, j = i - c * RT;
-        const float v = (j < R && g.o3 + c < I3) ? __ldcg(g.A3 + (int64_t)(g.o3 + c) * R + j) : 0.f;
-        A3n[c * LDR + j] = v;
-        A3t[j * 32 + c] = v;
+        A3n[c * LDR + j] = (j < R && g.o3 + c < I3) ? __ldcg(g.A3 + (int64_t)(g.o3 + c) * R + j) : 0.f;
     }
+    float* gsb = sm + L::GSB;
     for (int j = tid; j < RT; j += kBoxThreads) sv[j] = j < R ? __ldcg(g.s + j) : 0.f;
     if (wantG)
         for (int i = tid; i < 2 * kBoxMaxS * RT; i += kBoxThreads) acc1[i] = 0.f;   // acc1, acc2 adjacent
+    __syncthreads();
+    for (int i = tid; i < 32 * RT; i += kBoxThreads) {   // lanes along c: conflict-free transposed stores
+        const int j = i >> 5, c = i & 31;
+        A3t[j * 32 + c] = A3n[c * LDR + j];
+    }
 
     float g3[2][TN];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int q = 0; q < TN; ++q) g3[c][q] = 0.f;
-    float gsr = 0.f, fsum = 0.f;
+    float gsv[TN];   // this thread's share of the box's gradient of s, columns TN g1 ..
+#pragma unroll
+    for (int q = 0; q < TN; ++q) gsv[q] = 0.f;
+    float fsum = 0.f;
 
     for (int t1 = 0; t1 < g.n1; ++t1) {
         const int i1b = g.o1 + t1 * B1;
@@ -191,8 +200,9 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
             for (int i = tid; i < 64 * 32; i += kBoxThreads) {   // a warp reads 32 consecutive i3: 128 bytes
                 const int row = i >> 5, col = i & 31;
                 const int i1 = i1b + (row >> lb2), i2 = i2b + (row & (B2 - 1)), i3 = g.o3 + col;
-                Yn[i] = (g.X && i1 < I1 && i2 < I2 && i3 < I3) ? __ldg(g.X + ((int64_t)i1 * I2 + i2) * I3 + i3)
-                                                                : 0.f;   // X == nullptr: the all-zero slice
+                Yn[row * L::LDY + col] = (g.X && i1 < I1 && i2 < I2 && i3 < I3)
+                                             ? __ldg(g.X + ((int64_t)i1 * I2 + i2) * I3 + i3)
+                                             : 0.f;   // X == nullptr: the all-zero slice
             }
             __syncthreads();
             // Khatri-Rao panel, natural layout (lanes along j) and k-major layout (lanes along rows)
@@ -237,7 +247,7 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                     const int row = 4 * g0 + i, col = 2 * g1 + c;
                     const int i1 = i1b + (row >> lb2), i2 = i2b + (row & (B2 - 1)), i3 = g.o3 + col;
                     const bool valid = i1 < I1 && i2 < I2 && i3 < I3;
-                    const float x = Yn[row * 32 + col];
+                    const float x = Yn[row * L::LDY + col];
                     if (wantF) {
                         float f, yy;
                         loss_eval<float>(g.loss, x, m[i][c], g.eps, f, yy);
@@ -251,7 +261,7 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float v[2] = {y[i][0], y[i][1]};
-                sts_vec<2>(Yn + (4 * g0 + i) * 32 + 2 * g1, v);
+                sts_vec<2>(Yn + (4 * g0 + i) * L::LDY + 2 * g1, v);
             }
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -279,7 +289,7 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
 #pragma unroll 4
                 for (int r = 0; r < 64; ++r) {
                     float a[2], b[TN];
-                    lds_vec<2>(a, Yn + r * 32 + 2 * g0);
+                    lds_vec<2>(a, Yn + r * L::LDY + 2 * g0);
                     lds_vec<TN>(b, KRn + r * LDR + TN * g1);
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
@@ -287,10 +297,23 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                         for (int q = 0; q < TN; ++q) g3[c][q] = fmaf(a[c], b[q], g3[c][q]);
                 }
             }
+            if (wantS) {   // g_s[j] += sum over this thread's rows of A1[i1][j] A2[i2][j] T[row][j]
+                const int row0 = 4 * g0, i1l = row0 >> lb2, i2l = row0 & (B2 - 1);   // B2 >= 4: one i1
+                float a1[TN];
+                lds_vec<TN>(a1, A1t + i1l * LDR + TN * g1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float a2[TN];
+                    lds_vec<TN>(a2, A2t + (i2l + i) * LDR + TN * g1);
+#pragma unroll
+                    for (int q = 0; q < TN; ++q) gsv[q] = fmaf(a1[q] * a2[q], tv[i][q], gsv[q]);
+                }
+            }
+            if (!wantG) continue;
 #pragma unroll
             for (int i = 0; i < 4; ++i) sts_vec<TN>(Ts + (4 * g0 + i) * LDR + TN * g1, tv[i]);   // KRt is free now
             __syncthreads();
-            if (wantG) {
+            {
                 for (int i = tid; i < B1 * RT; i += kBoxThreads) {
                     const int il = i / RT, j = i - il * RT;
                     float acc = 0.f;
@@ -303,12 +326,6 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                     for (int i1l = 0; i1l < B1; ++i1l) acc = fmaf(A1s[i1l * LDR + j], Ts[(i1l * B2 + il) * LDR + j], acc);
                     acc2[(t2 * B2 + il) * RT + j] += acc;
                 }
-            }
-            if (wantS && tid < RT) {
-                float acc = 0.f;
-                for (int row = 0; row < 64; ++row)
-                    acc += A1t[(row >> lb2) * LDR + tid] * A2t[(row & (B2 - 1)) * LDR + tid] * Ts[row * LDR + tid];
-                gsr += acc;
             }
         }
     }
@@ -333,7 +350,21 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                 if (i3 < I3 && j < R && g3[c][q] != 0.f) atomicAdd(g.G3 + (int64_t)i3 * R + j, g3[c][q]);
             }
     }
-    if (wantS && tid < R && gsr != 0.f) atomicAdd(g.gs + tid, gsr);
+    if (wantS) {   // over the 16 row groups g0: 8 lanes of a warp, then the warp pair (warp & 1)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) {
+            float v = gsv[q];
+            v += __shfl_xor_sync(SGCP_FULL_MASK, v, 1);
+            v += __shfl_xor_sync(SGCP_FULL_MASK, v, 2);
+            v += __shfl_xor_sync(SGCP_FULL_MASK, v, 4);
+            if ((tid & 7) == 0) gsb[(warp & 1) * RT + TN * g1 + q] = v;
+        }
+        __syncthreads();
+        if (tid < R) {
+            const float v = gsb[tid] + gsb[RT + tid];
+            if (v != 0.f) atomicAdd(g.gs + tid, v);
+        }
+    }
     if (wantF) {
         const double tot = box_block_sum((double)fsum, red);
         if (tid == 0 && tot != 0.0) atomicAdd(g.f, tot);
