@@ -244,6 +244,17 @@ inline uint32_t reservoir_index(uint64_t seed, int64_t t) {
 // Hot-row privatisation limits of the sparse kernel.
 constexpr int kMaxHot = 64;
 
+// p[0..3] += c (p 16-byte aligned) as one reduction without a returned value (red, not atom: the
+// adder never reads the old values, and a returning atomic costs L2-to-SM traffic and a
+// scoreboard slot per request).
+__device__ __forceinline__ void red_add_f4(float* p, float4 c) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(c.x), "f"(c.y), "f"(c.z), "f"(c.w)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_f2(float* p, float2 c) {   // p 8-byte aligned
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(c.x), "f"(c.y) : "memory");
+}
+
 __device__ __forceinline__ void set_err(int* err, int bits) {
     if (err) atomicOr(err, bits);
 }

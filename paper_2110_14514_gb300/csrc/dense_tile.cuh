@@ -330,25 +330,39 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
         }
     }
     __syncthreads();
-    if (wantG) {
-        const int S1 = B1 * g.n1, S2 = B2 * g.n2;
-        for (int i = tid; i < S1 * R; i += kBoxThreads) {
-            const int r = i / R, j = i - r * R;
-            const float v = acc1[r * RT + j];
-            if (g.o1 + r < I1 && v != 0.f) atomicAdd(g.G1 + (int64_t)(g.o1 + r) * R + j, v);
-        }
-        for (int i = tid; i < S2 * R; i += kBoxThreads) {
-            const int r = i / R, j = i - r * R;
-            const float v = acc2[r * RT + j];
-            if (g.o2 + r < I2 && v != 0.f) atomicAdd(g.G2 + (int64_t)(g.o2 + r) * R + j, v);
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-            for (int q = 0; q < TN; ++q) {
-                const int i3 = g.o3 + 2 * g0 + c, j = TN * g1 + q;
-                if (i3 < I3 && j < R && g3[c][q] != 0.f) atomicAdd(g.G3 + (int64_t)i3 * R + j, g3[c][q]);
+    if (wantG) {   // the box's rows, four columns per 16-byte reduction (R % 4 == 0: rows stay 16-byte aligned)
+        const int S1 = B1 * g.n1, S2 = B2 * g.n2, Q = R / 4;
+        const bool vec = ((reinterpret_cast<uintptr_t>(g.G1) | reinterpret_cast<uintptr_t>(g.G2) |
+                           reinterpret_cast<uintptr_t>(g.G3)) & 15) == 0;
+        auto add4 = [&](float* dst, float4 v) {
+            if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) return;
+            if (vec) {
+                red_add_f4(dst, v);
+            } else {
+                atomicAdd(dst, v.x), atomicAdd(dst + 1, v.y), atomicAdd(dst + 2, v.z), atomicAdd(dst + 3, v.w);
             }
+        };
+        for (int i = tid; i < S1 * Q; i += kBoxThreads) {
+            const int r = i / Q, j = 4 * (i - r * Q);
+            if (g.o1 + r < I1) add4(g.G1 + (int64_t)(g.o1 + r) * R + j, *reinterpret_cast<const float4*>(acc1 + r * RT + j));
+        }
+        for (int i = tid; i < S2 * Q; i += kBoxThreads) {
+            const int r = i / Q, j = 4 * (i - r * Q);
+            if (g.o2 + r < I2) add4(g.G2 + (int64_t)(g.o2 + r) * R + j, *reinterpret_cast<const float4*>(acc2 + r * RT + j));
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i3 = g.o3 + 2 * g0 + c;
+            if (i3 >= I3) continue;
+            const int j = TN * g1;   // TN consecutive columns
+            if constexpr (TN == 4) {
+                if (j < R) add4(g.G3 + (int64_t)i3 * R + j, make_float4(g3[c][0], g3[c][1], g3[c][2], g3[c][3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < TN; ++q)
+                    if (j + q < R && g3[c][q] != 0.f) atomicAdd(g.G3 + (int64_t)i3 * R + j + q, g3[c][q]);
+            }
+        }
     }
     if (wantS) {   // over the 16 row groups g0: 8 lanes of a warp, then the warp pair (warp & 1)
 #pragma unroll

@@ -131,14 +131,6 @@ __device__ __forceinline__ void gen_sample(const SparseGradArgs& a, const SliceD
     errb |= ERRB_SAMPLING;
 }
 
-// G row += c, 16 bytes at once, as a reduction without a returned value (red, not atom: the
-// scatter never reads the old row, and a returning atomic costs L2-to-SM traffic and a scoreboard
-// slot per request).
-__device__ __forceinline__ void red_add_f4(float* p, float4 c) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(c.x), "f"(c.y), "f"(c.z), "f"(c.w)
-                 : "memory");
-}
-
 __device__ __forceinline__ float4 f4mul(float4 a, float4 b) {
     return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
 }
