@@ -90,3 +90,35 @@ def test_sparse_backward_is_the_sampled_gradient(sg):
     for k in range(3):
         assert rel(A[k].grad.cpu().numpy(), Go[k]) < 1e-5
     assert rel(s.grad.cpu().numpy(), gso) < 1e-5
+
+
+def test_graph_captured_step_matches_oracle_after_new_inputs(sg):
+    """GraphedGCPLoss: forward + backward captured once; after new values are written into the
+    static slice and factors, a replay gives the oracle's loss and gradients at the new point."""
+    from paper_2110_14514_gb300.autograd import GraphedGCPLoss
+    cfg = S.workload("dense_poisson_3way")
+    A_np = S.init_factors(cfg)
+    s_np = np.full(cfg["rank"], 0.5, np.float32)
+    X = torch.from_numpy(S.dense_slice(cfg, 3)[0]).cuda()
+    A = [torch.from_numpy(a).cuda().requires_grad_(True) for a in A_np]
+    s = torch.from_numpy(s_np).cuda().requires_grad_(True)
+    p = sg.params(cfg["dims"], cfg["rank"], "poisson")
+    with sg.Context(p, [a.detach() for a in A]) as ctx:
+        step = GraphedGCPLoss(ctx, s, A, X=X)
+        rng = np.random.default_rng(11)
+        for t in (4, 5):
+            X2 = S.dense_slice(cfg, t)[0]
+            A2 = [(a * (0.9 + 0.2 * rng.random(a.shape))).astype(np.float32) for a in A_np]
+            s2 = (s_np * (0.8 + 0.4 * rng.random(s_np.shape))).astype(np.float32)
+            with torch.no_grad():
+                X.copy_(torch.from_numpy(X2))
+                s.copy_(torch.from_numpy(s2))
+                for a, a2 in zip(A, A2):
+                    a.copy_(torch.from_numpy(a2))
+            F = step.replay().item()
+            Go, gso, Fo = gcp.dense_gradient(X2, s2, A2, "poisson")
+            assert abs(F - Fo) <= 1e-4 * abs(Fo)
+            for k in range(3):
+                assert rel(A[k].grad.cpu().numpy(), Go[k]) < 1e-5
+            assert rel(s.grad.cpu().numpy(), gso) < 1e-5
+        ctx.check()
