@@ -555,8 +555,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (i3 < I3)
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        atomicAdd(reinterpret_cast<float4*>(a.G[2] + i3 * R + 16 * cq + 4 * q),
-                                  make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
+                        red_add_f4(a.G[2] + i3 * R + 16 * cq + 4 * q,
+                                   make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]));
             }
         };
         if (new_b3) {   // the A3 panel changes: T and G3 of this tile must be done first
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float4 w = *reinterpret_cast<const float4*>(red + (q * kB2 + i2l) * kStageLd + c4);
                     g.x += w.x, g.y += w.y, g.z += w.z, g.w += w.w;
                 }
-                atomicAdd(reinterpret_cast<float4*>(a.G[1] + (cur.i2b + i2l) * R + c4), g);
+                red_add_f4(a.G[1] + (cur.i2b + i2l) * R + c4, g);
             }
         }
         // red (= Yr) is read before the next epilogue writes Y: the barrier at the loop top orders it

@@ -539,8 +539,8 @@ __global__ void __launch_bounds__(256, 2) k_factor_update_rows(const FactorUpdat
             for (int x = 0; x < 4; ++x) {
                 float* P = a.gacc + (int64_t)k * RR + (l4 + x) * R + m4;
                 float* E = a.gacc + ((int64_t)a.ndim + k) * RR + (l4 + x) * R + m4;
-                atomicAdd(reinterpret_cast<float4*>(P), make_float4(P4[x][0], P4[x][1], P4[x][2], P4[x][3]));
-                atomicAdd(reinterpret_cast<float4*>(E), make_float4(E4[x][0], E4[x][1], E4[x][2], E4[x][3]));
+                red_add_f4(P, make_float4(P4[x][0], P4[x][1], P4[x][2], P4[x][3]));
+                red_add_f4(E, make_float4(E4[x][0], E4[x][1], E4[x][2], E4[x][3]));
             }
         }
     }
