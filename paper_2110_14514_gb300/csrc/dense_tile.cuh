@@ -14,9 +14,12 @@
 //   G3 += Y' . KR                                (KR carries s)
 // The three products run on one 16 x 16 thread grid; each keeps a 4 x 2,
 // 4 x RT/16 or 2 x RT/16 register tile and reads its operands from k-major
-// shared arrays, one 64- or 128-bit load per operand per k, so a warp's loads
-// are a single shared-memory wavefront each (the products are FMA-bound, not
-// load-bound).  R is padded to RT in {16, 32, 64} with zero columns.
+// shared arrays, one 64- or 128-bit load per operand per k.  A 128-bit load
+// takes four shared-memory wavefronts (one per quarter warp) even where lanes
+// share addresses, so these tiles issue ~1.5 FMA instructions per wavefront:
+// the products are bound by shared-memory wavefronts.  R is padded to RT in
+// {16, 32, 48, 64} with zero columns (RT = 48: three single-word loads per
+// operand row instead of one vector load).
 #pragma once
 
 #include "common.cuh"
@@ -80,6 +83,12 @@ __device__ __forceinline__ void lds_vec<1>(float (&d)[1], const float* p) {
     d[0] = *p;
 }
 template <>
+__device__ __forceinline__ void lds_vec<3>(float (&d)[3], const float* p) {   // 4-byte aligned: three words
+    d[0] = p[0];
+    d[1] = p[1];
+    d[2] = p[2];
+}
+template <>
 __device__ __forceinline__ void lds_vec<2>(float (&d)[2], const float* p) {
     const float2 v = *reinterpret_cast<const float2*>(p);
     d[0] = v.x;
@@ -99,6 +108,12 @@ __device__ __forceinline__ void sts_vec(float* p, const float (&d)[N]);
 template <>
 __device__ __forceinline__ void sts_vec<1>(float* p, const float (&d)[1]) {
     *p = d[0];
+}
+template <>
+__device__ __forceinline__ void sts_vec<3>(float* p, const float (&d)[3]) {
+    p[0] = d[0];
+    p[1] = d[1];
+    p[2] = d[2];
 }
 template <>
 __device__ __forceinline__ void sts_vec<2>(float* p, const float (&d)[2]) {
@@ -386,12 +401,13 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
 }
 
 // Padded rank for R (R <= 64, R % 4 == 0).
-__host__ __device__ inline int box_rt(int R) { return R <= 16 ? 16 : (R <= 32 ? 32 : 64); }
+__host__ __device__ inline int box_rt(int R) { return R <= 16 ? 16 : (R <= 32 ? 32 : (R <= 48 ? 48 : 64)); }
 
 // Dispatch on the padded rank.
 __device__ __forceinline__ void dense_box_any(const BoxGeom& g, int want, float* sm) {
     if (g.R <= 16) dense_box<16>(g, want, sm);
     else if (g.R <= 32) dense_box<32>(g, want, sm);
+    else if (g.R <= 48) dense_box<48>(g, want, sm);
     else dense_box<64>(g, want, sm);
 }
 

@@ -353,7 +353,8 @@ static bool dense_box_path(const DenseGradArgs<T>&, cudaStream_t, cudaError_t*) 
 template <>
 bool dense_box_path<float>(const DenseGradArgs<float>& a, cudaStream_t st, cudaError_t* e) {
     if (a.ndim != 3 || a.R > 64) return false;
-    *e = a.R <= 16 ? run_box<16>(a, st) : (a.R <= 32 ? run_box<32>(a, st) : run_box<64>(a, st));
+    *e = a.R <= 16 ? run_box<16>(a, st)
+                   : (a.R <= 32 ? run_box<32>(a, st) : (a.R <= 48 ? run_box<48>(a, st) : run_box<64>(a, st)));
     return true;
 }
 

@@ -56,7 +56,7 @@ def run(sg, X, A, s, loss, precision, want=7):
 
 @pytest.mark.parametrize("loss", ["gaussian", "poisson", "bernoulli_logit", "bernoulli_odds"])
 @pytest.mark.parametrize("dims,R", [((37, 45, 70), 16), ((33, 31, 29), 32), ((20, 70, 40), 64),
-                                    ((8, 9, 40), 4), ((50, 3, 33), 12)])
+                                    ((8, 9, 40), 4), ((50, 3, 33), 12), ((41, 29, 67), 40), ((36, 50, 33), 48)])
 def test_dense3_fp32_matches_oracle(sg, loss, dims, R):
     X, A, s = case(dims, R, loss, np.float32)
     G, gs, f = run(sg, X, A, s, loss, sg.PREC_F32)
