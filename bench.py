@@ -519,7 +519,7 @@ def run_native_dense(args, cfg, world, rank, local):
     launches = ctx.stats()["kernels_launched"] - k0
     total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     value = world * args.steps * grads_per_step * omega / total_s
-    if lsq_lbfgs:   # host-driven L-BFGS: gradient evaluations per step vary; report slice updates / s
+    if lsq_lbfgs:   # L-BFGS: gradient evaluations per step vary; report slice updates / s
         value = world * args.steps / total_s
     # dominant kernel: one factor gradient over the slice, back to back behind a sleep kernel
     A, _, _ = ctx.factors()
