@@ -141,12 +141,19 @@ __device__ __forceinline__ double box_block_sum(double v, double* red) {
 // Factor, s and slice reads go through L2 (ld.global.cg) for the factors and s,
 // which a persistent caller may have rewritten from another SM, and through the
 // read-only path for X, which no kernel writes while it is read.
-template <int RT>
+//
+// SPLIT (factor-gradient tiles): T and G3 run side by side on the two halves of
+// the block instead of one after the other on all of it -- warps 0-3 form T on
+// 8 x TN register tiles, warps 4-7 accumulate G3 on 4 x TN register tiles -- so
+// the two products issue about 2.7 and 2 FMAs per shared-memory wavefront
+// (8 x 4 / 12 and 4 x 4 / 8 at RT = 64) instead of 2 and 1.33; tiles without
+// factor gradients keep the 256-thread T.
+template <int RT, bool SPLIT = false>
 __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
     using L = TileLayout<RT>;
     constexpr int LDR = L::LDR;
     constexpr int TN = RT / 16;   // j values per thread in T and G3
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // 16 x 16 thread grid; a warp covers 8 x 4 of it, so per-k operand reads are contiguous
     const int g0 = (tid & 7) + 8 * (warp & 1);
     const int g1 = ((tid >> 3) & 3) + 4 * (warp >> 1);
@@ -185,9 +192,10 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
         A3t[j * 32 + c] = A3n[c * LDR + j];
     }
 
-    float g3[2][TN];
+    constexpr int G3C = SPLIT ? 4 : 2;   // i3 columns per thread in G3
+    float g3[G3C][TN];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < G3C; ++c)
 #pragma unroll
         for (int q = 0; q < TN; ++q) g3[c][q] = 0.f;
     float gsv[TN];   // this thread's share of the box's gradient of s, columns TN g1 ..
@@ -284,49 +292,108 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                 sts_vec<4>(Yt + (2 * g1 + c) * 64 + 4 * g0, v);
             }
             __syncthreads();
-            // T = Y . A3 on rows 4 g0 .., j = TN g1 ..
-            float tv[4][TN];
+            if (SPLIT && wantG) {
+                if (warp < 4) {
+                    // T = Y . A3 on rows 8 u0 .. 8 u0 + 7, j = TN u1 ..; a quarter warp covers two u0 and
+                    // four u1, so its Yt and A3 vectors fall on distinct banks (one wavefront each)
+                    const int u0 = 2 * (lane >> 3) + (lane & 1), u1 = 4 * warp + ((lane >> 1) & 3);
+                    float tv[8][TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int q = 0; q < TN; ++q) tv[i][q] = 0.f;
+                        for (int q = 0; q < TN; ++q) tv[i][q] = 0.f;
 #pragma unroll 4
-            for (int c = 0; c < 32; ++c) {
-                float a[4], b[TN];
-                lds_vec<4>(a, Yt + c * 64 + 4 * g0);
-                lds_vec<TN>(b, A3n + c * LDR + TN * g1);
+                    for (int c = 0; c < 32; ++c) {
+                        float a[4], a2[4], b[TN];
+                        lds_vec<4>(a, Yt + c * 64 + 8 * u0);
+                        lds_vec<4>(a2, Yt + c * 64 + 8 * u0 + 4);
+                        lds_vec<TN>(b, A3n + c * LDR + TN * u1);
+#pragma unroll
+                        for (int q = 0; q < TN; ++q) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) tv[i][q] = fmaf(a[i], b[q], tv[i][q]);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) tv[4 + i][q] = fmaf(a2[i], b[q], tv[4 + i][q]);
+                        }
+                    }
+                    if (wantS) {   // rows 8 u0 .. 8 u0 + 3 share one i1, rows 8 u0 + 4 .. + 7 another (B2 >= 4)
+                        float a1lo[TN], a1hi[TN];
+                        lds_vec<TN>(a1lo, A1t + ((8 * u0) >> lb2) * LDR + TN * u1);
+                        lds_vec<TN>(a1hi, A1t + ((8 * u0 + 4) >> lb2) * LDR + TN * u1);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float a2[TN];
+                            lds_vec<TN>(a2, A2t + ((8 * u0 + i) & (B2 - 1)) * LDR + TN * u1);
+#pragma unroll
+                            for (int q = 0; q < TN; ++q)
+                                gsv[q] = fmaf((i < 4 ? a1lo[q] : a1hi[q]) * a2[q], tv[i][q], gsv[q]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) sts_vec<TN>(Ts + (8 * u0 + i) * LDR + TN * u1, tv[i]);   // KRt is free now
+                } else {
+                    // G3 += Y' . KR on columns 4 v0 .. 4 v0 + 3, j = TN v1 ..
+                    const int v0 = lane & 7, v1 = 4 * (warp - 4) + (lane >> 3);
+#pragma unroll 4
+                    for (int r = 0; r < 64; ++r) {
+                        float a[2], a2[2], b[TN];
+                        lds_vec<2>(a, Yn + r * L::LDY + 4 * v0);
+                        lds_vec<2>(a2, Yn + r * L::LDY + 4 * v0 + 2);
+                        lds_vec<TN>(b, KRn + r * LDR + TN * v1);
+#pragma unroll
+                        for (int q = 0; q < TN; ++q) {
+                            g3[0][q] = fmaf(a[0], b[q], g3[0][q]);
+                            g3[1][q] = fmaf(a[1], b[q], g3[1][q]);
+                            g3[G3C - 2][q] = fmaf(a2[0], b[q], g3[G3C - 2][q]);
+                            g3[G3C - 1][q] = fmaf(a2[1], b[q], g3[G3C - 1][q]);
+                        }
+                    }
+                }
+            } else {
+                // T = Y . A3 on rows 4 g0 .., j = TN g1 ..
+                float tv[4][TN];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int q = 0; q < TN; ++q) tv[i][q] = fmaf(a[i], b[q], tv[i][q]);
-            }
-            if (wantG) {   // G3 += Y' . KR on columns 2 g0 .., j = TN g1 ..
+                    for (int q = 0; q < TN; ++q) tv[i][q] = 0.f;
 #pragma unroll 4
-                for (int r = 0; r < 64; ++r) {
-                    float a[2], b[TN];
-                    lds_vec<2>(a, Yn + r * L::LDY + 2 * g0);
-                    lds_vec<TN>(b, KRn + r * LDR + TN * g1);
+                for (int c = 0; c < 32; ++c) {
+                    float a[4], b[TN];
+                    lds_vec<4>(a, Yt + c * 64 + 4 * g0);
+                    lds_vec<TN>(b, A3n + c * LDR + TN * g1);
 #pragma unroll
-                    for (int c = 0; c < 2; ++c)
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int q = 0; q < TN; ++q) g3[c][q] = fmaf(a[c], b[q], g3[c][q]);
+                        for (int q = 0; q < TN; ++q) tv[i][q] = fmaf(a[i], b[q], tv[i][q]);
                 }
-            }
-            if (wantS) {   // g_s[j] += sum over this thread's rows of A1[i1][j] A2[i2][j] T[row][j]
-                const int row0 = 4 * g0, i1l = row0 >> lb2, i2l = row0 & (B2 - 1);   // B2 >= 4: one i1
-                float a1[TN];
-                lds_vec<TN>(a1, A1t + i1l * LDR + TN * g1);
+                if (!SPLIT && wantG) {   // G3 += Y' . KR on columns 2 g0 .., j = TN g1 ..
+#pragma unroll 4
+                    for (int r = 0; r < 64; ++r) {
+                        float a[2], b[TN];
+                        lds_vec<2>(a, Yn + r * L::LDY + 2 * g0);
+                        lds_vec<TN>(b, KRn + r * LDR + TN * g1);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float a2[TN];
-                    lds_vec<TN>(a2, A2t + (i2l + i) * LDR + TN * g1);
+                        for (int c = 0; c < 2; ++c)
 #pragma unroll
-                    for (int q = 0; q < TN; ++q) gsv[q] = fmaf(a1[q] * a2[q], tv[i][q], gsv[q]);
+                            for (int q = 0; q < TN; ++q) g3[c][q] = fmaf(a[c], b[q], g3[c][q]);
+                    }
                 }
-            }
-            if (!wantG) continue;
+                if (wantS) {   // g_s[j] += sum over this thread's rows of A1[i1][j] A2[i2][j] T[row][j]
+                    const int row0 = 4 * g0, i1l = row0 >> lb2, i2l = row0 & (B2 - 1);   // B2 >= 4: one i1
+                    float a1[TN];
+                    lds_vec<TN>(a1, A1t + i1l * LDR + TN * g1);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) sts_vec<TN>(Ts + (4 * g0 + i) * LDR + TN * g1, tv[i]);   // KRt is free now
+                    for (int i = 0; i < 4; ++i) {
+                        float a2[TN];
+                        lds_vec<TN>(a2, A2t + (i2l + i) * LDR + TN * g1);
+#pragma unroll
+                        for (int q = 0; q < TN; ++q) gsv[q] = fmaf(a1[q] * a2[q], tv[i][q], gsv[q]);
+                    }
+                }
+                if (!wantG) continue;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sts_vec<TN>(Ts + (4 * g0 + i) * LDR + TN * g1, tv[i]);   // KRt is free now
+            }
             __syncthreads();
             {
                 for (int i = tid; i < B1 * RT; i += kBoxThreads) {
@@ -365,11 +432,14 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
             const int r = i / Q, j = 4 * (i - r * Q);
             if (g.o2 + r < I2) add4(g.G2 + (int64_t)(g.o2 + r) * R + j, *reinterpret_cast<const float4*>(acc2 + r * RT + j));
         }
+        // G3 rows of this thread: 2 g0 .. (256-thread G3) or, in the split, 4 v0 .. on warps 4-7
+        const bool g3_mine = !SPLIT || warp >= 4;
+        const int c0 = SPLIT ? 4 * (lane & 7) : 2 * g0;
+        const int j = SPLIT ? TN * (4 * (warp - 4) + (lane >> 3)) : TN * g1;   // TN consecutive columns
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int i3 = g.o3 + 2 * g0 + c;
-            if (i3 >= I3) continue;
-            const int j = TN * g1;   // TN consecutive columns
+        for (int c = 0; c < G3C; ++c) {
+            const int i3 = g.o3 + c0 + c;
+            if (!g3_mine || i3 >= I3) continue;
             if constexpr (TN == 4) {
                 if (j < R) add4(g.G3 + (int64_t)i3 * R + j, make_float4(g3[c][0], g3[c][1], g3[c][2], g3[c][3]));
             } else {
@@ -379,18 +449,28 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
             }
         }
     }
-    if (wantS) {   // over the 16 row groups g0: 8 lanes of a warp, then the warp pair (warp & 1)
+    if (wantS) {
+        // 256-thread T: over the 16 row groups g0 (8 lanes of a warp, then the warp pair warp & 1);
+        // split T: over the 8 row groups u0 of a warp (lane bits 0, 3 and 4), warps 0-3 only
+        const bool split = SPLIT && wantG;
 #pragma unroll
         for (int q = 0; q < TN; ++q) {
             float v = gsv[q];
-            v += __shfl_xor_sync(SGCP_FULL_MASK, v, 1);
-            v += __shfl_xor_sync(SGCP_FULL_MASK, v, 2);
-            v += __shfl_xor_sync(SGCP_FULL_MASK, v, 4);
-            if ((tid & 7) == 0) gsb[(warp & 1) * RT + TN * g1 + q] = v;
+            if (split) {
+                v += __shfl_xor_sync(SGCP_FULL_MASK, v, 1);
+                v += __shfl_xor_sync(SGCP_FULL_MASK, v, 8);
+                v += __shfl_xor_sync(SGCP_FULL_MASK, v, 16);
+                if (warp < 4 && (lane & 0x19) == 0) gsb[TN * (4 * warp + ((lane >> 1) & 3)) + q] = v;
+            } else {
+                v += __shfl_xor_sync(SGCP_FULL_MASK, v, 1);
+                v += __shfl_xor_sync(SGCP_FULL_MASK, v, 2);
+                v += __shfl_xor_sync(SGCP_FULL_MASK, v, 4);
+                if ((tid & 7) == 0) gsb[(warp & 1) * RT + TN * g1 + q] = v;
+            }
         }
         __syncthreads();
         if (tid < R) {
-            const float v = gsb[tid] + gsb[RT + tid];
+            const float v = gsb[tid] + (split ? 0.f : gsb[RT + tid]);
             if (v != 0.f) atomicAdd(g.gs + tid, v);
         }
     }
@@ -404,11 +484,12 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
 __host__ __device__ inline int box_rt(int R) { return R <= 16 ? 16 : (R <= 32 ? 32 : (R <= 48 ? 48 : 64)); }
 
 // Dispatch on the padded rank.
+template <bool SPLIT = false>
 __device__ __forceinline__ void dense_box_any(const BoxGeom& g, int want, float* sm) {
-    if (g.R <= 16) dense_box<16>(g, want, sm);
-    else if (g.R <= 32) dense_box<32>(g, want, sm);
-    else if (g.R <= 48) dense_box<48>(g, want, sm);
-    else dense_box<64>(g, want, sm);
+    if (g.R <= 16) dense_box<16, SPLIT>(g, want, sm);
+    else if (g.R <= 32) dense_box<32, SPLIT>(g, want, sm);
+    else if (g.R <= 48) dense_box<48, SPLIT>(g, want, sm);
+    else dense_box<64, SPLIT>(g, want, sm);
 }
 
 constexpr int kBoxSmemFloats = TileLayout<64>::TOTAL;

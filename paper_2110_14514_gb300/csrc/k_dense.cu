@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kBoxThreads, 2) k_dense3_box(const DenseGradAr
     g.gs = a.gs;
     g.f = a.f;
     g.ysc = a.y_scale ? *a.y_scale : 1.0f;
-    dense_box<RT>(g, a.want, box_sm);
+    dense_box<RT, true>(g, a.want, box_sm);
     if (a.tstep_on && last_block_ticket(a.tstep.st)) temporal_step_tail<float>(a.tstep, a.gs, R);
 }
 
