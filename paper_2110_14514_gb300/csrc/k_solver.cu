@@ -709,19 +709,6 @@ cudaError_t launch_obj_finish_w(SolverState* st, const T* s, int R, double mu, i
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(1024) k_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
-                               const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip) {
-    if (skip && *skip) return;
-    obj_finish_f_block(st, ndim, R, grams, SH, *hist_len > 0, lam, set_cur, err);
-}
-
-cudaError_t launch_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
-                                const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip,
-                                cudaStream_t stream, int64_t* launches) {
-    k_obj_finish_f<<<1, 1024, 0, stream>>>(st, ndim, R, grams, SH, hist_len, lam, set_cur, err, skip);
-    if (launches) *launches += 1;
-    return cudaGetLastError();
-}
 
 // S_H = sum_{h in window} w theta^(t-h) s_h s_h'
 template <typename T>
@@ -1178,6 +1165,51 @@ template <typename T>
 cudaError_t launch_reg_objective(SolverState* st, const T* W, int64_t n, double lam, int set_cur, int* err,
                                  const int32_t* skip, cudaStream_t stream, int64_t* launches) {
     k_reg_objective<T><<<kLbCluster, kLbThreads, 0, stream>>>(st, W, n, lam, set_cur, err, skip);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+// Factor solver's objective terms beyond the sampled loss: F_new += 1/2 sum_h w_h ||Mbar_h - M_h||^2
+// (eq. gcp_stream_objective, telescoped Gram form: sum over entries (l, m) of S_H[l][m] times
+// sum_{k, kk} prod_n Gram_n(which(k, n), which(kk, n))[l][m]) + lambda/2 sum_n ||A^(n)||^2.  One
+// 8-CTA cluster: a work item is one (entry, k, kk) triple, whose ndim Gram entries are independent
+// loads, so each thread has a few loads in flight instead of one block walking every product of every
+// entry; the per-thread sums are reduced across the cluster in a fixed order.
+__global__ void __cluster_dims__(kLbCluster, 1, 1) __launch_bounds__(kLbThreads)
+    k_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH, const int32_t* hist_len,
+                   double lam, int set_cur, int* err, const int32_t* skip) {
+    __shared__ double red[32];
+    __shared__ double part;
+    if (skip && *skip) return;   // the same flag for every CTA of the cluster
+    const bool hist = *hist_len > 0;
+    const int RR = R * R, D2 = ndim * ndim;
+    double acc = 0.0, reg = 0.0;
+    for (int64_t it = lb_first(); it < (int64_t)RR * D2; it += lb_stride()) {
+        const int i = (int)(it / D2), kp = (int)(it - (int64_t)i * D2);
+        const int k = kp / ndim, kk = kp - k * ndim;
+        const int l = i / R, m = i - l * R;
+        if (hist) {
+            double prod = 1.0;
+#pragma unroll 4
+            for (int n = 0; n < ndim; ++n) prod *= gram_entry(grams, ndim, R, n, which_mat(k, n), which_mat(kk, n), l, m);
+            acc += __ldcg(SH + i) * prod;
+        }
+        if (kp == 0 && l == m)
+            for (int n = 0; n < ndim; ++n) reg += __ldcg(grams + (int64_t)n * RR + i);
+    }
+    const double tot = lb_cluster_sum(0.5 * acc + 0.5 * lam * reg, red, &part);
+    if (lb_leader()) {
+        const double F = __ldcg(&st->F_new) + tot;
+        st->F_new = F;
+        if (!isfinite(F)) set_err(err, ERRB_NUMERIC);
+        if (set_cur) st->F_cur = F;
+    }
+}
+
+cudaError_t launch_obj_finish_f(SolverState* st, int ndim, int R, const double* grams, const double* SH,
+                                const int32_t* hist_len, double lam, int set_cur, int* err, const int32_t* skip,
+                                cudaStream_t stream, int64_t* launches) {
+    k_obj_finish_f<<<kLbCluster, kLbThreads, 0, stream>>>(st, ndim, R, grams, SH, hist_len, lam, set_cur, err, skip);
     if (launches) *launches += 1;
     return cudaGetLastError();
 }
