@@ -202,10 +202,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tb = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
     const int te = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
 
-    __nv_bfloat16* KRh[2] = {reinterpret_cast<__nv_bfloat16*>(sm + P.KRh0), reinterpret_cast<__nv_bfloat16*>(sm + P.KRh1)};
+    auto KRhp = [&](int b) { return reinterpret_cast<__nv_bfloat16*>(sm + (b ? P.KRh1 : P.KRh0)); };
     __nv_bfloat16* KRl = reinterpret_cast<__nv_bfloat16*>(sm + P.KRl);
-    __half* KR3[2] = {BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.KR30),
-                      BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.KR31)};
+    auto KR3p = [&](int b) { return reinterpret_cast<__half*>(sm + (b ? P.KR31 : P.KR30)); };
     __nv_bfloat16* A3hi = reinterpret_cast<__nv_bfloat16*>(sm + P.A3hi);
     __nv_bfloat16* A3lo = reinterpret_cast<__nv_bfloat16*>(sm + P.A3lo);
     __half* A316 = BF16 ? nullptr : reinterpret_cast<__half*>(sm + P.A316);
@@ -312,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid < lo || tid >= lo + cnt) return;
         const float* A1 = stage + sbuf * 24 * kStageLd;
         const float* A2 = A1 + kB1 * kStageLd;
-        __nv_bfloat16* kh = KRh[kbuf];
+        __nv_bfloat16* kh = KRhp(kbuf);
         const int nj = R / 8;
         for (int i = tid - lo; i < kRows * nj; i += cnt) {
             const int rlo = i & 7, rest = i >> 3;
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(kh) + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KRl) + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
             if (!BF16)
-                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KR3[kbuf]) + off) =
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(KR3p(kbuf)) + off) =
                     make_uint4(h16[0], h16[1], h16[2], h16[3]);
         }
     };
@@ -358,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // counts 16-byte units), loops unrolled, so the issuing thread spends a few instructions per MMA
     auto issue_gemm1 = [&](int dbuf, int kbuf) {
         if (tid == 0) {
-            const uint64_t ahd = make_desc(smem_u32(KRh[kbuf]), 128, sboR), ald = make_desc(smem_u32(KRl), 128, sboR);
+            const uint64_t ahd = make_desc(smem_u32(KRhp(kbuf)), 128, sboR), ald = make_desc(smem_u32(KRl), 128, sboR);
             const uint64_t bh = make_desc(smem_u32(A3hi), 128, sboR), bl = make_desc(smem_u32(A3lo), 128, sboR);
             const uint32_t d = tmem + (uint32_t)dbuf * 128;
             const int nk = R >> 4;
@@ -379,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t at = make_desc(smem_u32(Yr), 128, 2048);
             const uint64_t bt = make_desc(smem_u32(BF16 ? (const void*)A3hi : (const void*)A316), sboR, 128);
             const uint64_t ag = make_desc(smem_u32(Yr), 2048, 128);
-            const uint64_t bg = make_desc(smem_u32(BF16 ? (const void*)KRh[kbuf] : (const void*)KR3[kbuf]), sboR, 128);
+            const uint64_t bg = make_desc(smem_u32(BF16 ? (const void*)KRhp(kbuf) : (const void*)KR3p(kbuf)), sboR, 128);
             const uint64_t stp = (uint64_t)(2 * sboR) >> 4;
 #pragma unroll
             for (int kk = 0; kk < kCols / 16; ++kk)
