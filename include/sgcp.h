@@ -136,8 +136,13 @@ typedef struct {
 
 /* One slice.  Sparse: nnz COO entries (idx [nnz][ndim] int32, vals [nnz]).
  * Dense: vals holds the full slice in C order, idx is NULL.
- * on_host = 1 means idx / vals are host pointers; the call copies them to the
- * device on the context's stream before use (the copy is part of the call). */
+ * on_host = 1 means idx / vals are host pointers; the call queues their copy to
+ * the device on a copy stream of the context, ordered before every use of the
+ * slice and after the work of the step before last, so that it can overlap the
+ * previous step.  From pinned (page-locked) host memory the copy is
+ * asynchronous: the host buffers must stay unchanged until the context stream
+ * has passed the call (sgcp_check, sgcp_stats or a synchronisation of that
+ * stream); pageable host memory may be reused once the call returns. */
 typedef struct {
     int32_t is_sparse;
     int32_t on_host;
@@ -378,6 +383,18 @@ sgcp_status sgcp_check(sgcp_ctx* ctx);
 
 /* Synchronise and report solver statistics of the last slice. */
 sgcp_status sgcp_stats(sgcp_ctx* ctx, sgcp_stats_t* out);
+
+/* Queue on the context stream, behind the work queued so far, a device-to-host
+ * copy of the two objective estimates of the last processed slice: out[0] =
+ * the temporal solver's F (EstimateObjective of Alg. 3 at its accepted point),
+ * out[1] = the factor solver's (Alg. 4), the values sgcp_stats reports as F_w
+ * and F_f.  out: host memory for 2 doubles, owned by the caller; with pinned
+ * (page-locked) memory the call returns at once and the values are valid once
+ * the context stream has passed this point (cudaStreamSynchronize on it, or
+ * sgcp_check); with pageable memory the copy completes before the call
+ * returns.  Lets a caller read every step's result without draining the GPU
+ * between steps.  No device error check: sgcp_check reports latched errors. */
+sgcp_status sgcp_objectives_async(sgcp_ctx* ctx, double* out);
 
 /* Checkpoint: the state that makes the stream resumable (t, i, Abar, s,
  * history window, factor-solver ADAM moments, learning rate).  sgcp_state_size

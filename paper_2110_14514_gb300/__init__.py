@@ -111,6 +111,7 @@ SIGNATURES = [
     ("sgcp_history", c_int32, [c_void_p, POINTER(c_int64), c_void_p, POINTER(c_int32)]),
     ("sgcp_check", c_int32, [c_void_p]),
     ("sgcp_stats", c_int32, [c_void_p, POINTER(sgcp_stats_t)]),
+    ("sgcp_objectives_async", c_int32, [c_void_p, c_void_p]),
     ("sgcp_state_size", c_int32, [c_void_p, POINTER(c_size_t)]),
     ("sgcp_state_export", c_int32, [c_void_p, c_void_p, c_size_t]),
     ("sgcp_state_import", c_int32, [c_void_p, c_void_p, c_size_t]),
@@ -423,6 +424,12 @@ class Context:
         code = lib.sgcp_stats(self.h, ctypes.byref(st))
         _check(code, self.h)
         return {f: getattr(st, f) for f, _ in sgcp_stats_t._fields_}
+
+    def objectives_async(self, out):
+        """Queue the copy of the last slice's (F_w, F_f) into out (a pinned host float64 tensor of
+        2 elements) on the context stream; valid after the stream reaches it (sgcp_objectives_async)."""
+        assert out.dtype == self._torch.float64 and out.numel() >= 2 and not out.is_cuda and out.is_contiguous()
+        _check(lib.sgcp_objectives_async(self.h, c_void_p(out.data_ptr())), self.h)
 
     def state_export(self):
         n = c_size_t()

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <initializer_list>
 #include <new>
@@ -85,10 +86,17 @@ struct sgcp_ctx {
     int nhot = kMaxHot;
 
     // staging of host slices
-    void* stage_idx = nullptr;
-    size_t stage_idx_bytes = 0;
-    void* stage_vals = nullptr;
-    size_t stage_vals_bytes = 0;
+    // staging of host (and realigned) slices: two buffer pairs used in turn, filled on copy_stream
+    // so that the copy of one step's slice overlaps the work of the step before it
+    void* stage_idx[2] = {nullptr, nullptr};
+    size_t stage_idx_bytes[2] = {0, 0};
+    void* stage_vals[2] = {nullptr, nullptr};
+    size_t stage_vals_bytes[2] = {0, 0};
+    int stage_next = 0;                       // buffer pair of the next staged slice
+    bool stage_used[2] = {false, false};      // pair holds a slice that queued work may read
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_stage_used[2] = {nullptr, nullptr};   // end of the work queued while a pair was current
+    cudaEvent_t ev_staged = nullptr;          // the latest staging copies are complete
 
     // slice currently loaded
     bool loaded = false;
@@ -243,27 +251,48 @@ sgcp_status load_slice(sgcp_ctx* c, const sgcp_slice* X, int64_t t, bool force_i
     if (X->on_host || restage) {
         const size_t ib = sparse ? (size_t)nnz * c->ndim * sizeof(int32_t) : 0;
         const size_t vb = (size_t)nnz * (sparse ? sizeof(float) : c->esz);
-        if (ib > c->stage_idx_bytes) {
-            dfree(c, c->stage_idx);
-            c->stage_idx = nullptr;
-            c->stage_idx_bytes = 0;
-            sgcp_status st = dalloc(c, &c->stage_idx, ib);
-            if (st) return st;
-            c->stage_idx_bytes = ib;
+        // Pair b is refilled; the other pair was current for all the work queued since the last
+        // staged slice, whose end is marked here.  Pair b was last read by the work before that
+        // mark two staged slices ago: the copy stream waits for it, the context stream waits for
+        // the copies.
+        if (!c->copy_stream) {   // created with the first staged slice: contexts fed device slices never hold it
+            CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+            CK(cudaEventCreateWithFlags(&c->ev_staged, cudaEventDisableTiming), "staging event");
+            CK(cudaEventCreateWithFlags(&c->ev_stage_used[0], cudaEventDisableTiming), "staging event");
+            CK(cudaEventCreateWithFlags(&c->ev_stage_used[1], cudaEventDisableTiming), "staging event");
         }
-        if (vb > c->stage_vals_bytes) {
-            dfree(c, c->stage_vals);
-            c->stage_vals = nullptr;
-            c->stage_vals_bytes = 0;
-            sgcp_status st = dalloc(c, &c->stage_vals, vb);
+        const int b = c->stage_next;
+        if (c->stage_used[b ^ 1]) CK(cudaEventRecord(c->ev_stage_used[b ^ 1], c->stream), "staging event");
+        if (ib > c->stage_idx_bytes[b]) {
+            dfree(c, c->stage_idx[b]);
+            c->stage_idx[b] = nullptr;
+            c->stage_idx_bytes[b] = 0;
+            sgcp_status st = dalloc(c, &c->stage_idx[b], ib);
             if (st) return st;
-            c->stage_vals_bytes = vb;
+            c->stage_idx_bytes[b] = ib;
         }
+        if (vb > c->stage_vals_bytes[b]) {
+            dfree(c, c->stage_vals[b]);
+            c->stage_vals[b] = nullptr;
+            c->stage_vals_bytes[b] = 0;
+            sgcp_status st = dalloc(c, &c->stage_vals[b], vb);
+            if (st) return st;
+            c->stage_vals_bytes[b] = vb;
+        }
+        if (c->stage_used[b]) CK(cudaStreamWaitEvent(c->copy_stream, c->ev_stage_used[b], 0), "staging wait");
         const cudaMemcpyKind kind = X->on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        if (ib) CK(cudaMemcpyAsync(c->stage_idx, X->idx, ib, kind, c->stream), "copy slice idx");
-        if (vb) CK(cudaMemcpyAsync(c->stage_vals, X->vals, vb, kind, c->stream), "copy slice vals");
-        idx_d = c->stage_idx;
-        vals_d = c->stage_vals;
+        if (!X->on_host) {   // a realigned device slice: work queued on the context stream may still write it
+            CK(cudaEventRecord(c->ev_staged, c->stream), "staging order");
+            CK(cudaStreamWaitEvent(c->copy_stream, c->ev_staged, 0), "staging order");
+        }
+        if (ib) CK(cudaMemcpyAsync(c->stage_idx[b], X->idx, ib, kind, c->copy_stream), "copy slice idx");
+        if (vb) CK(cudaMemcpyAsync(c->stage_vals[b], X->vals, vb, kind, c->copy_stream), "copy slice vals");
+        CK(cudaEventRecord(c->ev_staged, c->copy_stream), "staging event");
+        CK(cudaStreamWaitEvent(c->stream, c->ev_staged, 0), "staging wait");
+        c->stage_used[b] = true;
+        c->stage_next = b ^ 1;
+        idx_d = c->stage_idx[b];
+        vals_d = c->stage_vals[b];
         force_ingest = true;
     }
     c->cur.idx = (const int32_t*)idx_d;
@@ -1549,6 +1578,7 @@ void sgcp_destroy(sgcp_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     for (int i = 0; i < 2; ++i)
         if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
     for (void* p : c->allocs) c->custom_alloc ? c->ualloc.free(p, c->ualloc.user) : (void)cudaFree(p);
@@ -1558,6 +1588,10 @@ void sgcp_destroy(sgcp_ctx* c) {
     if (c->lb_stream) cudaStreamDestroy(c->lb_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->ev_staged) cudaEventDestroy(c->ev_staged);
+    for (int i = 0; i < 2; ++i)
+        if (c->ev_stage_used[i]) cudaEventDestroy(c->ev_stage_used[i]);
     delete c;
 }
 
@@ -1855,6 +1889,19 @@ sgcp_status sgcp_stats(sgcp_ctx* c, sgcp_stats_t* out) {
     out->kernels_launched = c->launches;
     out->evals_f = c->P.optimizer == SGCP_OPT_LBFGS ? f.evals : 0;
     return st;
+}
+
+sgcp_status sgcp_objectives_async(sgcp_ctx* c, double* out) {
+    if (!c || !out) return SGCP_ERR_ARG;
+    if (sgcp_status st = check_ready(c)) return st;
+    const size_t off = offsetof(SolverState, F_cur);
+    cudaError_t e = cudaMemcpyAsync(out, reinterpret_cast<const char*>(c->st_w) + off, sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + 1, reinterpret_cast<const char*>(c->st_f) + off, sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "objective read-back");
+    return SGCP_OK;
 }
 
 // Checkpoint layout: header, then Abar, s, history weights, u, v (element type T).

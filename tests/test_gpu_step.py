@@ -356,3 +356,43 @@ def test_stored_slice_history_rejects_lbfgs_mixed_slices_and_checkpoints(sg):
         with pytest.raises(sg.SgcpError) as e:
             ctx.state_export()
         assert e.value.status == sg.ERR_UNSUPPORTED
+
+
+def test_objective_read_back_without_draining_the_stream(sg):
+    """sgcp_objectives_async queues each step's (F_w, F_f) copy behind that step: four steps from
+    pinned host slices with no host wait in between give, after one wait, the last values that
+    sgcp_stats reports, and every step's values agree with a context stepped with a wait after each
+    step (FP32 atomic sums: relative 1e-5)."""
+    dims, R = (300, 170, 90), 16
+    cfg = S.workload("sparse_binary_zipf")
+    rng = np.random.default_rng(5)
+    A0 = [(0.3 * rng.random((n, R)) + 0.05).astype(np.float32) for n in dims]
+    host = []
+    for t in range(1, 5):
+        idx, val = S.sparse_slice(cfg, t, nnz=6000, dims=dims)
+        host.append((torch.from_numpy(np.ascontiguousarray(idx)).pin_memory(),
+                     torch.from_numpy(np.ascontiguousarray(val)).pin_memory()))
+    kw = dict(H=2, w=1.0, kappa_w=2, tau_w=5, alpha_w=0.05, kappa_f=2, tau_f=5, alpha_f=0.01,
+              p=900, q=900, p_obj=1500, q_obj=1500, seed=23)
+    p = sg.params(dims, R, "bernoulli_logit", **kw)
+    ref = []
+    with sg.Context(p, [dev(a) for a in A0]) as ctx:
+        for i, v in host:
+            ctx.step(idx=i, vals=v)
+            st = ctx.stats()
+            ref.append((st["F_w"], st["F_f"]))
+    out = torch.full((len(host), 2), float("nan"), dtype=torch.float64).pin_memory()
+    with sg.Context(p, [dev(a) for a in A0]) as ctx:
+        for k, (i, v) in enumerate(host):
+            ctx.step(idx=i, vals=v)
+            ctx.objectives_async(out[k])
+        ctx.stream.synchronize()
+        ctx.check()
+        st = ctx.stats()
+        assert out[-1, 0].item() == st["F_w"] and out[-1, 1].item() == st["F_f"]
+    got = out.numpy()
+    assert np.isfinite(got).all()
+    for k, (fw, ff) in enumerate(ref):
+        assert abs(got[k, 0] - fw) <= 1e-5 * max(abs(fw), 1.0), (k, got[k, 0], fw)
+        assert abs(got[k, 1] - ff) <= 1e-5 * max(abs(ff), 1.0), (k, got[k, 1], ff)
+    assert len({float(x) for x in got[:, 1]}) == len(host)   # one value per step, not one repeated
