@@ -337,6 +337,9 @@ def run_native(args, cfg, world, rank, local):
     # copied back into its own pinned row behind that step, without draining the GPU in between)
     e2e_steps = max(2, min(args.steps, 5))
     f_host = torch.zeros((e2e_steps, 2), dtype=torch.float64).pin_memory()
+    for w in range(2):                            # untimed: the two staging buffers are allocated here
+        i, v = pinned[w % N_SLICES]
+        ctx.step(idx=i, vals=v)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -810,16 +813,24 @@ def run_native_batched(args, cfg, world, rank, local):
     total_s = sum(step_s)
     value = world * args.steps * entries / total_s
     # end to end: host slices copied inside the call, per-stream objectives read back
-    e2e_steps = max(2, args.steps // 2)
+    # (every stream's F_w, F_f gathered and copied back behind each step, without draining the GPU)
+    e2e_steps = max(3, args.steps // 2)
+    f_host = torch.zeros((e2e_steps, 2 * n), dtype=torch.float64).pin_memory()
+    for w in range(2):                            # untimed: the two staging buffers are allocated here
+        b.step(host[w % n_sl])
     torch.cuda.synchronize()
     te = time.perf_counter()
     d2h = 0
     for k in range(e2e_steps):
         b.step(host[k % n_sl])
-        Fs = [b.stats(s)["F_f"] for s in range(n)]
-        d2h += n * 8
+        b.objectives_async(f_host[k])
+        d2h += n * 16
+    b.stream.synchronize()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
+    b.check()
+    if not bool(torch.isfinite(f_host).all()):
+        raise RuntimeError("batched end-to-end steps returned a non-finite objective")
     h2d = sum(int(np.prod(d)) * 4 for d, _, _ in shapes)
     table = b.tune_table()
     b.close()

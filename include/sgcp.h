@@ -460,8 +460,11 @@ const char* sgcp_batch_last_error(const sgcp_batch* batch);
 /* Advance every stream by one slice.  X: host array of n_streams pointers to
  * dense float slices in C order (I_1 x I_2 x I_3 of that stream); device
  * pointers when x_on_host = 0, host pointers when x_on_host = 1 (the call then
- * copies them to library-owned device buffers on the batch stream).  The
- * caller keeps device inputs alive until the step has completed.
+ * queues their copies into one of two library-owned staging buffers, used in
+ * turn, on a copy stream of the batch, so that they overlap the step before;
+ * the batch stream waits for them).  The caller keeps device inputs alive,
+ * and pinned host inputs unchanged, until the step has completed; pageable
+ * host inputs may be reused once the call returns.
  * Asynchronous on the batch stream. */
 sgcp_status sgcp_batch_step(sgcp_batch* batch, const void* const* X, int32_t x_on_host);
 
@@ -472,6 +475,16 @@ sgcp_status sgcp_batch_factors(sgcp_batch* batch, int32_t s, void* const* A_out,
 
 /* Synchronise; statistics of stream s after its last slice (as sgcp_stats). */
 sgcp_status sgcp_batch_stats(sgcp_batch* batch, int32_t s, sgcp_stats_t* out);
+
+/* Queue on the batch stream, behind the work queued so far, the read-back of
+ * every stream's two objective estimates after its last slice (the F_w and F_f
+ * of sgcp_batch_stats; EstimateObjective of Alg. 3 and 4): out[2 s] and
+ * out[2 s + 1] for stream s.  out: host memory for 2 x (number of streams)
+ * doubles, owned by the caller; with pinned memory the call returns at once
+ * and the values are valid once the batch stream has passed this point
+ * (sgcp_batch_check or a synchronisation of the stream).  One gather kernel
+ * and one copy; the gather buffer is allocated at the first call. */
+sgcp_status sgcp_batch_objectives_async(sgcp_batch* batch, double* out);
 
 /* Synchronise and return the latched device error status of the batch. */
 sgcp_status sgcp_batch_check(sgcp_batch* batch);

@@ -112,6 +112,7 @@ SIGNATURES = [
     ("sgcp_check", c_int32, [c_void_p]),
     ("sgcp_stats", c_int32, [c_void_p, POINTER(sgcp_stats_t)]),
     ("sgcp_objectives_async", c_int32, [c_void_p, c_void_p]),
+    ("sgcp_batch_objectives_async", c_int32, [c_void_p, c_void_p]),
     ("sgcp_state_size", c_int32, [c_void_p, POINTER(c_size_t)]),
     ("sgcp_state_export", c_int32, [c_void_p, c_void_p, c_size_t]),
     ("sgcp_state_import", c_int32, [c_void_p, c_void_p, c_size_t]),
@@ -552,6 +553,13 @@ class Batch:
         st = sgcp_stats_t()
         _check(lib.sgcp_batch_stats(self.h, s, ctypes.byref(st)), batch=self.h)
         return {f: getattr(st, f) for f, _ in sgcp_stats_t._fields_}
+
+    def objectives_async(self, out):
+        """Queue the read-back of every stream's (F_w, F_f) into out (a pinned host float64 tensor
+        of 2 x n elements) on the batch stream (sgcp_batch_objectives_async)."""
+        t = self._torch
+        assert out.dtype == t.float64 and out.numel() >= 2 * self.n and not out.is_cuda and out.is_contiguous()
+        _check(lib.sgcp_batch_objectives_async(self.h, c_void_p(out.data_ptr())), batch=self.h)
 
     def check(self):
         _check(lib.sgcp_batch_check(self.h), batch=self.h)

@@ -31,8 +31,17 @@ struct sgcp_batch {
     int* finished = nullptr;
     int* err = nullptr;
     void* arena = nullptr;
-    float* xstage = nullptr;               // host-slice staging, one region per stream
+    // host-slice staging: two buffers used in turn, one region per stream in each, filled on
+    // copy_stream so that the copies of one step's slices overlap the step before it
+    float* xstage[2] = {nullptr, nullptr};
     std::vector<int64_t> xoff;
+    int64_t xstage_floats = 0;
+    int xnext = 0;                         // buffer of the next staged step
+    bool xused[2] = {false, false};        // buffer holds slices that queued work may read
+    cudaStream_t copy_stream = nullptr;    // created with the first staged step
+    cudaEvent_t ev_xused[2] = {nullptr, nullptr};   // end of the work queued while a buffer was current
+    cudaEvent_t ev_xstaged = nullptr;
+    double* fout = nullptr;                // [nS][2] objective estimates gathered for the host
     std::vector<std::vector<int64_t>> hist_t;
     std::vector<int64_t> t;
     std::vector<BatchStepEntry> hE;
@@ -533,10 +542,16 @@ void sgcp_batch_destroy(sgcp_batch* b) {
     if (!b) return;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->copy_stream) cudaStreamSynchronize(b->copy_stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    void* ptrs[] = {b->arena, b->dS, b->dE, b->ctl, b->dorder, b->finished, b->err, b->xstage};
+    void* ptrs[] = {b->arena, b->dS, b->dE, b->ctl, b->dorder, b->finished, b->err, b->xstage[0], b->xstage[1],
+                    b->fout};
     for (void* p : ptrs) bfree(b, p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
+    if (b->ev_xstaged) cudaEventDestroy(b->ev_xstaged);
+    for (int i = 0; i < 2; ++i)
+        if (b->ev_xused[i]) cudaEventDestroy(b->ev_xused[i]);
     delete b;
 }
 
@@ -547,24 +562,41 @@ sgcp_status sgcp_batch_step(sgcp_batch* b, const void* const* X, int32_t x_on_ho
     if (!X) return bfail(b, SGCP_ERR_ARG, "batch step: X is NULL");
     for (int s = 0; s < b->nS; ++s)
         if (!X[s]) return bfail(b, SGCP_ERR_ARG, "batch step: a slice pointer is NULL");
-    if (x_on_host && !b->xstage) {
-        int64_t tot = 0;
-        b->xoff.resize(b->nS);
-        for (int s = 0; s < b->nS; ++s) {
-            b->xoff[s] = tot;
-            const BatchStream& S = b->hS[s];
-            tot += ((int64_t)S.dims[0] * S.dims[1] * S.dims[2] + 63) / 64 * 64;
+    int xb = -1;   // staging buffer of this step (host slices)
+    if (x_on_host) {
+        if (b->xoff.empty()) {
+            int64_t tot = 0;
+            b->xoff.resize(b->nS);
+            for (int s = 0; s < b->nS; ++s) {
+                b->xoff[s] = tot;
+                const BatchStream& S = b->hS[s];
+                tot += ((int64_t)S.dims[0] * S.dims[1] * S.dims[2] + 63) / 64 * 64;
+            }
+            b->xstage_floats = tot;
         }
-        if (!balloc(b, &b->xstage, tot * sizeof(float))) return bfail(b, SGCP_ERR_OOM, "slice staging allocation failed");
+        if (!b->copy_stream) {
+            BCK(cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking), "copy stream");
+            BCK(cudaEventCreateWithFlags(&b->ev_xstaged, cudaEventDisableTiming), "staging event");
+            BCK(cudaEventCreateWithFlags(&b->ev_xused[0], cudaEventDisableTiming), "staging event");
+            BCK(cudaEventCreateWithFlags(&b->ev_xused[1], cudaEventDisableTiming), "staging event");
+        }
+        // Buffer xb is refilled; the other buffer was current for all the work queued since the
+        // last staged step, whose end is marked here.  xb was last read by the work before that
+        // mark two staged steps ago: the copy stream waits for it, the batch stream for the copies.
+        xb = b->xnext;
+        if (!b->xstage[xb] && !balloc(b, &b->xstage[xb], b->xstage_floats * sizeof(float)))
+            return bfail(b, SGCP_ERR_OOM, "slice staging allocation failed");
+        if (b->xused[xb ^ 1]) BCK(cudaEventRecord(b->ev_xused[xb ^ 1], b->stream), "staging event");
+        if (b->xused[xb]) BCK(cudaStreamWaitEvent(b->copy_stream, b->ev_xused[xb], 0), "staging wait");
     }
     for (int s = 0; s < b->nS; ++s) {
         const BatchStream& S = b->hS[s];
         BatchStepEntry& E = b->hE[s];
         const float* x = (const float*)X[s];
         if (x_on_host) {
-            float* dst = b->xstage + b->xoff[s];
+            float* dst = b->xstage[xb] + b->xoff[s];
             BCK(cudaMemcpyAsync(dst, X[s], (size_t)S.dims[0] * S.dims[1] * S.dims[2] * sizeof(float),
-                                cudaMemcpyHostToDevice, b->stream),
+                                cudaMemcpyHostToDevice, b->copy_stream),
                 "copy slice");
             x = dst;
         }
@@ -585,6 +617,12 @@ sgcp_status sgcp_batch_step(sgcp_batch* b, const void* const* X, int32_t x_on_ho
                 if ((int64_t)j <= H) E.slot = (int32_t)j - 1;
             }
         }
+    }
+    if (x_on_host) {
+        BCK(cudaEventRecord(b->ev_xstaged, b->copy_stream), "staging event");
+        BCK(cudaStreamWaitEvent(b->stream, b->ev_xstaged, 0), "staging wait");
+        b->xused[xb] = true;
+        b->xnext = xb ^ 1;
     }
     BCK(launch_batch_begin(b->dE, b->hE.data(), b->nS, b->ctl, b->nS, b->finished, b->stream, &b->launches),
         "batch begin");
@@ -636,6 +674,29 @@ sgcp_status sgcp_batch_check(sgcp_batch* b) {
         b->last_error = buf;
         return b->sticky;
     }
+    return SGCP_OK;
+}
+
+namespace {
+// F_w, F_f of every stream (the accepted objective estimates of its temporal and factor solvers)
+// into out[2 s], out[2 s + 1]: one thread per stream reads the stream's two solver states.
+__global__ void k_batch_objectives(const BatchStream* __restrict__ dS, int nS, double* out) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nS; s += gridDim.x * blockDim.x) {
+        out[2 * s] = dS[s].st_w->F_cur;
+        out[2 * s + 1] = dS[s].st_f->F_cur;
+    }
+}
+}  // namespace
+
+sgcp_status sgcp_batch_objectives_async(sgcp_batch* b, double* out) {
+    if (!out) return SGCP_ERR_ARG;
+    if (sgcp_status st = batch_ready(b)) return st;
+    const size_t bytes = (size_t)b->nS * 2 * sizeof(double);
+    if (!b->fout && !balloc(b, &b->fout, bytes)) return bfail(b, SGCP_ERR_OOM, "objective buffer allocation failed");
+    k_batch_objectives<<<(b->nS + 127) / 128, 128, 0, b->stream>>>(b->dS, b->nS, b->fout);
+    BCK(cudaGetLastError(), "objective gather");
+    BCK(cudaMemcpyAsync(out, b->fout, bytes, cudaMemcpyDeviceToHost, b->stream), "objective read-back");
+    b->launches += 1;
     return SGCP_OK;
 }
 

@@ -111,6 +111,39 @@ def test_batched_streams_host_slices(sg):
     run_and_compare(sg, streams, 2, tol=2e-5, host=True)
 
 
+def test_batched_host_slices_queued_without_waiting(sg):
+    """Pinned host slices, three steps queued with no host wait (the staging buffers alternate and
+    the third step refills the first while the second runs), every stream's (F_w, F_f) read back
+    behind each step with sgcp_batch_objectives_async: the values agree with a batch that waits
+    after every step (FP32 sums: 1e-5) and, after the last step, equal sgcp_batch_stats exactly."""
+    n_steps = 3
+    streams = make_streams(n_steps, seed=9)
+    plist = [sg.params(st["dims"], st["R"], st["loss"], seed=st["seed"], **KW) for st in streams]
+    n = len(streams)
+    pinned = [[torch.from_numpy(st["X"][t]).pin_memory() for st in streams] for t in range(n_steps)]
+    ref = []
+    with sg.Batch(plist, [[torch.from_numpy(a).cuda() for a in st["A0"]] for st in streams]) as b:
+        for t in range(n_steps):
+            b.step(pinned[t])
+            ref.append([(b.stats(s)["F_w"], b.stats(s)["F_f"]) for s in range(n)])
+    out = torch.full((n_steps, 2 * n), float("nan"), dtype=torch.float64).pin_memory()
+    with sg.Batch(plist, [[torch.from_numpy(a).cuda() for a in st["A0"]] for st in streams]) as b:
+        for t in range(n_steps):
+            b.step(pinned[t])
+            b.objectives_async(out[t])
+        b.stream.synchronize()
+        b.check()
+        last = [(b.stats(s)["F_w"], b.stats(s)["F_f"]) for s in range(n)]
+    got = out.numpy()
+    assert np.isfinite(got).all()
+    for s in range(n):
+        assert (got[-1, 2 * s], got[-1, 2 * s + 1]) == last[s], s
+        for t in range(n_steps):
+            for c in range(2):
+                r = ref[t][s][c]
+                assert abs(got[t, 2 * s + c] - r) <= 1e-5 * max(abs(r), 1.0), (t, s, c, got[t, 2 * s + c], r)
+
+
 def test_autotuned_unit_shapes_keep_parity(sg):
     streams = make_streams(2, seed=7, shapes=SHAPES[:3])
     table, cfg = run_and_compare(sg, streams, 2, tol=2e-5, batch_kw=dict(autotune=True, tune_reps=2))
