@@ -710,14 +710,37 @@ cudaError_t launch_obj_finish_w(SolverState* st, const T* s, int R, double mu, i
 }
 
 
-// S_H = sum_{h in window} w theta^(t-h) s_h s_h'
+// S_H = sum_{h in window} w theta^(t-h) s_h s_h' (one block).  The window is taken in rounds of
+// kShSlots slots: each slot's weight w theta^(t-h) is formed once per round (not once per entry)
+// and its s_h row staged in shared memory; every entry adds the slots in window order, carrying
+// its sum in S_H across rounds, so the result equals the slot-by-slot sum of history_SH_elem.
+constexpr int kShSlots = 32;
 template <typename T>
-__global__ void k_history_SH(int R, const T* s_hist, const int64_t* h_dev, const int32_t* hist_len,
-                             const SliceDesc* slice, double w, double theta, double* SH) {
+__global__ void __launch_bounds__(256) k_history_SH(int R, const T* s_hist, const int64_t* h_dev,
+                                                    const int32_t* hist_len, const SliceDesc* slice, double w,
+                                                    double theta, double* SH) {
+    __shared__ double wh[kShSlots];
+    __shared__ T sh[kShSlots * 128];   // R <= 128
     const int n = *hist_len;
     const int64_t t = slice->t;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x)
-        SH[i] = history_SH_elem<T>(R, s_hist, h_dev, n, t, w, theta, i);
+    const int RR = R * R;
+    if (n <= 0) {
+        for (int i = threadIdx.x; i < RR; i += blockDim.x) SH[i] = 0.0;
+        return;
+    }
+    for (int h0 = 0; h0 < n; h0 += kShSlots) {
+        const int hn = n - h0 < kShSlots ? n - h0 : kShSlots;
+        __syncthreads();   // the previous round's slots are no longer read
+        if (threadIdx.x < hn) wh[threadIdx.x] = w * pow(theta, (double)(t - __ldcg(h_dev + h0 + threadIdx.x)));
+        for (int e = threadIdx.x; e < hn * R; e += blockDim.x) sh[e] = __ldcg(s_hist + (int64_t)h0 * R + e);
+        __syncthreads();
+        for (int i = threadIdx.x; i < RR; i += blockDim.x) {
+            const int l = i / R, m = i - l * R;
+            double acc = h0 == 0 ? 0.0 : SH[i];
+            for (int h = 0; h < hn; ++h) acc += wh[h] * (double)sh[h * R + l] * (double)sh[h * R + m];
+            SH[i] = acc;
+        }
+    }
 }
 
 template <typename T>
