@@ -228,16 +228,18 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                                              : 0.f;   // X == nullptr: the all-zero slice
             }
             __syncthreads();
-            // Khatri-Rao panel, natural layout (lanes along j) and k-major layout (lanes along rows)
-            for (int i = tid; i < 64 * (RT / 4); i += kBoxThreads) {
-                const int row = i / (RT / 4), j0 = (i - row * (RT / 4)) * 4;
-                float a[4], b[4], p[4];
-                lds_vec<4>(a, A1s + (row >> lb2) * LDR + j0);
-                lds_vec<4>(b, A2t + (row & (B2 - 1)) * LDR + j0);
+            // Khatri-Rao panel, natural layout (lanes along j; only G3 reads it) and k-major layout
+            // (lanes along rows)
+            if (wantG)
+                for (int i = tid; i < 64 * (RT / 4); i += kBoxThreads) {
+                    const int row = i / (RT / 4), j0 = (i - row * (RT / 4)) * 4;
+                    float a[4], b[4], p[4];
+                    lds_vec<4>(a, A1s + (row >> lb2) * LDR + j0);
+                    lds_vec<4>(b, A2t + (row & (B2 - 1)) * LDR + j0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) p[q] = a[q] * b[q];
-                sts_vec<4>(KRn + row * LDR + j0, p);
-            }
+                    for (int q = 0; q < 4; ++q) p[q] = a[q] * b[q];
+                    sts_vec<4>(KRn + row * LDR + j0, p);
+                }
             for (int i = tid; i < RT * 16; i += kBoxThreads) {
                 const int j = i >> 4, r0 = (i & 15) * 4;
                 float p[4];
@@ -281,11 +283,12 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                     }
                 }
             if (!wantY) continue;
+            if (wantG)   // Y row-major: only G3 reads it
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float v[2] = {y[i][0], y[i][1]};
-                sts_vec<2>(Yn + (4 * g0 + i) * L::LDY + 2 * g1, v);
-            }
+                for (int i = 0; i < 4; ++i) {
+                    const float v[2] = {y[i][0], y[i][1]};
+                    sts_vec<2>(Yn + (4 * g0 + i) * L::LDY + 2 * g1, v);
+                }
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const float v[4] = {y[0][c], y[1][c], y[2][c], y[3][c]};
