@@ -240,12 +240,13 @@ __device__ void dense_box(const BoxGeom& g, int want, float* sm) {
                     for (int q = 0; q < 4; ++q) p[q] = a[q] * b[q];
                     sts_vec<4>(KRn + row * LDR + j0, p);
                 }
-            for (int i = tid; i < RT * 16; i += kBoxThreads) {
+            for (int i = tid; i < RT * 16; i += kBoxThreads) {   // rows r0 .. r0 + 3 share one i1 (B2 >= 4)
                 const int j = i >> 4, r0 = (i & 15) * 4;
+                const float a = A1s[(r0 >> lb2) * LDR + j];
+                const float* b = A2t + (r0 & (B2 - 1)) * LDR + j;
                 float p[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    p[q] = A1s[((r0 + q) >> lb2) * LDR + j] * A2t[((r0 + q) & (B2 - 1)) * LDR + j];
+                for (int q = 0; q < 4; ++q) p[q] = a * b[q * LDR];
                 sts_vec<4>(KRt + j * 64 + r0, p);
             }
             __syncthreads();
