@@ -142,3 +142,13 @@ def test_batch_argument_errors_are_synchronous_without_a_gpu(sg):
     half.alloc = sg.ALLOC_FN(lambda n, u: None)
     pa = (sg.sgcp_params * 1)(good)
     assert sg.sgcp_batch_create(1, pa, arr, None, ctypes.byref(half), None, ctypes.byref(out)) == sg.ERR_ARG
+
+
+def test_objective_read_back_argument_errors_without_a_gpu(sg):
+    """The asynchronous objective read-backs check their handles and output pointer before any
+    CUDA call."""
+    buf = (ctypes.c_double * 4)()
+    assert sg.sgcp_objectives_async(None, buf) == sg.ERR_ARG
+    assert sg.sgcp_objectives_async(None, None) == sg.ERR_ARG
+    assert sg.sgcp_batch_objectives_async(None, buf) == sg.ERR_ARG
+    assert sg.sgcp_batch_objectives_async(None, None) == sg.ERR_ARG
