@@ -383,7 +383,9 @@ def run_native(args, cfg, world, rank, local):
                                  "bandwidth of the algorithmic gathers and scatters, most of which L2 serves",
                          "kernel": "k_sparse_grad<3,32> (factor gradient, 2e5 samples)",
                          "kernel_us": kern_s * 1e6},
-            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "note": "wall clock of steps queued back to back from pinned host slices, each step's F_w, "
+                            "F_f read back; no L2 flush between these steps (the device-timed value flushes)"},
             "clocks": clk,
             "step_ms": {"min": min(step_ms), "max": max(step_ms)},
         }
