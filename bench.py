@@ -390,9 +390,13 @@ def run_native(args, cfg, world, rank, local):
             "step_ms": {"min": min(step_ms), "max": max(step_ms)},
         }
         if not args.no_dense_record:
-            out["dense_256_r64"] = dense_precision_record(dev)
+            out["dense_256_r64"], dense_results = dense_precision_record(dev)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(cfg, host[0])
+            if not args.no_dense_record:
+                err, timing = dense_oracle_errors(dense_results)
+                out["dense_256_r64"]["err_vs_fp64"] = err
+                out["cpu_baseline"]["dense_256_r64"] = timing
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -426,40 +430,40 @@ def cpu_baseline(cfg, slice0, budget_s=10.0):
 DENSE_SOLVER = dict(H=10, w=1.0, theta=1.0, kappa_w=20, kappa_f=5, tau_w=100, tau_f=100, alpha_w=10.0, alpha_f=1e-4)
 
 
-def dense_precision_record(dev, n_time=2):
-    """The second half of the metric on the 256^3, R = 64 Gaussian slices: per-slice update time
-    (sgcp_step with the Table 2 Gaussian-row solvers, kappa_w = 20, kappa_f = 5, tau = 100), the
-    dense factor-gradient kernel time, and the error of every gradient result (G1, G2, G3, g_s, F)
-    against the FP64 oracle at one point near the planted factors, for the plain FP32 path and the
-    BF16 / FP16 tensor-core MTTKRP paths."""
-    import torch
-    import paper_2110_14514_gb300 as sg
-    from oracle import gcp
+def dense_record_point():
+    """The 256^3, R = 64 Gaussian slices 1 and 2 and the point of the precision record: planted
+    factors + 0.05 N(0,1) (seed 9) and the planted s_1 (inputs only; no gradient arithmetic)."""
     cfg = S.workload("dense_gaussian_3way")
     X, s_true = S.dense_slice(cfg, 1)
     X2, _ = S.dense_slice(cfg, 2)
-    A_true = S.truth(cfg)
     rng = np.random.default_rng(9)
-    A_pt = [(a + 0.05 * rng.standard_normal(a.shape)).astype(np.float32) for a in A_true]
-    s_pt = s_true.astype(np.float32)
-    Go, gso, Fo = gcp.dense_gradient(X, s_pt, A_pt, "gaussian")
+    A_pt = [(a + 0.05 * rng.standard_normal(a.shape)).astype(np.float32) for a in S.truth(cfg)]
+    return cfg, X, X2, s_true.astype(np.float32), A_pt
+
+
+def dense_precision_record(dev, n_time=2):
+    """The second half of the metric on the 256^3, R = 64 Gaussian slices: per-slice update time
+    (sgcp_step with the Table 2 Gaussian-row solvers, kappa_w = 20, kappa_f = 5, tau = 100) and the
+    dense factor-gradient kernel time for the plain FP32 path and the BF16 / FP16 tensor-core MTTKRP
+    paths. Also returns every gradient result (G1, G2, G3, g_s, F) of each path at one point near
+    the planted factors; the cpu_baseline leg compares them with the FP64 oracle
+    (dense_oracle_errors)."""
+    import torch
+    import paper_2110_14514_gb300 as sg
+    cfg, X, X2, s_pt, A_pt = dense_record_point()
     Xd = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev) for x in (X, X2)]
     A0 = [torch.from_numpy(a).to(dev) for a in S.init_factors(cfg)]
     Apd = [torch.from_numpy(a).to(dev) for a in A_pt]
     spd = torch.from_numpy(s_pt).to(dev)
 
-    def rel(a, b):
-        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
-
     out = {"solver": DENSE_SOLVER, "point": "planted factors + 0.05 N(0,1), planted s_1"}
+    results = {}
     for name, prec in (("fp32", sg.PREC_F32), ("bf16", sg.PREC_BF16_MTTKRP), ("fp16", sg.PREC_F16_MTTKRP)):
         p = sg.params(cfg["dims"], cfg["rank"], "gaussian", precision=prec, seed=77, **DENSE_SOLVER)
         with sg.Context(p, A0) as ctx:
             G, gs, f = ctx.gradient(spd, Apd, X=Xd[0])
             ctx.check()
-            errs = {f"G{k + 1}": rel(G[k].cpu().numpy(), Go[k]) for k in range(3)}
-            errs["gs"] = rel(gs.cpu().numpy(), gso)
-            errs["F"] = abs(f.item() - Fo) / abs(Fo)
+            results[name] = ([g.cpu().numpy() for g in G], gs.cpu().numpy(), f.item())
             ctx.step(X=Xd[0])                          # graph build and warm-up
             torch.cuda.synchronize()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_time)]
@@ -484,9 +488,30 @@ def dense_precision_record(dev, n_time=2):
             ctx.check()
         out[f"{name}_ms_per_slice"] = ms
         out[f"{name}_kernel_us"] = e0.elapsed_time(e1) * 1e3 / nrep
-        out.setdefault("err_vs_fp64", {})[name] = errs
     out["bf16_speedup_vs_fp32_per_slice"] = out["fp32_ms_per_slice"] / out["bf16_ms_per_slice"]
-    return out
+    return out, results
+
+
+def dense_oracle_errors(results):
+    """cpu_baseline leg of the dense record: the FP64 oracle's gradient (loss + all gradients) of the
+    record's slice at the record's point, timed on one host core, and the relative error of every
+    result of each precision against it."""
+    from oracle import gcp
+    _, X, _, s_pt, A_pt = dense_record_point()
+    t0 = time.perf_counter()
+    Go, gso, Fo = gcp.dense_gradient(X, s_pt, A_pt, "gaussian")
+    dt = time.perf_counter() - t0
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+    err = {}
+    for name, (G, gs, f) in results.items():
+        err[name] = {f"G{k + 1}": rel(G[k], Go[k]) for k in range(3)}
+        err[name]["gs"] = rel(gs, gso)
+        err[name]["F"] = abs(f - Fo) / abs(Fo)
+    timing = {"value": X.size / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
+              "sample": "one FP64 oracle dense gradient (loss + all gradients) of one 256^3 slice, R = 64"}
+    return err, timing
 
 
 def run_native_dense(args, cfg, world, rank, local):
@@ -620,12 +645,11 @@ def run_native_dense(args, cfg, world, rank, local):
 def run_native_autograd(args, cfg, world, rank, local):
     """100^3, R = 16 Poisson slices (the autograd configuration): one step is the GCP loss forward
     and its hand-written backward through torch.autograd (GCPLoss; m recomputed in the backward
-    launch), set beside the same loss and gradients from one fused FP32 call, with both compared
-    to the FP64 oracle gradient of the first slice."""
+    launch), set beside the same loss and gradients from one fused FP32 call; the cpu_baseline leg
+    compares both with the FP64 oracle gradient of the first slice."""
     import torch
     import paper_2110_14514_gb300 as sg
     from paper_2110_14514_gb300.autograd import GraphedGCPLoss, gcp_loss
-    from oracle import gcp
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -696,19 +720,16 @@ def run_native_autograd(args, cfg, world, rank, local):
     t1.record()
     torch.cuda.synchronize()
     e2e_s = t0.elapsed_time(t1) / 1e3
-    # accuracy at the current point against the FP64 oracle (first slice)
+    # both gradients of the first slice at the current point (the cpu_baseline leg compares them
+    # with the FP64 oracle's)
     ag_step(dsl[0])
     G_ag = [a.grad.double().cpu().numpy() for a in A]
     gs_ag = s.grad.double().cpu().numpy()
     Gp, gsp, _ = ctx.gradient(sd, Ad, X=dsl[0])
-    Go, gso, _ = gcp.dense_gradient(host[0].astype(np.float64), sd.double().cpu().numpy(),
-                                    [a.double().cpu().numpy() for a in Ad], cfg["loss"])
-
-    def rel(a, b):
-        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    acc = {"autograd_vs_oracle": max([rel(G_ag[k], Go[k]) for k in range(3)] + [rel(gs_ag, gso)]),
-           "plain_vs_oracle": max([rel(Gp[k].double().cpu().numpy(), Go[k]) for k in range(3)] +
-                                  [rel(gsp.double().cpu().numpy(), gso)])}
+    Gp = [g.double().cpu().numpy() for g in Gp]
+    gsp = gsp.double().cpu().numpy()
+    s_cur = sd.double().cpu().numpy()
+    A_cur = [a.double().cpu().numpy() for a in Ad]
     # the kernels alone: the two launches of an autograd step (loss pass, then the factor and
     # temporal gradients) back to back behind a sleep kernel, outputs preallocated (the 4 MB
     # slice stays in L2 across these launches)
@@ -746,7 +767,7 @@ def run_native_autograd(args, cfg, world, rank, local):
                    "graphed_value": world * args.steps * omega / graphed_s,
                    "graphed_note": "GraphedGCPLoss: the same forward + backward captured in a CUDA graph and "
                                    "replayed after a device copy of the step's slice into its static buffer",
-                   "accuracy_rel_max": acc},
+},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
@@ -758,17 +779,24 @@ def run_native_autograd(args, cfg, world, rank, local):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's gradients of the first slice at the current point, ~10 s on one host core; the
+        # first also gives the accuracy of both device gradients
+        from oracle import gcp
         Xh = host[0].astype(np.float64)
-        Ah = [a.double().cpu().numpy() for a in A0]
-        sh = np.full(R, 0.5)
         t0c = time.perf_counter()
         n = 0
-        while time.perf_counter() - t0c < 10.0:
-            gcp.dense_gradient(Xh, sh, Ah, cfg["loss"])
+        while n == 0 or time.perf_counter() - t0c < 10.0:
+            Go, gso, _ = gcp.dense_gradient(Xh, s_cur, A_cur, cfg["loss"])
             n += 1
         dt = time.perf_counter() - t0c
         out["cpu_baseline"] = {"value": n * omega / dt, "unit": "entries/s", "cores": 1, "kind": "oracle",
                                "sample": f"{n} FP64 oracle dense gradients (loss + all gradients) of one 100^3 slice"}
+
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        out["config"]["accuracy_rel_max"] = {
+            "autograd_vs_oracle": max([rel(G_ag[k], Go[k]) for k in range(3)] + [rel(gs_ag, gso)]),
+            "plain_vs_oracle": max([rel(Gp[k], Go[k]) for k in range(3)] + [rel(gsp, gso)])}
     return out
 
 
