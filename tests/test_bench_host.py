@@ -82,3 +82,63 @@ def test_single_process_max_is_the_value():
     import bench
     assert bench.max_over_ranks(3.25, None) == 3.25
     assert bench.whole_job_rate(1, 4, 10.0, 2.0) == 20.0
+
+
+# functions that make up bench.py's CPU-baseline legs (the oracle timed on host cores) and the
+# helpers that only they reach
+_BASELINE_LEGS = {"cpu_baseline", "batched_cpu_baseline", "dense_oracle_errors", "run_reference"}
+_LEG_HELPERS = {"_oracle_init", "_oracle_sparse_worker", "OraclePool"}
+
+
+def _guarded(node, parents):
+    """True where `node` sits in a baseline leg, a leg helper, or the body of an `if` that tests
+    --no-cpu-baseline or --impl."""
+    import ast
+    child = node
+    while child in parents:
+        p = parents[child]
+        if isinstance(p, (ast.FunctionDef, ast.ClassDef)) and p.name in _BASELINE_LEGS | _LEG_HELPERS:
+            return True
+        if isinstance(p, ast.If) and child in p.body:
+            names = {a.attr for a in ast.walk(p.test) if isinstance(a, ast.Attribute)}
+            if names & {"no_cpu_baseline", "impl"}:
+                return True
+        child = p
+    return False
+
+
+def test_bench_reaches_the_oracle_only_from_its_baseline_legs():
+    """bench.py imports the oracle only inside its CPU-baseline legs or behind their flags, and
+    calls those legs only behind the same flags: the timed device path never runs oracle code."""
+    import ast
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    parents = {c: p for p in ast.walk(tree) for c in ast.iter_child_nodes(p)}
+    imports = [n for n in ast.walk(tree)
+               if (isinstance(n, ast.ImportFrom) and (n.module or "").split(".")[0] == "oracle")
+               or (isinstance(n, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in n.names))]
+    assert len(imports) >= 3
+    for n in imports:
+        assert _guarded(n, parents), f"oracle imported outside a baseline leg at bench.py:{n.lineno}"
+    uses = [n for n in ast.walk(tree) if isinstance(n, ast.Name) and n.id in _BASELINE_LEGS | _LEG_HELPERS]
+    assert uses
+    for n in uses:
+        assert _guarded(n, parents), f"{n.id} used outside a baseline leg at bench.py:{n.lineno}"
+
+
+def test_dense_record_errors_vanish_at_the_oracle_gradient():
+    """dense_oracle_errors compares each precision's results with the oracle's FP64 gradient at
+    the record's point: the oracle's own gradient scores zero, a perturbed one its perturbation."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from oracle import gcp
+    _, X, _, s_pt, A_pt = bench.dense_record_point()
+    Go, gso, Fo = gcp.dense_gradient(X, s_pt, A_pt, "gaussian")
+    G2 = [g.copy() for g in Go]
+    G2[1] *= 1.001
+    err, timing = bench.dense_oracle_errors({"exact": (Go, gso, Fo), "g2": (G2, gso, Fo * (1 + 1e-6))})
+    assert all(v == 0.0 for v in err["exact"].values()), err["exact"]
+    assert err["g2"]["G1"] == 0.0 and err["g2"]["G3"] == 0.0 and err["g2"]["gs"] == 0.0
+    assert abs(err["g2"]["G2"] - 1e-3) < 1e-9 and abs(err["g2"]["F"] - 1e-6) < 1e-9
+    assert timing["kind"] == "oracle" and timing["cores"] == 1 and timing["value"] > 0
+    assert np.isfinite(timing["value"])
