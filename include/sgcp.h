@@ -185,6 +185,7 @@ typedef struct {
                                      (the first point plus every line-search trial); ADAM: 0 */
     int32_t pad;
 } sgcp_stats_t;
+typedef sgcp_stats_t sgcp_step_stats;   /* the same record under its per-step name */
 
 /* Device-memory provider for the state a context or a batch owns (the variables of Alg. 1 and
  * Table 1: factor matrices, Abar, ADAM moments and checkpoints, history window, Gram sums, the
@@ -363,7 +364,7 @@ sgcp_status sgcp_kruskal_score(int32_t nmodes, int32_t rank, const int64_t* dims
                                const void* const* A, const void* const* B, double* score_out, int32_t* perm_out,
                                void* cuda_stream);
 
-/* Process the next slice: one pass of the loop body of Alg. 1 (temporal/* Process the next slice: one pass of the loop body of Alg. 1 (temporal/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
+/* Process the next slice: one pass of the loop body of Alg. 1 (temporal
  * solve, factor solve, reservoir history update, Abar <- A).  Asynchronous;
  * the whole solver sequence runs as CUDA graphs on the context stream. */
 sgcp_status sgcp_step(sgcp_ctx* ctx, const sgcp_slice* X_t);

@@ -304,7 +304,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     make_uint4(h16[0], h16[1], h16[2], h16[3]);
         }
     };
-    // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16)
     // KR panel of a tile from its staged rows: KR = (s A1) (.) A2 as bf16 hi / lo (and fp16).
     // A warp covers 8 consecutive rows x 4 chunks of 8 j, so its 16-byte stores hit distinct banks.
     auto build_kr = [&](int sbuf, int kbuf, int lo, int cnt) {   // by threads lo .. lo + cnt - 1
