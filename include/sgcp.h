@@ -210,10 +210,10 @@ typedef struct {
 
 typedef struct sgcp_ctx sgcp_ctx;
 
-/* Version string of the library. */
+/* Version string of the library (library plumbing: no passage of the paper). */
 const char* sgcp_version(void);
 
-/* Human-readable name of a status code. */
+/* Human-readable name of a status code (library plumbing: no passage of the paper). */
 const char* sgcp_status_string(sgcp_status status);
 
 /* Defaults of Table 2 of the paper (beta1 = 0.9, beta2 = 0.999, eps = 1e-8,
@@ -239,10 +239,12 @@ sgcp_status sgcp_create(const sgcp_params* params, const void* const* init_facto
                         int32_t n_hist, const int64_t* hist_t, const void* hist_s,
                         int64_t t0, const sgcp_allocator* allocator, void* cuda_stream, sgcp_ctx** out);
 
-/* Destroy a context and free its device state (synchronises its stream). */
+/* Destroy a context and free its device state (synchronises its stream).  The end
+ * of the stream of Alg. 1; library plumbing with no passage of its own.  NULL is a no-op. */
 void sgcp_destroy(sgcp_ctx* ctx);
 
-/* Message describing the most recent error of ctx ("" if none). */
+/* Message describing the most recent error of ctx ("" if none; library plumbing).
+ * The string is owned by the context and valid until its next call or destruction. */
 const char* sgcp_last_error(const sgcp_ctx* ctx);
 
 /* Load a slice into the context: copies host data if on_host, checks
@@ -268,7 +270,9 @@ sgcp_status sgcp_ingest(sgcp_ctx* ctx, const sgcp_slice* X);
 sgcp_status sgcp_gradient(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, const void* const* A,
                           const sgcp_grad_opts* opts, void* const* G_out, void* gs_out, double* f_out);
 
-/* Materialise the coordinates of one sparse sample draw (the same draw
+/* Materialise the coordinates of one sparse sample draw, the stratified
+ * sample of Alg. 6 (GRAD sets) or of Alg. 5 (OBJ sets), Sec. 4.3: nonzeros
+ * drawn uniformly, zeros by rejection against the nonzero hash (the same draw
  * sgcp_gradient makes with these arguments): coords_out (device int32,
  * [n][ndim]) with n = p + q (GRAD sets) or p_obj + q_obj (OBJ sets),
  * nonzero samples first; attempt_out (device int32 [n] or NULL) receives the
@@ -276,8 +280,10 @@ sgcp_status sgcp_gradient(sgcp_ctx* ctx, const sgcp_slice* X, const void* s, con
 sgcp_status sgcp_sample_coords(sgcp_ctx* ctx, const sgcp_slice* X, int32_t sample_set, int64_t t,
                                uint32_t draw, int32_t* coords_out, int32_t* attempt_out);
 
-/* The sparse gradient of sgcp_gradient without a context and without any
- * device allocation.  The paper has no counterpart: this entry point exists
+/* The sparse gradient of sgcp_gradient (Sec. 2.2 eqs. gcp_grad_A and
+ * gcp_grad_lambda over the stratified sample of Alg. 6) without a context
+ * and without any device allocation.  The paper has no counterpart of this
+ * calling form: it exists
  * for callers that cannot let a library allocate device memory -- for
  * instance a serving process that reserves its whole GPU memory budget at
  * start-up, or a latency-critical loop where a cudaMalloc, which may
@@ -369,20 +375,28 @@ sgcp_status sgcp_kruskal_score(int32_t nmodes, int32_t rank, const int64_t* dims
  * the whole solver sequence runs as CUDA graphs on the context stream. */
 sgcp_status sgcp_step(sgcp_ctx* ctx, const sgcp_slice* X_t);
 
-/* Copy the current factor matrices (device, ndim pointers) and the last
- * temporal weights (device, R) out of the context; either may be NULL.
+/* Copy the current factor matrices A^(k) (device, ndim pointers) and the last
+ * temporal weights s_t (device, R) out of the context, i.e. the model Alg. 1
+ * holds after its last slice; either may be NULL.
  * t_out (host, may be NULL) receives the index of the last processed slice.
  * Asynchronous on the context stream. */
 sgcp_status sgcp_factors(sgcp_ctx* ctx, void* const* A_out, void* s_out, int64_t* t_out);
 
-/* Copy the history window: h_out (host, H int64 time indices) and s_out
- * (device, H x R weights, may be NULL); *n_out receives |window|. */
+/* Copy the history window of Sec. 4.1 (the reservoir-sampled time indices h
+ * and their temporal weights s_h): h_out (host, H int64 time indices) and s_out
+ * (device, H x R weights, may be NULL); *n_out receives |window|.  h_out and
+ * n_out are filled at once from the context's host-side window bookkeeping;
+ * the s_out copy is asynchronous on the context stream. */
 sgcp_status sgcp_history(sgcp_ctx* ctx, int64_t* h_out, void* s_out, int32_t* n_out);
 
-/* Synchronise the context stream and return its latched device error status. */
+/* Synchronise the context stream and return its latched device error status
+ * (library plumbing: the device error word described above). */
 sgcp_status sgcp_check(sgcp_ctx* ctx);
 
-/* Synchronise and report solver statistics of the last slice. */
+/* Synchronise and report solver statistics of the last slice: the objective
+ * estimates of Alg. 3 and Alg. 4 (EstimateObjective, Alg. 5), the epochs each
+ * ran and which were accepted, and the ADAM learning rates after the decays of
+ * Alg. 3 / Alg. 4 (sgcp_stats_t above). */
 sgcp_status sgcp_stats(sgcp_ctx* ctx, sgcp_stats_t* out);
 
 /* Queue on the context stream, behind the work queued so far, a device-to-host
@@ -397,7 +411,8 @@ sgcp_status sgcp_stats(sgcp_ctx* ctx, sgcp_stats_t* out);
  * between steps.  No device error check: sgcp_check reports latched errors. */
 sgcp_status sgcp_objectives_async(sgcp_ctx* ctx, double* out);
 
-/* Checkpoint: the state that makes the stream resumable (t, i, Abar, s,
+/* Checkpoint (library plumbing; the state is that of Alg. 1 and Table 1): the
+ * state that makes the stream resumable (t, i, Abar, s,
  * history window, factor-solver ADAM moments, learning rate).  sgcp_state_size
  * gives the byte size; export writes it to a host buffer, import restores it
  * into a context created with the same params.  Both synchronise. */
@@ -446,19 +461,29 @@ typedef struct {
     int64_t spin_limit;            /* empty polls before a block gives up (SGCP_ERR_TIMEOUT); 0 = default 2^22 */
 } sgcp_batch_opts;
 
+/* Defaults of sgcp_batch_opts (library plumbing): autotune off, tune_reps 3,
+ * no table, grid_blocks 0 (every resident block), spin_limit 0 (2^22).
+ * Returns SGCP_ERR_ARG if opts is NULL. */
 sgcp_status sgcp_batch_opts_default(sgcp_batch_opts* opts);
 
-/* params: host array of n_streams parameter sets.  init_factors: host array
+/* Create a batch of n_streams independent streams, each as sgcp_create would
+ * (Alg. 1 before its loop).  params: host array of n_streams parameter sets.  init_factors: host array
  * of 3 * n_streams device pointers (stream s, mode k at [3 s + k]), each an
  * I_k x R float matrix copied into the batch.  opts may be NULL (defaults).
  * allocator and cuda_stream as in sgcp_create.  Streams start at t = 0 with empty history. */
 sgcp_status sgcp_batch_create(int32_t n_streams, const sgcp_params* params, const void* const* init_factors,
                               const sgcp_batch_opts* opts, const sgcp_allocator* allocator, void* cuda_stream,
                               sgcp_batch** out);
+
+/* Destroy a batch and free its device state (synchronises its stream; library
+ * plumbing).  NULL is a no-op. */
 void sgcp_batch_destroy(sgcp_batch* batch);
+
+/* Message describing the most recent error of the batch ("" if none; library plumbing). */
 const char* sgcp_batch_last_error(const sgcp_batch* batch);
 
-/* Advance every stream by one slice.  X: host array of n_streams pointers to
+/* Advance every stream by one slice: the loop body of Alg. 1 for each stream
+ * (see above).  X: host array of n_streams pointers to
  * dense float slices in C order (I_1 x I_2 x I_3 of that stream); device
  * pointers when x_on_host = 0, host pointers when x_on_host = 1 (the call then
  * queues their copies into one of two library-owned staging buffers, used in
@@ -469,12 +494,14 @@ const char* sgcp_batch_last_error(const sgcp_batch* batch);
  * Asynchronous on the batch stream. */
 sgcp_status sgcp_batch_step(sgcp_batch* batch, const void* const* X, int32_t x_on_host);
 
-/* Stream s: copy its factor matrices (3 device pointers, entries may be NULL)
+/* Stream s: copy the model Alg. 1 holds after its last slice, its factor
+ * matrices (3 device pointers, entries may be NULL)
  * and temporal weights (device, R floats, may be NULL); t_out (host) receives
  * its last slice index.  Asynchronous on the batch stream. */
 sgcp_status sgcp_batch_factors(sgcp_batch* batch, int32_t s, void* const* A_out, void* s_out, int64_t* t_out);
 
-/* Synchronise; statistics of stream s after its last slice (as sgcp_stats). */
+/* Synchronise; statistics of stream s after its last slice (as sgcp_stats: the
+ * Alg. 3 / Alg. 4 objective estimates, epochs and learning rates). */
 sgcp_status sgcp_batch_stats(sgcp_batch* batch, int32_t s, sgcp_stats_t* out);
 
 /* Queue on the batch stream, behind the work queued so far, the read-back of
@@ -487,14 +514,16 @@ sgcp_status sgcp_batch_stats(sgcp_batch* batch, int32_t s, sgcp_stats_t* out);
  * and one copy; the gather buffer is allocated at the first call. */
 sgcp_status sgcp_batch_objectives_async(sgcp_batch* batch, double* out);
 
-/* Synchronise and return the latched device error status of the batch. */
+/* Synchronise and return the latched device error status of the batch
+ * (library plumbing). */
 sgcp_status sgcp_batch_check(sgcp_batch* batch);
 
-/* The tuning table of the batch (known plus newly timed entries): up to cap
+/* The tuning table of the batch (library plumbing: tile shapes of the
+ * gradient unit, no passage of the paper; known plus newly timed entries): up to cap
  * entries to out (host); *n_out receives the table size. */
 sgcp_status sgcp_batch_tune_table(const sgcp_batch* batch, sgcp_tune_entry* out, int32_t cap, int32_t* n_out);
 
-/* The unit tile shape stream s runs with (its table entry). */
+/* The unit tile shape stream s runs with (its table entry; library plumbing). */
 sgcp_status sgcp_batch_unit_config(const sgcp_batch* batch, int32_t s, sgcp_tune_entry* out);
 
 #ifdef __cplusplus

@@ -152,3 +152,27 @@ def test_objective_read_back_argument_errors_without_a_gpu(sg):
     assert sg.sgcp_objectives_async(None, None) == sg.ERR_ARG
     assert sg.sgcp_batch_objectives_async(None, buf) == sg.ERR_ARG
     assert sg.sgcp_batch_objectives_async(None, None) == sg.ERR_ARG
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each function the header declares sits under a comment (shared by a run of declarations
+    with no blank line between) that cites the passage of the paper defining its operation
+    (Alg., eq., Sec. or Table) or says it is library plumbing with no such passage."""
+    src = open(HEADER).read()
+    tokens = re.finditer(r"/\*.*?\*/|\b(sgcp_[a-z_0-9]+)\s*\(", src, flags=re.S)
+    last_comment, last_end, seen = None, 0, {}
+    for m in tokens:
+        if m.group(0).startswith("/*"):
+            last_comment = re.sub(r"\s*\n\s*\*?\s*", " ", m.group(0))   # one line, no leading '*'
+            last_end = m.end()
+            continue
+        between = src[last_end:m.start()]
+        if last_comment is None or re.search(r"\n[ \t]*\n", between):
+            seen.setdefault(m.group(1), None)
+            continue
+        seen.setdefault(m.group(1), last_comment)
+    names = declared_functions()
+    assert set(names) <= set(seen), set(names) - set(seen)
+    cite = re.compile(r"Alg\. \d|eqs?\. |Sec\. \d|Table \d|library plumbing")
+    missing = [n for n in names if not (seen[n] and cite.search(seen[n]))]
+    assert not missing, missing
